@@ -1,0 +1,122 @@
+/*
+ * crkdg_oracle.h -- plain FP64 CPU reference of the bound-preserving compact
+ * Runge--Kutta discontinuous Galerkin (cRKDG) method of Liu, Sun and Zhang
+ * (arXiv 2412.16002).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  The product path
+ * (paper_2412_16002_gb300/) never links, imports or calls it, and it shares no
+ * code, tables or headers with the CUDA path.
+ *
+ * Representation: modal tensor Legendre basis P_i(xi) P_j(eta) on each cell
+ * (the CUDA path is nodal at Gauss points; both define the same discrete
+ * scheme because every integral uses the same (k+1)-point Gauss quadrature and
+ * both mass matrices are integrated exactly).
+ */
+#ifndef CRKDG_ORACLE_H
+#define CRKDG_ORACLE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_MAXN 6 /* nodes per direction: k <= 5 */
+#define ORC_MAXM 4 /* components: Euler 2D */
+#define ORC_MAXS 6 /* RK stages */
+
+enum { ORC_FLUX_ADVECTION = 0, ORC_FLUX_BURGERS = 1, ORC_FLUX_EULER = 2 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_OUTFLOW = 1, ORC_BC_REFLECT = 2, ORC_BC_DIRICHLET = 3,
+       ORC_BC_EXACT = 4 };
+enum { ORC_OP_G = 0, ORC_OP_F = 1 };
+
+/* exact-solution exterior state (test-only boundary condition, e.g. Sec. 4.2) */
+typedef void (*orc_exact_fn)(double x, double y, double t, double *u, void *ctx);
+
+typedef struct orc_problem {
+    int dim, nx, ny, k, n, L, m, nmodes, ncell;
+    double x0, x1, y0, y1, hx, hy;
+    int flux;
+    double gamma, vel[2];
+    double lo, hi, eps;      /* scalar bounds [lo,hi]; Euler epsilon of B^eps */
+    int bc[4];               /* sides: 0 left, 1 right, 2 bottom, 3 top */
+    double bc_state[4][ORC_MAXM];
+    int limiter_on;          /* 1: scaling limiter after every stage */
+    int max_halvings;
+    orc_exact_fn exact;
+    void *exact_ctx;
+    double xg[ORC_MAXN], wg[ORC_MAXN]; /* Gauss-Legendre on [-1,1] */
+    double xl[ORC_MAXN], wl[ORC_MAXN]; /* Gauss-Lobatto on [-1,1] */
+} orc_problem;
+
+typedef struct orc_info {
+    double dt_taken;
+    int restarts;
+    long long cells_limited;
+    double theta_min;
+} orc_info;
+
+/* quadrature (Sec. 2.2.1) */
+void orc_gauss_legendre(int n, double *x, double *w);
+void orc_gauss_lobatto(int L, double *x, double *w);
+double orc_legendre(int i, double x);
+double orc_dlegendre(int i, double x);
+
+orc_problem *orc_create(int dim, int nx, int ny, int k, double x0, double x1, double y0,
+                        double y1, int flux, double gamma, double vx, double vy, double lo,
+                        double hi, double eps, const int *bc, const double *bc_state);
+void orc_destroy(orc_problem *P);
+void orc_set_exact(orc_problem *P, orc_exact_fn fn, void *ctx);
+void orc_set_options(orc_problem *P, int limiter_on, int max_halvings);
+size_t orc_state_size(const orc_problem *P); /* doubles: ncell*m*n^dim */
+
+/* nodal (Gauss points, layout [m][ny][nx][n_y][n_x]) <-> modal */
+void orc_nodal_to_modal(const orc_problem *P, const double *nodal, double *modal);
+void orc_modal_to_nodal(const orc_problem *P, const double *modal, double *nodal);
+
+/* state evaluation */
+void orc_point_state(const orc_problem *P, const double *c, int cell, double xi, double eta,
+                     double *u);
+void orc_cell_averages(const orc_problem *P, const double *c, double *avg); /* [cell][m] */
+
+/* physics */
+void orc_flux(const orc_problem *P, const double *u, int dir, double *f);
+double orc_speed(const orc_problem *P, const double *u, int dir);
+double orc_pressure(const orc_problem *P, const double *u);
+
+/* spatial operators G = -div^loc f (Sec. 2.1) and F = -div^DG f (eq. dxDG),
+ * modal in -> modal out; t is the time at which an exact boundary is sampled */
+void orc_apply(const orc_problem *P, int op, const double *in, double *out, double t);
+
+/* scaling limiter (Prop. 2.4 scalar; eq. Euler-limiter), in place.
+ * theta_out (optional, [ncell]) receives the combined scaling per cell. */
+long long orc_limit(const orc_problem *P, double *c, double *theta_out);
+int orc_averages_admissible(const orc_problem *P, const double *c); /* 1 if all in B^eps */
+/* minimum over S_K of each bound margin: scalar [u-lo, hi-u]; Euler [rho-eps, rhoe-eps] */
+void orc_min_margins(const orc_problem *P, const double *c, double *margins2);
+
+/* a0 = max over S_K points and directions of the spectral radius (Sec. 2.1 notation) */
+double orc_a0(const orc_problem *P, const double *c);
+double orc_max_dt(const orc_problem *P, const double *c, double cfl);
+
+/* one limited cRKDG step (Scheme 1L, eq. rkdg-lim) with the Sec. 4.1 restart loop.
+ * A: s*s row-major strictly lower; b: s.  Returns 0 ok, 4 if max_halvings exceeded
+ * (state unchanged). */
+int orc_step(const orc_problem *P, double *c, double dt, int s, const double *A, const double *b,
+             double t, orc_info *info);
+/* one attempt without restarts, recording every stage: u_stage and ut_stage are
+ * [s+1][state] (index s = final stage).  Returns 0 if every stage average was
+ * admissible, else the 1-based stage index that failed (states up to it are filled). */
+int orc_step_stages(const orc_problem *P, const double *c, double dt, int s, const double *A,
+                    const double *b, double t, double *u_stage, double *ut_stage);
+
+/* diagnostics */
+double orc_total_mass(const orc_problem *P, const double *c, int comp);
+double orc_l2_error_exact(const orc_problem *P, const double *c, double t, int nq);
+double orc_l1_error_exact(const orc_problem *P, const double *c, double t, int nq);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,210 @@
+"""Seeded synthetic inputs for the cRKDG workloads.
+
+This module holds no part of the method's arithmetic: it only places sample
+points (Gauss-Legendre nodes from numpy, the same points the nodal state is
+defined on) and evaluates initial conditions there.  Both the CUDA path and the
+CPU oracle receive the arrays it produces; neither imports the other.
+
+Nodal layout (the C-ABI layout): 1D ``[m][nx][n]``; 2D ``[m][ny][nx][n_y][n_x]``,
+values at the tensor Gauss points of each cell, ``n = k + 1``.
+
+Workloads (the paper's analytic initial data; there are no datasets):
+  * ``burgers_sine``      u0 = 0.5 + sin(pi x) on [0,2], periodic, bounds [-0.5, 1.5]
+  * ``euler_blast_tube``  1D Euler, [0,9], (rho,w,p) = (1,0,0.1(g-1)) for x<3 and
+                          (1e-3,0,1e-10(g-1)) for x>3, Dirichlet far states
+  * ``sedov``             2D Euler Sedov-type blast on [0,1.1]^2 (Example 4.7 geometry)
+  * ``riemann_quadrants`` seeded 2D four-quadrant Riemann problems on [0,1]^2
+  * ``random_euler`` / ``random_scalar``  seeded admissible states with
+                          zero-mean oscillations for operator and limiter parity
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+GAMMA = 1.4
+
+
+def gauss_nodes(k: int):
+    """(k+1) Gauss-Legendre nodes and weights on [-1, 1] (numpy)."""
+    return np.polynomial.legendre.leggauss(k + 1)
+
+
+def node_coords(dim, nx, ny, k, domain):
+    """Physical coordinates of every node, in the nodal layout without the component axis."""
+    xg, _ = gauss_nodes(k)
+    x0, x1 = domain[0], domain[1]
+    hx = (x1 - x0) / nx
+    cx = x0 + (np.arange(nx) + 0.5) * hx
+    if dim == 1:
+        return cx[:, None] + 0.5 * hx * xg[None, :]
+    y0, y1 = domain[2], domain[3]
+    hy = (y1 - y0) / ny
+    cy = y0 + (np.arange(ny) + 0.5) * hy
+    X = np.broadcast_to(cx[None, :, None, None] + 0.5 * hx * xg[None, None, None, :], (ny, nx, k + 1, k + 1))
+    Y = np.broadcast_to(cy[:, None, None, None] + 0.5 * hy * xg[None, None, :, None], (ny, nx, k + 1, k + 1))
+    return np.ascontiguousarray(X), np.ascontiguousarray(Y)
+
+
+def prim_to_cons(rho, w, p, gamma=GAMMA):
+    """(rho, velocity tuple, p) -> conservative components (rho, m..., E), eq. (Euler-2)."""
+    w = [np.asarray(wi, dtype=np.float64) * np.ones_like(rho) for wi in w]
+    kin = 0.5 * rho * sum(wi * wi for wi in w)
+    return np.stack([rho] + [rho * wi for wi in w] + [p / (gamma - 1.0) + kin])
+
+
+@dataclass
+class Workload:
+    """A problem description shared by the CUDA path and the oracle."""
+    name: str
+    dim: int
+    nx: int
+    ny: int
+    k: int
+    domain: tuple
+    flux: str
+    bc: tuple
+    state: np.ndarray
+    gamma: float = GAMMA
+    velocity: tuple = (1.0, 0.0)
+    bounds: tuple = (0.0, 1.0)
+    eps: float = 1e-13
+    bc_state: dict = field(default_factory=dict)
+    cfl: float = 0.1
+    t_end: float = 0.0
+    tableau: str = "heun3"
+
+    @property
+    def m(self):
+        return self.dim + 2 if self.flux == "euler" else 1
+
+    @property
+    def cells(self):
+        return self.nx * self.ny
+
+    @property
+    def dofs_per_cell(self):
+        return self.m * (self.k + 1) ** self.dim
+
+
+def burgers_sine(nx=200, k=2, cfl=0.1, t_end=0.3):
+    X = node_coords(1, nx, 1, k, (0.0, 2.0))
+    u = 0.5 + np.sin(np.pi * X)
+    return Workload("burgers_sine", 1, nx, 1, k, (0.0, 2.0), "burgers", ("periodic",) * 4,
+                    u[None].copy(), bounds=(-0.5, 1.5), cfl=cfl, t_end=t_end, tableau="heun3")
+
+
+def euler_blast_tube(nx=4096, k=2, cfl=0.178, t_end=6.0, gamma=GAMMA):
+    dom = (0.0, 9.0)
+    X = node_coords(1, nx, 1, k, dom)
+    left = X < 3.0
+    rho = np.where(left, 1.0, 1e-3)
+    p = np.where(left, (gamma - 1.0) * 0.1, (gamma - 1.0) * 1e-10)
+    U = prim_to_cons(rho, (0.0,), p, gamma)
+    sl = prim_to_cons(np.array(1.0), (0.0,), np.array((gamma - 1.0) * 0.1), gamma)
+    sr = prim_to_cons(np.array(1e-3), (0.0,), np.array((gamma - 1.0) * 1e-10), gamma)
+    return Workload("euler1d_blast_tube", 1, nx, 1, k, dom, "euler",
+                    ("dirichlet", "dirichlet", "outflow", "outflow"), np.ascontiguousarray(U),
+                    gamma=gamma, eps=1e-13, bc_state={0: sl.tolist(), 1: sr.tolist()}, cfl=cfl,
+                    t_end=t_end, tableau="heun3")
+
+
+def sedov(n=2048, k=3, cfl=0.103, t_end=1.0, gamma=GAMMA, p_ambient=1e-13):
+    dom = (0.0, 1.1, 0.0, 1.1)
+    X, Y = node_coords(2, n, n, k, dom)
+    dx = 1.1 / n
+    rho = np.ones_like(X)
+    E = np.full_like(X, p_ambient / (gamma - 1.0))
+    E[0, 0] = 0.244816 / (dx * dx)
+    zero = np.zeros_like(X)
+    U = np.stack([rho, zero, zero, E])
+    return Workload("sedov2d", 2, n, n, k, dom, "euler",
+                    ("reflect", "outflow", "reflect", "outflow"), np.ascontiguousarray(U),
+                    gamma=gamma, eps=1e-13, cfl=cfl, t_end=t_end,
+                    tableau="rk4" if k == 3 else "heun3")
+
+
+def riemann_states(seed):
+    """Four quadrant states (rho, wx, wy, p): rho~U[0.1,2], p~U[0.01,2], |w|<1 (disc)."""
+    rng = np.random.default_rng(seed)
+    st = []
+    for _ in range(4):
+        rho = rng.uniform(0.1, 2.0)
+        p = rng.uniform(0.01, 2.0)
+        r = math.sqrt(rng.uniform(0.0, 1.0)) * 0.999
+        a = rng.uniform(0.0, 2.0 * math.pi)
+        st.append((rho, r * math.cos(a), r * math.sin(a), p))
+    return st
+
+
+def riemann_quadrants(seed, n=1024, k=2, cfl=0.178, t_end=0.2, gamma=GAMMA):
+    dom = (0.0, 1.0, 0.0, 1.0)
+    X, Y = node_coords(2, n, n, k, dom)
+    st = riemann_states(seed)
+    q = (X >= 0.5).astype(int) + 2 * (Y >= 0.5).astype(int)  # 0 SW, 1 SE, 2 NW, 3 NE
+    rho = np.choose(q, [s[0] for s in st])
+    wx = np.choose(q, [s[1] for s in st])
+    wy = np.choose(q, [s[2] for s in st])
+    p = np.choose(q, [s[3] for s in st])
+    U = prim_to_cons(rho, (wx, wy), p, gamma)
+    return Workload(f"riemann2d_seed{seed}", 2, n, n, k, dom, "euler", ("outflow",) * 4,
+                    np.ascontiguousarray(U), gamma=gamma, eps=1e-13, cfl=cfl, t_end=t_end,
+                    tableau="rk4" if k == 3 else "heun3")
+
+
+def _zero_mean(rng, shape_cells, k, dim):
+    """Random nodal oscillation with zero cell average under the Gauss weights."""
+    _, w = gauss_nodes(k)
+    n = k + 1
+    r = rng.uniform(-1.0, 1.0, size=shape_cells + (n,) * dim)
+    if dim == 1:
+        mean = (r * w).sum(-1, keepdims=True) / 2.0
+    else:
+        mean = (r * w[None, :] * w[:, None]).sum((-1, -2), keepdims=True) / 4.0
+    return r - mean
+
+
+def random_euler(dim, nx, ny, k, seed, osc=0.6, gamma=GAMMA):
+    """Smooth admissible Euler field plus zero-mean nodal oscillations.
+
+    With osc near or above 1 some nodes leave the admissible set while every
+    cell average stays admissible, which exercises both limiter branches."""
+    rng = np.random.default_rng(seed)
+    if dim == 1:
+        X = node_coords(1, nx, 1, k, (0.0, 1.0))
+        cells = (nx,)
+        ph = rng.uniform(0, 2 * np.pi, 4)
+        rho = 1.0 + 0.5 * np.sin(2 * np.pi * X + ph[0])
+        w = (0.5 * np.sin(2 * np.pi * X + ph[1]),)
+        p = 1.0 + 0.5 * np.sin(2 * np.pi * X + ph[2])
+    else:
+        X, Y = node_coords(2, nx, ny, k, (0.0, 1.0, 0.0, 1.0))
+        cells = (ny, nx)
+        ph = rng.uniform(0, 2 * np.pi, 6)
+        rho = 1.0 + 0.5 * np.sin(2 * np.pi * X + ph[0]) * np.cos(2 * np.pi * Y + ph[1])
+        w = (0.5 * np.sin(2 * np.pi * Y + ph[2]), 0.5 * np.cos(2 * np.pi * X + ph[3]))
+        p = 1.0 + 0.5 * np.sin(2 * np.pi * (X + Y) + ph[4])
+    U = prim_to_cons(rho, w, p, gamma)
+    m = U.shape[0]
+    for c in range(m):
+        amp = osc * (np.abs(U[c]).mean() if c in (0, m - 1) else 0.3)
+        U[c] = U[c] + amp * _zero_mean(rng, cells, k, dim)
+    return np.ascontiguousarray(U)
+
+
+def random_scalar(dim, nx, ny, k, seed, lo=-0.5, hi=1.5, osc=0.6):
+    """Smooth field inside (lo, hi) plus zero-mean oscillations that may cross the bounds."""
+    rng = np.random.default_rng(seed)
+    mid, half = 0.5 * (lo + hi), 0.5 * (hi - lo)
+    if dim == 1:
+        X = node_coords(1, nx, 1, k, (0.0, 1.0))
+        u = mid + 0.8 * half * np.sin(2 * np.pi * X + rng.uniform(0, 6.3))
+        cells = (nx,)
+    else:
+        X, Y = node_coords(2, nx, ny, k, (0.0, 1.0, 0.0, 1.0))
+        u = mid + 0.8 * half * np.sin(2 * np.pi * X + rng.uniform(0, 6.3)) * np.cos(2 * np.pi * Y)
+        cells = (ny, nx)
+    u = u + osc * half * _zero_mean(rng, cells, k, dim)
+    return np.ascontiguousarray(u[None])
