@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Throughput of the cRKDG hot path on one GB300 (or N independent replicas).
+
+Metric: cell-DOF updates per second per RK stage = cells * m(k+1)^d * s / time,
+counting every accepted time step (s stages + limiters + the final stage + the
+dt control).  One bench step = one cRKDG time step of the workload.
+
+Default workload (N=1): 1D Euler (gamma 1.4) blast tube on [0,9], 4096 cells,
+P^2, Heun-3 cRKDG with the positivity limiter, FP64, eps 1e-13, CFL 0.178.
+
+Arms:
+  --impl gb300      (default) the CUDA library through its C ABI.
+  --impl reference  the CPU oracle on the host cores (rank 0 only).
+Under torchrun each rank advances its own replica (weak scaling, no data-path
+collective); the reported time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# FP64 peak of the GB300 derived from the unit count and clock: 152 SMs x 4 FP64
+# flop per clock (two DFMA per clock per SM, the 1.25 TFLOP/s class rate) x 2070 MHz.
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+
+WORKLOADS = {
+    "euler1d_blast_tube_4096_p2": dict(kind="euler1d", nx=4096, k=2),
+    "burgers_sine_200_p2": dict(kind="burgers", nx=200, k=2),
+    "sedov_2048_q3": dict(kind="sedov", nx=2048, k=3),
+    "riemann_1024_q2": dict(kind="riemann", nx=1024, k=2),
+}
+DEFAULT = "euler1d_blast_tube_4096_p2"
+
+
+def make_workload(name, seed=0):
+    from paper_2412_16002_gb300 import inputs
+
+    w = WORKLOADS[name]
+    if w["kind"] == "euler1d":
+        return inputs.euler_blast_tube(w["nx"], w["k"])
+    if w["kind"] == "burgers":
+        return inputs.burgers_sine(w["nx"], w["k"])
+    if w["kind"] == "sedov":
+        return inputs.sedov(w["nx"], w["k"])
+    return inputs.riemann_quadrants(seed, w["nx"], w["k"])
+
+
+TAB_S = {"midpoint2": 2, "heun3": 3, "rk4": 4}
+TAB_NSLOT = {"midpoint2": 1, "heun3": 2, "rk4": 4}
+TAB_NA = {"midpoint2": 1, "heun3": 2, "rk4": 3}  # nonzero a_ij
+
+
+def flux_flops(flux, dim):
+    """FP64 operations of one flux evaluation f(u).e_dir (divisions and roots count 1)."""
+    if flux == "euler":
+        return 10 if dim == 1 else 14
+    return 1 if flux == "advection" else 2
+
+
+def algorithmic_flops(wl):
+    """FP64 flops per cell per time step of the method as written (Scheme 1L), split into
+    the inner-stage kernel and the final-stage kernel.  Counts: flux at every node and
+    trace point; volume term 2n per node per component per direction; trace interpolation
+    2n per trace point per component; lift 5 per node per component per direction; stage
+    combination 2 per node per component per nonzero a_ij; limiter: average 2 per node per
+    component, S_K interpolation 2n per point per component, rho*e 6 per point and 10 per
+    theta; LF flux per face point per stage: 2 speeds (10), 2 fluxes, 8 per component;
+    u* accumulation 2 per node per component per nonzero b_i; a0 10 per S_K point."""
+    d, n, m = wl.dim, wl.k + 1, wl.m
+    nn = n ** d
+    ntr = 2 * d * (n if d == 2 else 1)
+    L = (n + 3) // 2
+    nsk = 2 * n * L if d == 2 else L
+    s, nslot, na = TAB_S[wl.tableau], TAB_NSLOT[wl.tableau], TAB_NA[wl.tableau]
+    ff = flux_flops(wl.flux, d)
+    g = nn * (ff * (2 if d == 2 else 1) * (1 if d == 2 else 1) + 2 * n * m * d + 5 * m * d) + ntr * (2 * n * m + ff)
+    lim = 2 * nn * m + nsk * (2 * n * m) + (nsk * 6 + 20 if wl.flux == "euler" else 10)
+    inner = s * g + na * 2 * nn * m + (s - 1) * lim + nslot * 2 * nn * m
+    lf = ntr * nslot * (20 + 2 * ff + 8 * m)
+    final = lf + nn * m * 5 * d + lim + nsk * 10
+    return inner, final
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[2:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def read_traffic(kernel, workload):
+    """DRAM bytes per launch recorded by the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.startswith("dram_bytes_per_launch:"):
+            try:
+                return float(line.split(":", 1)[1].split()[0])
+            except ValueError:
+                return None
+    return None
+
+
+def oracle_rate(wl, budget_s=10.0, max_steps=10**6):
+    """Oracle (plain C, one host thread) on the same workload: DOF-stage updates / s."""
+    from oracle import HEUN3, MIDPOINT2, RK4, Oracle
+
+    tabs = {"midpoint2": MIDPOINT2, "heun3": HEUN3, "rk4": RK4}
+    o = Oracle(wl.dim, wl.nx, wl.ny, wl.k, wl.domain, wl.flux, gamma=wl.gamma, velocity=wl.velocity,
+               bounds=wl.bounds, eps=wl.eps, bc=wl.bc, bc_state=wl.bc_state)
+    o.set_state(wl.state)
+    t = 0.0
+    steps = 0
+    t0 = time.perf_counter()
+    while steps < max_steps and time.perf_counter() - t0 < budget_s:
+        dt = o.max_dt(wl.cfl)
+        rc, info = o.step(dt, tabs[wl.tableau], t)
+        if rc != 0:
+            break
+        t += info["dt_taken"]
+        steps += 1
+    el = time.perf_counter() - t0
+    units = wl.cells * wl.dofs_per_cell * TAB_S[wl.tableau] * steps
+    return units / el, steps, el
+
+
+def run_reference(args, wl, name):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from oracle import HEUN3, MIDPOINT2, RK4, Oracle
+
+    tabs = {"midpoint2": MIDPOINT2, "heun3": HEUN3, "rk4": RK4}
+    o = Oracle(wl.dim, wl.nx, wl.ny, wl.k, wl.domain, wl.flux, gamma=wl.gamma, velocity=wl.velocity,
+               bounds=wl.bounds, eps=wl.eps, bc=wl.bc, bc_state=wl.bc_state)
+    o.set_state(wl.state)
+    t = 0.0
+    for _ in range(args.warmup):
+        rc, info = o.step(o.max_dt(wl.cfl), tabs[wl.tableau], t)
+        t += info["dt_taken"]
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rc, info = o.step(o.max_dt(wl.cfl), tabs[wl.tableau], t)
+        t += info["dt_taken"]
+    el = time.perf_counter() - t0
+    units = wl.cells * wl.dofs_per_cell * TAB_S[wl.tableau] * args.steps
+    v = units / el
+    line = {
+        "impl": "reference", "metric": "cell-DOF updates/s per RK stage", "value": v,
+        "unit": "cell-DOF-stage/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "cells": wl.cells, "k": wl.k, "m": wl.m, "tableau": wl.tableau,
+                   "cfl": wl.cfl},
+        "cpu_baseline": {"value": v, "unit": "cell-DOF-stage/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full time steps of {name} after {args.warmup} warm-up steps"},
+        "e2e": {"value": v, "unit": "cell-DOF-stage/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_gb300(args, wl, name):
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        from paper_2412_16002_gb300 import build
+
+        build()
+    if world > 1:
+        dist.barrier()
+    from paper_2412_16002_gb300.solver import Solver
+
+    stream = torch.cuda.current_stream()
+    g = Solver.from_workload(wl, stream=stream)
+    u0 = torch.from_numpy(wl.state).to(dev)
+    g.set_state(u0)
+    t = 0.0
+    for _ in range(args.warmup):
+        info = g.step(g.max_dt(wl.cfl), wl.tableau)
+        t += info["dt_taken"]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    g.set_profiling(True)
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    restarts = 0
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        info = g.step(g.max_dt(wl.cfl), wl.tableau)
+        ev[i][1].record(stream)
+        restarts += info["restarts"]
+        t += info["dt_taken"]
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    kt, kn = g.kernel_times()
+    g.set_profiling(False)
+    tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ms_max = float(tt.item())
+    units = wl.cells * wl.dofs_per_cell * TAB_S[wl.tableau] * args.steps * world
+    value = units / (ms_max / 1e3)
+
+    # end to end through the C ABI with host buffers: H2D of the state, one step, D2H
+    host_in = torch.from_numpy(g.get_state().reshape(-1).copy()).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    import ctypes as C
+
+    lib, h = g.lib, g.h
+    nbytes = host_in.numel() * 8
+    e2e_steps = max(3, args.steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g._chk(lib.crkdg_set_state(h, C.c_void_p(host_in.data_ptr()), host_in.numel(), 0))
+        g.step(g.max_dt(wl.cfl), wl.tableau)
+        g._chk(lib.crkdg_get_state(h, C.c_void_p(host_out.data_ptr()), host_out.numel(), 0))
+        host_in.copy_(host_out)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = wl.cells * wl.dofs_per_cell * TAB_S[wl.tableau] * e2e_steps * world / float(e2e_t.item())
+
+    if rank == 0:
+        inner_f, final_f = algorithmic_flops(wl)
+        avg_inner = kt["inner"] / max(kn["inner"], 1)
+        avg_final = kt["final"] / max(kn["final"], 1)
+        dom, avg_ms, fl = ("k_inner", avg_inner, inner_f) if avg_inner >= avg_final else ("k_final", avg_final, final_f)
+        achieved = fl * wl.cells / (avg_ms / 1e3) / 1e12
+        line = {
+            "metric": "cell-DOF updates/s per RK stage",
+            "value": value,
+            "unit": "cell-DOF-stage/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": name, "cells": wl.cells, "k": wl.k, "m": wl.m, "dofs_per_cell": wl.dofs_per_cell,
+                       "tableau": wl.tableau, "stages": TAB_S[wl.tableau], "cfl": wl.cfl,
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas{world}",
+                       "restarts_in_timed_steps": restarts, "t_after": t},
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "traffic": read_traffic(dom, name),
+                         "peak_source": "FP64 derived from unit count and clock (152 SMs x 4 flop/clk x 2070 MHz)",
+                         "avg_launch_ms": {"k_inner": avg_inner, "k_final": avg_final},
+                         "flops_per_cell": {"k_inner": inner_f, "k_final": final_f}},
+            "e2e": {"value": e2e_value, "unit": "cell-DOF-stage/s", "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes},
+            "gpu_launches": int(kn["inner"] + kn["final"]),
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            v, n, el = oracle_rate(wl, budget_s=args.cpu_seconds)
+            line["cpu_baseline"] = {"value": v, "unit": "cell-DOF-stage/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"{n} time steps of {name} from the initial state ({el:.1f} s, one thread)"}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+    wl = make_workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, wl, args.workload)
+    else:
+        run_gb300(args, wl, args.workload)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * crkdg.h -- C ABI of the GB300 (sm_103a) bound-preserving compact-stencil
+ * Runge--Kutta discontinuous Galerkin library (cRKDG; Liu, Sun and Zhang,
+ * "A bound-preserving Runge--Kutta discontinuous Galerkin method with compact
+ * stencils for hyperbolic conservation laws", arXiv 2412.16002).
+ *
+ * What one step computes (Scheme 1L, Appendix B.2, eq. rkdg-lim):
+ *     u^(1) = u~^n
+ *     u^(i) = u~^n + dt sum_{j<i} a_ij G(u~^(j)),  u~^(i) = L(u^(i)),  i = 2..s
+ *     u^{n+1} = u~^n + dt sum_i b_i F(u~^(i)),    u~^{n+1} = L(u^{n+1})
+ * with G = -div^loc f (interior traces on every edge, Sec. 2.1), F = -div^DG f
+ * with the Lax--Friedrichs flux (eq. dxDG), and L the Zhang--Shu scaling limiter
+ * (Prop. 2.4 for scalar laws, eq. Euler-limiter1/2 for the Euler equations).
+ * If any stage's cell averages leave B (B^eps for Euler) the step is redone
+ * from u~^n with dt halved (Sec. 4.1, Algorithm).
+ *
+ * Discretisation: uniform Cartesian mesh (1D or 2D), tensor-product Q^k basis
+ * (k = 1..3), nodal at the (k+1)^d tensor Gauss points; (k+1)-point Gauss on
+ * every edge (Prop. 2.1); the limiter point set S_K is the union of the
+ * Gauss x Gauss-Lobatto and Gauss-Lobatto x Gauss points (Prop. 2.2, Fig. 1)
+ * with L = ceil((k+3)/2) Gauss-Lobatto points.
+ *
+ * Conventions for every entry point:
+ *   - State layout: FP64 nodal values, component-major:
+ *       1D  [m][nx][n]            2D  [m][ny][nx][n_y][n_x],  n = k+1,
+ *     count = m * nx * ny * n^dim doubles.  m = 1 (advection, Burgers),
+ *     3 (1D Euler: rho, m, E), 4 (2D Euler: rho, m_x, m_y, E).
+ *   - Pointers are host pointers unless an argument says "device"; an
+ *     on_device flag selects which for state transfers.  The caller keeps
+ *     ownership of everything it passes; the library copies and owns its own
+ *     device buffers, which live until crkdg_destroy.
+ *   - Work is issued on options.cuda_stream (NULL = legacy default stream);
+ *     calls that return host data synchronise that stream.
+ *   - Every call returns a crkdg_status; no C++ exception crosses the ABI.
+ *     crkdg_last_error(h) describes the last failure on that handle.  A handle
+ *     is not thread-safe: calls on one handle must not overlap.
+ */
+#ifndef CRKDG_H
+#define CRKDG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct crkdg_ctx *crkdg_t;
+
+typedef enum {
+    CRKDG_OK = 0,
+    CRKDG_E_ARG = 1,         /* invalid argument (sizes, kinds, tableau, NULL) */
+    CRKDG_E_CUDA = 2,        /* a CUDA runtime call failed; see crkdg_last_error */
+    CRKDG_E_OOM = 3,         /* device allocation failed */
+    CRKDG_E_BOUNDS = 4,      /* averages left B after max_halvings; state unchanged */
+    CRKDG_E_TIMEOUT = 5,     /* a bounded device-side wait expired */
+    CRKDG_E_UNSUPPORTED = 6  /* valid but not built (e.g. k > 3) */
+} crkdg_status;
+
+enum { CRKDG_BC_PERIODIC = 0, CRKDG_BC_OUTFLOW = 1, CRKDG_BC_REFLECT = 2, CRKDG_BC_DIRICHLET = 3 };
+enum { CRKDG_FLUX_ADVECTION = 0, CRKDG_FLUX_BURGERS = 1, CRKDG_FLUX_EULER = 2 };
+enum { CRKDG_PREC_FP64 = 0, CRKDG_PREC_MIXED = 1 };
+enum { CRKDG_IND_OFF = 0, CRKDG_IND_TVB = 1, CRKDG_IND_MLP = 2 };
+
+/* Mesh: the domain [x0,x1] (x [y0,y1] in 2D) cut into nx (x ny) equal cells.
+ * bc[s] for the sides s = 0 left, 1 right, 2 bottom, 3 top; a periodic side
+ * must be paired with a periodic opposite side.  bc_state[s] holds the
+ * conservative exterior state of a Dirichlet side.  Boundary data enter only
+ * the final stage (compactness, Sec. 1 and the Compactness remark of Sec. 3.2). */
+typedef struct {
+    int dim;
+    int nx, ny;
+    double x0, x1, y0, y1;
+    int bc[4];
+    double bc_state[4][4];
+} crkdg_mesh;
+
+/* Flux f of eq. (claws): kind ADVECTION f = a u (velocity a), BURGERS
+ * f = u^2/2 in every direction, EULER eq. (Euler), (Euler-2) with gamma. */
+typedef struct {
+    int kind;
+    double gamma;
+    double velocity[2];
+} crkdg_flux;
+
+/* Invariant region: scalar B = [lo, hi] (eq. scalar-bound); Euler B^eps with
+ * rho >= eps and rho e >= eps (Sec. 2.2.2, eq. Euler-limiter2). */
+typedef struct {
+    double lo, hi;
+    double eps;
+} crkdg_bounds;
+
+/* Butcher tableau (eq. butcher): A is s*s row-major, strictly lower triangular,
+ * b has s entries, all >= 0 (Sec. 3.3).  s <= 4.  Host pointers. */
+typedef struct {
+    int s;
+    const double *A;
+    const double *b;
+} crkdg_tableau;
+
+typedef struct {
+    int precision;      /* CRKDG_PREC_FP64 (default) or CRKDG_PREC_MIXED */
+    int max_halvings;   /* restart cap of the Sec. 4.1 loop (default 20) */
+    int indicator;      /* CRKDG_IND_* troubled-cell indicator (default off) */
+    double tvb_M;       /* TVB constant of the plain indicator (default 10) */
+    void *cuda_stream;  /* cudaStream_t to issue work on (NULL: default stream) */
+} crkdg_options;
+
+typedef struct {
+    double dt_taken;          /* dt of the accepted attempt */
+    int restarts;             /* halvings before acceptance */
+    long long cells_limited;  /* cells with theta < 1 over all stages of the accepted attempt */
+    double theta_min;         /* smallest theta of the accepted attempt */
+    long long troubled;       /* cells flagged by the indicator (0 if off) */
+    double mass_drift;        /* reserved (0) */
+} crkdg_step_info;
+
+/* Fill *opt with the defaults. */
+void crkdg_options_default(crkdg_options *opt);
+
+/* Create a solver.  k: polynomial degree 1..3; m must match the flux kind and
+ * dim (see the state layout above).  opt may be NULL (defaults).  On success
+ * *out receives a handle.  Errors: CRKDG_E_ARG, CRKDG_E_UNSUPPORTED,
+ * CRKDG_E_OOM, CRKDG_E_CUDA (no handle is returned). */
+crkdg_status crkdg_create(const crkdg_mesh *mesh, int k, int m, const crkdg_flux *flux,
+                          const crkdg_bounds *bounds, const crkdg_options *opt, crkdg_t *out);
+
+/* Release every device buffer of h.  h may be NULL. */
+crkdg_status crkdg_destroy(crkdg_t h);
+
+/* Copy count doubles of nodal state in (host or device pointer) and apply the
+ * scaling limiter once, so that u^n lies in B on every S_K (the hypothesis of
+ * Theorem 3.5).  count must equal the state size. */
+crkdg_status crkdg_set_state(crkdg_t h, const double *nodal, size_t count, int on_device);
+
+/* Copy the current nodal state out (host or device pointer). */
+crkdg_status crkdg_get_state(crkdg_t h, double *nodal, size_t count, int on_device);
+
+/* Trial step of eq. (numerical_experiment:CFL): *dt = cfl * dx / a0, with a0
+ * the largest spectral radius |w.nu| + c (|u| for Burgers, |a.nu| for
+ * advection) over all S_K points of the current state. */
+crkdg_status crkdg_max_dt(crkdg_t h, double cfl, double *dt);
+
+/* One limited cRKDG step of size dt (restarting with dt/2 while any stage's
+ * averages leave B, at most max_halvings times).  info may be NULL.
+ * CRKDG_E_BOUNDS leaves the state at u^n. */
+crkdg_status crkdg_step(crkdg_t h, double dt, const crkdg_tableau *tab, crkdg_step_info *info);
+
+/* Run up to nsteps steps, each of size min(cfl*dx/a0, t_end - *t), advancing
+ * *t; stops early when *t reaches t_end.  *steps_done (nullable) receives the
+ * number of accepted steps and *restarts (nullable) the total halvings. */
+crkdg_status crkdg_advance(crkdg_t h, int nsteps, double cfl, double t_end,
+                           const crkdg_tableau *tab, double *t, int *steps_done, int *restarts);
+
+/* Operator evaluation on device arrays in the state layout, for verification:
+ * op 0: out = G(in) (Sec. 2.1), op 1: out = F(in) (eq. dxDG; boundary data at
+ * the mesh's BCs), op 2: out = L(in) (the scaling limiter, no admissibility
+ * test).  in and out are device pointers of state size; they may not alias. */
+enum { CRKDG_OP_G = 0, CRKDG_OP_F = 1, CRKDG_OP_LIMIT = 2 };
+crkdg_status crkdg_apply_operator(crkdg_t h, int op, const double *in_dev, double *out_dev);
+
+/* Cell averages of the current state, [ny][nx][m] doubles (host or device). */
+crkdg_status crkdg_cell_averages(crkdg_t h, double *avg, int on_device);
+
+/* Smallest bound margins over every S_K point of the current state, evaluated
+ * by the limiter's own interpolation: scalar {min(u-lo), min(hi-u)}, Euler
+ * {min(rho-eps), min(rho e - eps)}.  Both are >= 0 after every step. */
+crkdg_status crkdg_bound_margins(crkdg_t h, double margins[2]);
+
+/* sum_K |K| ubar_K of component comp, summed in a fixed order (deterministic). */
+crkdg_status crkdg_total_mass(crkdg_t h, int comp, double *mass);
+
+/* Kernel timing for measurement.  While on, crkdg_step brackets its
+ * inner-stage and final-stage launches with CUDA events on the library's
+ * stream and accumulates their durations; crkdg_kernel_times returns the
+ * milliseconds {inner, final} and the launch counts since profiling was last
+ * switched on.  Off by default; switching on resets the totals. */
+crkdg_status crkdg_set_profiling(crkdg_t h, int on);
+crkdg_status crkdg_kernel_times(crkdg_t h, double ms[2], long long launches[2]);
+
+/* Number of doubles of the state. */
+size_t crkdg_state_size(crkdg_t h);
+
+/* Human-readable description of the last error on h (static string if h is NULL). */
+const char *crkdg_last_error(crkdg_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CRKDG_H */

@@ -1,0 +1,609 @@
+// crkdg_api.cu -- the C ABI of include/crkdg.h: argument checks, device
+// buffers, the nodal tables, and the Sec. 4.1 restart loop around the
+// inner-stage and final-stage kernels.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "../../include/crkdg.h"
+#include "dg_types.h"
+
+using namespace crkdg;
+
+namespace {
+
+// Device-side scalars written by the kernels of one step.
+struct DevScal {
+    int flag;
+    int pad;
+    unsigned long long nlim;
+    unsigned long long thmin;
+    unsigned long long a0;
+    unsigned long long ord[2];
+};
+
+uint64_t bits_of(double x) {
+    uint64_t u;
+    memcpy(&u, &x, 8);
+    return u;
+}
+double from_bits(uint64_t u) {
+    double x;
+    memcpy(&x, &u, 8);
+    return x;
+}
+double from_ordbits(uint64_t u) {
+    return from_bits((u >> 63) ? (u & 0x7fffffffffffffffull) : ~u);
+}
+
+// ---------------------------------------------------------------- nodal tables
+// Closed-form Gauss--Legendre and Gauss--Lobatto rules (n <= 4, L <= 3) and
+// the Lagrange basis on the Gauss nodes.
+void gauss_rule(int n, double *x, double *w) {
+    if (n == 2) {
+        double a = 1.0 / sqrt(3.0);
+        x[0] = -a; x[1] = a;
+        w[0] = w[1] = 1.0;
+    } else if (n == 3) {
+        double a = sqrt(0.6);
+        x[0] = -a; x[1] = 0.0; x[2] = a;
+        w[0] = w[2] = 5.0 / 9.0;
+        w[1] = 8.0 / 9.0;
+    } else {
+        double r = 2.0 / 7.0 * sqrt(6.0 / 5.0);
+        double a = sqrt(3.0 / 7.0 - r), b = sqrt(3.0 / 7.0 + r);
+        double wa = (18.0 + sqrt(30.0)) / 36.0, wb = (18.0 - sqrt(30.0)) / 36.0;
+        x[0] = -b; x[1] = -a; x[2] = a; x[3] = b;
+        w[0] = wb; w[1] = wa; w[2] = wa; w[3] = wb;
+    }
+}
+
+void lobatto_rule(int L, double *x, double *w) {
+    if (L == 2) {
+        x[0] = -1.0; x[1] = 1.0;
+        w[0] = w[1] = 1.0;
+    } else {
+        x[0] = -1.0; x[1] = 0.0; x[2] = 1.0;
+        w[0] = w[2] = 1.0 / 3.0;
+        w[1] = 4.0 / 3.0;
+    }
+}
+
+double lagrange(int n, const double *x, int a, double t) {
+    double v = 1.0;
+    for (int b = 0; b < n; ++b)
+        if (b != a) v *= (t - x[b]) / (x[a] - x[b]);
+    return v;
+}
+
+double dlagrange(int n, const double *x, int a, double t) {
+    double s = 0.0;
+    for (int c = 0; c < n; ++c) {
+        if (c == a) continue;
+        double v = 1.0 / (x[a] - x[c]);
+        for (int b = 0; b < n; ++b)
+            if (b != a && b != c) v *= (t - x[b]) / (x[a] - x[b]);
+        s += v;
+    }
+    return s;
+}
+
+void build_tables(NodalTables *tab) {
+    for (int n = 2; n <= 4; ++n) {
+        NodalTables &T = tab[n - 2];
+        memset(&T, 0, sizeof(T));
+        int L = nlob(n);
+        gauss_rule(n, T.xg, T.wg);
+        lobatto_rule(L, T.xl, T.wl);
+        for (int a = 0; a < n; ++a) {
+            for (int q = 0; q < n; ++q) T.Dhat[a][q] = T.wg[q] * dlagrange(n, T.xg, a, T.xg[q]) / T.wg[a];
+            T.lm[a] = lagrange(n, T.xg, a, -1.0);
+            T.lp[a] = lagrange(n, T.xg, a, 1.0);
+            T.liftm[a] = T.lm[a] / T.wg[a];
+            T.liftp[a] = T.lp[a] / T.wg[a];
+            for (int al = 0; al < L; ++al) T.Igl[al][a] = lagrange(n, T.xg, a, T.xl[al]);
+            T.w1[a] = 0.5 * T.wg[a];
+        }
+        for (int b = 0; b < n; ++b)
+            for (int a = 0; a < n; ++a) T.w2[b * n + a] = 0.25 * T.wg[a] * T.wg[b];
+    }
+}
+
+}  // namespace
+
+struct crkdg_ctx {
+    crkdg_mesh mesh;
+    crkdg_flux flux;
+    crkdg_bounds bounds;
+    crkdg_options opt;
+    int k = 0, n = 0, m = 0, dim = 0, phys = 0;
+    int ncell = 0, nn = 0, ntr = 0;
+    size_t nstate = 0;
+    cudaStream_t st = nullptr;
+    double *u = nullptr, *unew = nullptr, *ustar = nullptr, *tr = nullptr, *aux = nullptr;
+    int tr_slots = 0;
+    DevScal *scal = nullptr;
+    DevScal *hs = nullptr;      // pinned readback
+    DevScal *hinit = nullptr;   // pinned initial values
+    bool a0_valid = false;
+    double a0 = 0.0;
+    bool prof = false;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    double prof_ms[2] = {0.0, 0.0};
+    long long prof_n[2] = {0, 0};
+    std::string err;
+};
+
+namespace {
+
+crkdg_status fail(crkdg_t h, crkdg_status s, const std::string &msg) {
+    if (h) h->err = msg;
+    return s;
+}
+
+#define CK(h, call)                                                                        \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(h, e_ == cudaErrorMemoryAllocation ? CRKDG_E_OOM : CRKDG_E_CUDA,   \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));               \
+    } while (0)
+
+Params base_params(const crkdg_ctx *h) {
+    Params P;
+    memset(&P, 0, sizeof(P));
+    P.nx = h->mesh.nx;
+    P.ny = h->dim == 2 ? h->mesh.ny : 1;
+    P.ncell = h->ncell;
+    P.rhx = 2.0 * h->mesh.nx / (h->mesh.x1 - h->mesh.x0);
+    P.rhy = h->dim == 2 ? 2.0 * h->mesh.ny / (h->mesh.y1 - h->mesh.y0) : 0.0;
+    P.gamma = h->flux.gamma;
+    P.velx = h->flux.velocity[0];
+    P.vely = h->flux.velocity[1];
+    P.lo = h->bounds.lo;
+    P.hi = h->bounds.hi;
+    P.eps = h->bounds.eps;
+    for (int s = 0; s < 4; ++s) {
+        P.bc[s] = (h->dim == 1 && s >= 2) ? BC_OUTFLOW : h->mesh.bc[s];
+        for (int c = 0; c < MAXM; ++c) P.bcs[s][c] = h->mesh.bc_state[s][c];
+    }
+    for (int i = 0; i < MAXS; ++i) P.slot[i] = -1;
+    return P;
+}
+
+Bufs base_bufs(const crkdg_ctx *h) {
+    Bufs B;
+    B.un = h->u;
+    B.ustar = h->ustar;
+    B.unew = h->unew;
+    B.tr = h->tr;
+    B.flag = &h->scal->flag;
+    B.nlim = &h->scal->nlim;
+    B.thmin = &h->scal->thmin;
+    B.a0 = &h->scal->a0;
+    B.aux = h->aux;
+    B.ord = h->scal->ord;
+    return B;
+}
+
+cudaError_t launch(crkdg_ctx *h, int kernel, const Params &P, const Bufs &B) {
+    int ncb = cells_per_block(h->dim, h->n);
+    int nblocks = (h->ncell + ncb - 1) / ncb;
+    if (h->dim == 1) return crkdg_launch_1d(kernel, h->n, h->phys, nblocks, h->st, P, B);
+    return crkdg_launch_2d(kernel, h->n, h->phys, nblocks, h->st, P, B);
+}
+
+crkdg_status reset_scalars(crkdg_ctx *h) {
+    CK(h, cudaMemcpyAsync(h->scal, h->hinit, sizeof(DevScal), cudaMemcpyHostToDevice, h->st));
+    return CRKDG_OK;
+}
+
+crkdg_status read_scalars(crkdg_ctx *h) {
+    CK(h, cudaMemcpyAsync(h->hs, h->scal, sizeof(DevScal), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    return CRKDG_OK;
+}
+
+crkdg_status ensure_traces(crkdg_ctx *h, int slots) {
+    if (slots <= h->tr_slots) return CRKDG_OK;
+    if (h->tr) cudaFree(h->tr);
+    h->tr = nullptr;
+    h->tr_slots = 0;
+    size_t bytes = (size_t)slots * h->m * h->ncell * h->ntr * sizeof(double);
+    CK(h, cudaMalloc(&h->tr, bytes));
+    h->tr_slots = slots;
+    return CRKDG_OK;
+}
+
+crkdg_status check_tableau(crkdg_t h, const crkdg_tableau *tab) {
+    if (!tab || !tab->A || !tab->b) return fail(h, CRKDG_E_ARG, "tableau: NULL");
+    if (tab->s < 1 || tab->s > MAXS) return fail(h, CRKDG_E_ARG, "tableau: need 1 <= s <= 4");
+    for (int i = 0; i < tab->s; ++i) {
+        if (!isfinite(tab->b[i]) || tab->b[i] < 0.0) return fail(h, CRKDG_E_ARG, "tableau: b must be finite and >= 0");
+        for (int j = 0; j < tab->s; ++j) {
+            double a = tab->A[i * tab->s + j];
+            if (!isfinite(a)) return fail(h, CRKDG_E_ARG, "tableau: A not finite");
+            if (j >= i && a != 0.0) return fail(h, CRKDG_E_ARG, "tableau: A must be strictly lower triangular");
+        }
+    }
+    return CRKDG_OK;
+}
+
+crkdg_status compute_a0(crkdg_ctx *h) {
+    crkdg_status s = reset_scalars(h);
+    if (s) return s;
+    Params P = base_params(h);
+    Bufs B = base_bufs(h);
+    CK(h, launch(h, K_A0, P, B));
+    s = read_scalars(h);
+    if (s) return s;
+    h->a0 = from_bits(h->hs->a0);
+    h->a0_valid = true;
+    return CRKDG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void crkdg_options_default(crkdg_options *opt) {
+    if (!opt) return;
+    opt->precision = CRKDG_PREC_FP64;
+    opt->max_halvings = 20;
+    opt->indicator = CRKDG_IND_OFF;
+    opt->tvb_M = 10.0;
+    opt->cuda_stream = nullptr;
+}
+
+crkdg_status crkdg_create(const crkdg_mesh *mesh, int k, int m, const crkdg_flux *flux,
+                          const crkdg_bounds *bounds, const crkdg_options *opt, crkdg_t *out) {
+    if (!out) return CRKDG_E_ARG;
+    *out = nullptr;
+    if (!mesh || !flux || !bounds) return CRKDG_E_ARG;
+    if (mesh->dim != 1 && mesh->dim != 2) return CRKDG_E_ARG;
+    if (k < 1) return CRKDG_E_ARG;
+    if (k > 3) return CRKDG_E_UNSUPPORTED;
+    if (flux->kind < CRKDG_FLUX_ADVECTION || flux->kind > CRKDG_FLUX_EULER) return CRKDG_E_ARG;
+    if (m != ncomp(flux->kind, mesh->dim)) return CRKDG_E_ARG;
+    int ny = mesh->dim == 2 ? mesh->ny : 1;
+    if (mesh->nx < 1 || ny < 1) return CRKDG_E_ARG;
+    if ((double)mesh->nx * ny * m * 64.0 > 9.0e15) return CRKDG_E_ARG;
+    if ((double)mesh->nx * ny > 2.0e9) return CRKDG_E_ARG;
+    if (!(mesh->x1 > mesh->x0) || (mesh->dim == 2 && !(mesh->y1 > mesh->y0))) return CRKDG_E_ARG;
+    int nsides = 2 * mesh->dim;
+    for (int s = 0; s < nsides; ++s)
+        if (mesh->bc[s] < CRKDG_BC_PERIODIC || mesh->bc[s] > CRKDG_BC_DIRICHLET) return CRKDG_E_ARG;
+    for (int d = 0; d < mesh->dim; ++d)
+        if ((mesh->bc[2 * d] == CRKDG_BC_PERIODIC) != (mesh->bc[2 * d + 1] == CRKDG_BC_PERIODIC)) return CRKDG_E_ARG;
+    if (flux->kind == CRKDG_FLUX_EULER && !(flux->gamma > 1.0 && bounds->eps > 0.0)) return CRKDG_E_ARG;
+    if (flux->kind != CRKDG_FLUX_EULER && !(bounds->lo <= bounds->hi)) return CRKDG_E_ARG;
+    crkdg_options o;
+    crkdg_options_default(&o);
+    if (opt) o = *opt;
+    if (o.max_halvings < 0 || o.max_halvings > 60) return CRKDG_E_ARG;
+    if (o.precision != CRKDG_PREC_FP64) return CRKDG_E_UNSUPPORTED;
+
+    crkdg_ctx *h = new (std::nothrow) crkdg_ctx();
+    if (!h) return CRKDG_E_OOM;
+    try {
+        h->mesh = *mesh;
+        h->mesh.ny = ny;
+        h->flux = *flux;
+        h->bounds = *bounds;
+        h->opt = o;
+        h->k = k;
+        h->n = k + 1;
+        h->m = m;
+        h->dim = mesh->dim;
+        h->phys = flux->kind;
+        h->ncell = mesh->nx * ny;
+        h->nn = h->dim == 2 ? h->n * h->n : h->n;
+        h->ntr = h->dim == 2 ? 4 * h->n : 2;
+        h->nstate = (size_t)h->ncell * h->nn * h->m;
+        h->st = (cudaStream_t)o.cuda_stream;
+        NodalTables tab[3];
+        build_tables(tab);
+        crkdg_status s = CRKDG_OK;
+        auto chk = [&](cudaError_t e, const char *what) {
+            if (e != cudaSuccess && s == CRKDG_OK) {
+                s = e == cudaErrorMemoryAllocation ? CRKDG_E_OOM : CRKDG_E_CUDA;
+                h->err = std::string(what) + ": " + cudaGetErrorString(e);
+            }
+        };
+        chk(h->dim == 1 ? crkdg_upload_tables_1d(tab) : crkdg_upload_tables_2d(tab), "upload tables");
+        size_t bytes = h->nstate * sizeof(double);
+        if (s == CRKDG_OK) chk(cudaMalloc(&h->u, bytes), "cudaMalloc state");
+        if (s == CRKDG_OK) chk(cudaMalloc(&h->unew, bytes), "cudaMalloc state");
+        if (s == CRKDG_OK) chk(cudaMalloc(&h->ustar, bytes), "cudaMalloc state");
+        if (s == CRKDG_OK) chk(cudaMalloc(&h->aux, (size_t)h->ncell * h->m * sizeof(double)), "cudaMalloc aux");
+        if (s == CRKDG_OK) chk(cudaMalloc(&h->scal, sizeof(DevScal)), "cudaMalloc scalars");
+        if (s == CRKDG_OK) chk(cudaMallocHost(&h->hs, sizeof(DevScal)), "cudaMallocHost");
+        if (s == CRKDG_OK) chk(cudaMallocHost(&h->hinit, sizeof(DevScal)), "cudaMallocHost");
+        if (s == CRKDG_OK) chk(cudaMemsetAsync(h->u, 0, bytes, h->st), "cudaMemset");
+        if (s == CRKDG_OK) chk(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+        if (s != CRKDG_OK) {
+            crkdg_destroy(h);
+            return s;
+        }
+        memset(h->hinit, 0, sizeof(DevScal));
+        h->hinit->thmin = bits_of(1.0);
+        h->hinit->ord[0] = h->hinit->ord[1] = ~0ull;
+        *out = h;
+        return CRKDG_OK;
+    } catch (...) {
+        crkdg_destroy(h);
+        return CRKDG_E_OOM;
+    }
+}
+
+crkdg_status crkdg_destroy(crkdg_t h) {
+    if (!h) return CRKDG_OK;
+    if (h->st || h->u) cudaStreamSynchronize(h->st);
+    for (int i = 0; i < 3; ++i)
+        if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    cudaFree(h->u);
+    cudaFree(h->unew);
+    cudaFree(h->ustar);
+    cudaFree(h->tr);
+    cudaFree(h->aux);
+    cudaFree(h->scal);
+    cudaFreeHost(h->hs);
+    cudaFreeHost(h->hinit);
+    delete h;
+    return CRKDG_OK;
+}
+
+size_t crkdg_state_size(crkdg_t h) { return h ? h->nstate : 0; }
+
+crkdg_status crkdg_set_profiling(crkdg_t h, int on) {
+    if (!h) return CRKDG_E_ARG;
+    if (on && !h->ev[0])
+        for (int i = 0; i < 3; ++i) CK(h, cudaEventCreate(&h->ev[i]));
+    h->prof = on != 0;
+    h->prof_ms[0] = h->prof_ms[1] = 0.0;
+    h->prof_n[0] = h->prof_n[1] = 0;
+    return CRKDG_OK;
+}
+
+crkdg_status crkdg_kernel_times(crkdg_t h, double ms[2], long long launches[2]) {
+    if (!h || !ms || !launches) return CRKDG_E_ARG;
+    ms[0] = h->prof_ms[0];
+    ms[1] = h->prof_ms[1];
+    launches[0] = h->prof_n[0];
+    launches[1] = h->prof_n[1];
+    return CRKDG_OK;
+}
+
+const char *crkdg_last_error(crkdg_t h) { return h ? h->err.c_str() : "invalid handle"; }
+
+crkdg_status crkdg_set_state(crkdg_t h, const double *nodal, size_t count, int on_device) {
+    if (!h) return CRKDG_E_ARG;
+    if (!nodal || count != h->nstate) return fail(h, CRKDG_E_ARG, "set_state: count must equal the state size");
+    try {
+        CK(h, cudaMemcpyAsync(h->unew, nodal, count * sizeof(double),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+        Params P = base_params(h);
+        Bufs B = base_bufs(h);
+        B.un = h->unew;
+        B.unew = h->u;
+        CK(h, reset_scalars(h) == CRKDG_OK ? cudaSuccess : cudaErrorUnknown);
+        CK(h, launch(h, K_LIMIT, P, B));
+        CK(h, cudaStreamSynchronize(h->st));
+        h->a0_valid = false;
+        return CRKDG_OK;
+    } catch (...) {
+        return CRKDG_E_OOM;
+    }
+}
+
+crkdg_status crkdg_get_state(crkdg_t h, double *nodal, size_t count, int on_device) {
+    if (!h) return CRKDG_E_ARG;
+    if (!nodal || count != h->nstate) return fail(h, CRKDG_E_ARG, "get_state: count must equal the state size");
+    CK(h, cudaMemcpyAsync(nodal, h->u, count * sizeof(double),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    return CRKDG_OK;
+}
+
+crkdg_status crkdg_max_dt(crkdg_t h, double cfl, double *dt) {
+    if (!h || !dt) return CRKDG_E_ARG;
+    if (!(cfl > 0.0)) return fail(h, CRKDG_E_ARG, "max_dt: cfl must be > 0");
+    try {
+        if (!h->a0_valid) {
+            crkdg_status s = compute_a0(h);
+            if (s) return s;
+        }
+        double hx = (h->mesh.x1 - h->mesh.x0) / h->mesh.nx;
+        double dx = hx;
+        if (h->dim == 2) {
+            double hy = (h->mesh.y1 - h->mesh.y0) / h->mesh.ny;
+            if (hy < dx) dx = hy;
+        }
+        *dt = h->a0 > 0.0 ? cfl * dx / h->a0 : INFINITY;
+        return CRKDG_OK;
+    } catch (...) {
+        return CRKDG_E_OOM;
+    }
+}
+
+crkdg_status crkdg_step(crkdg_t h, double dt, const crkdg_tableau *tab, crkdg_step_info *info) {
+    if (!h) return CRKDG_E_ARG;
+    try {
+        crkdg_status s = check_tableau(h, tab);
+        if (s) return s;
+        if (!(dt > 0.0) || !isfinite(dt)) return fail(h, CRKDG_E_ARG, "step: dt must be finite and > 0");
+        Params P = base_params(h);
+        P.s = tab->s;
+        P.mode = MODE_STEP;
+        int ns = 0;
+        for (int i = 0; i < tab->s; ++i) {
+            P.b[i] = tab->b[i];
+            for (int j = 0; j < tab->s; ++j) P.A[i][j] = tab->A[i * tab->s + j];
+            P.slot[i] = tab->b[i] != 0.0 ? ns++ : -1;
+        }
+        P.nslot = ns;
+        s = ensure_traces(h, ns > 0 ? ns : 1);
+        if (s) return s;
+        Bufs B = base_bufs(h);
+        for (int r = 0; r <= h->opt.max_halvings; ++r) {
+            P.dt = dt;
+            B.un = h->u;
+            B.unew = h->unew;
+            s = reset_scalars(h);
+            if (s) return s;
+            if (h->prof) CK(h, cudaEventRecord(h->ev[0], h->st));
+            CK(h, launch(h, K_INNER, P, B));
+            if (h->prof) CK(h, cudaEventRecord(h->ev[1], h->st));
+            CK(h, launch(h, K_FINAL, P, B));
+            if (h->prof) CK(h, cudaEventRecord(h->ev[2], h->st));
+            s = read_scalars(h);
+            if (s) return s;
+            if (h->prof) {
+                float t0 = 0.f, t1 = 0.f;
+                CK(h, cudaEventElapsedTime(&t0, h->ev[0], h->ev[1]));
+                CK(h, cudaEventElapsedTime(&t1, h->ev[1], h->ev[2]));
+                h->prof_ms[0] += t0;
+                h->prof_ms[1] += t1;
+                h->prof_n[0] += 1;
+                h->prof_n[1] += 1;
+            }
+            if (h->hs->flag == 0) {
+                double *t = h->u;
+                h->u = h->unew;
+                h->unew = t;
+                h->a0 = from_bits(h->hs->a0);
+                h->a0_valid = true;
+                if (info) {
+                    info->dt_taken = dt;
+                    info->restarts = r;
+                    info->cells_limited = (long long)h->hs->nlim;
+                    info->theta_min = from_bits(h->hs->thmin);
+                    info->troubled = 0;
+                    info->mass_drift = 0.0;
+                }
+                return CRKDG_OK;
+            }
+            dt *= 0.5;
+        }
+        return fail(h, CRKDG_E_BOUNDS, "step: cell averages left the admissible set after max_halvings restarts");
+    } catch (...) {
+        return CRKDG_E_OOM;
+    }
+}
+
+crkdg_status crkdg_advance(crkdg_t h, int nsteps, double cfl, double t_end, const crkdg_tableau *tab,
+                           double *t, int *steps_done, int *restarts) {
+    if (!h || !t) return CRKDG_E_ARG;
+    int done = 0, rs = 0;
+    crkdg_status s = CRKDG_OK;
+    for (int i = 0; i < nsteps; ++i) {
+        if (!(*t < t_end)) break;
+        double dt;
+        s = crkdg_max_dt(h, cfl, &dt);
+        if (s) break;
+        if (dt > t_end - *t) dt = t_end - *t;
+        crkdg_step_info info;
+        s = crkdg_step(h, dt, tab, &info);
+        if (s) break;
+        *t += info.dt_taken;
+        ++done;
+        rs += info.restarts;
+    }
+    if (steps_done) *steps_done = done;
+    if (restarts) *restarts = rs;
+    return s;
+}
+
+crkdg_status crkdg_apply_operator(crkdg_t h, int op, const double *in_dev, double *out_dev) {
+    if (!h) return CRKDG_E_ARG;
+    if (!in_dev || !out_dev || in_dev == out_dev) return fail(h, CRKDG_E_ARG, "apply_operator: bad pointers");
+    try {
+        Params P = base_params(h);
+        Bufs B = base_bufs(h);
+        P.s = 1;
+        P.dt = 1.0;
+        P.b[0] = 1.0;
+        if (op == CRKDG_OP_G) {
+            P.mode = MODE_OP_G;
+            B.un = in_dev;
+            B.ustar = out_dev;
+            CK(h, launch(h, K_INNER, P, B));
+        } else if (op == CRKDG_OP_F) {
+            crkdg_status s = ensure_traces(h, 1);
+            if (s) return s;
+            B.tr = h->tr;
+            P.slot[0] = 0;
+            P.nslot = 1;
+            P.mode = MODE_OP_G;
+            B.un = in_dev;
+            B.ustar = h->ustar;
+            CK(h, launch(h, K_INNER, P, B));
+            P.mode = MODE_OP_F;
+            B.unew = out_dev;
+            CK(h, launch(h, K_FINAL, P, B));
+        } else if (op == CRKDG_OP_LIMIT) {
+            B.un = in_dev;
+            B.unew = out_dev;
+            CK(h, launch(h, K_LIMIT, P, B));
+        } else {
+            return fail(h, CRKDG_E_ARG, "apply_operator: unknown op");
+        }
+        CK(h, cudaStreamSynchronize(h->st));
+        return CRKDG_OK;
+    } catch (...) {
+        return CRKDG_E_OOM;
+    }
+}
+
+crkdg_status crkdg_cell_averages(crkdg_t h, double *avg, int on_device) {
+    if (!h || !avg) return CRKDG_E_ARG;
+    Params P = base_params(h);
+    Bufs B = base_bufs(h);
+    CK(h, launch(h, K_AVG, P, B));
+    CK(h, cudaMemcpyAsync(avg, h->aux, (size_t)h->ncell * h->m * sizeof(double),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    return CRKDG_OK;
+}
+
+crkdg_status crkdg_bound_margins(crkdg_t h, double margins[2]) {
+    if (!h || !margins) return CRKDG_E_ARG;
+    crkdg_status s = reset_scalars(h);
+    if (s) return s;
+    Params P = base_params(h);
+    Bufs B = base_bufs(h);
+    CK(h, launch(h, K_MARGINS, P, B));
+    s = read_scalars(h);
+    if (s) return s;
+    margins[0] = from_ordbits(h->hs->ord[0]);
+    margins[1] = from_ordbits(h->hs->ord[1]);
+    return CRKDG_OK;
+}
+
+crkdg_status crkdg_total_mass(crkdg_t h, int comp, double *mass) {
+    if (!h || !mass || comp < 0 || comp >= h->m) return CRKDG_E_ARG;
+    try {
+        std::string tmp;
+        double *host = new (std::nothrow) double[(size_t)h->ncell * h->m];
+        if (!host) return CRKDG_E_OOM;
+        crkdg_status s = crkdg_cell_averages(h, host, 0);
+        if (s) {
+            delete[] host;
+            return s;
+        }
+        double acc = 0.0;  // fixed cell order: deterministic
+        for (int c = 0; c < h->ncell; ++c) acc += host[(size_t)c * h->m + comp];
+        delete[] host;
+        double hx = (h->mesh.x1 - h->mesh.x0) / h->mesh.nx;
+        double hy = h->dim == 2 ? (h->mesh.y1 - h->mesh.y0) / h->mesh.ny : 1.0;
+        *mass = acc * hx * hy;
+        return CRKDG_OK;
+    } catch (...) {
+        return CRKDG_E_OOM;
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,13 @@
+// dg_2d.cu -- 2D instantiations of the FP64 cRKDG kernels (see dg_core.cuh).
+#include "dg_core.cuh"
+
+using namespace crkdg;
+
+cudaError_t crkdg_upload_tables_2d(const NodalTables *t) {
+    return cudaMemcpyToSymbol(c_tab, t, sizeof(NodalTables) * 3);
+}
+
+cudaError_t crkdg_launch_2d(int kernel, int n, int phys, int nblocks, cudaStream_t st, const Params &P,
+                            const Bufs &B) {
+    return launch_dim<2>(kernel, n, phys, nblocks, st, P, B);
+}

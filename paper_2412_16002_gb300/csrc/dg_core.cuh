@@ -1,0 +1,793 @@
+// dg_core.cuh -- device code of the FP64 cRKDG path (arXiv 2412.16002).
+//
+// Included by exactly one translation unit per dimension (dg_1d.cu, dg_2d.cu),
+// each of which owns its copy of the constant tables.
+//
+// Work decomposition: one thread per (cell, node).  A block holds NCB cells of
+// n^d nodes each; the line operators (volume term, traces, lift, S_K
+// interpolation) exchange node data through shared memory.  Per-cell
+// reductions (average, min/max over S_K) are taken by one leader thread per
+// cell in a fixed order, so every result is deterministic.
+//
+// Nodal Q^k form of the operators (collocation at the Gauss points, exact
+// diagonal mass matrix), per x-line of a cell with traces u_L = sum_a l_a(-1) u_a,
+// u_R = sum_a l_a(+1) u_a:
+//   G_a = (2/h) [ sum_q Dhat[a][q] f_q - l_a(+1)/w_a f(u_R) + l_a(-1)/w_a f(u_L) ]
+// (Sec. 2.1 with the (k+1)-point Gauss rule); in 2D the y-lines add the same
+// term.  F replaces f(u_R), f(u_L) by the Lax--Friedrichs flux (eq. dxDG), so
+// F = G + lift(fhat - f(u_int)); the final kernel adds exactly that correction.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "dg_types.h"
+
+namespace crkdg {
+
+static __constant__ NodalTables c_tab[3];  // n = 2, 3, 4
+
+// ----------------------------------------------------------------------------- helpers
+
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+__device__ __forceinline__ double bitsd(unsigned long long u) { return __longlong_as_double((long long)u); }
+// order-preserving map of a double onto uint64 (for atomicMin over signed values)
+__device__ __forceinline__ unsigned long long ordbits(double x) {
+    unsigned long long u = dbits(x);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+// theta = num/den clamped to [0, 1]; a non-positive denominator gives 0
+__device__ __forceinline__ double ratio01(double num, double den) {
+    if (!(den > 0.0)) return 0.0;
+    double t = num / den;
+    if (!(t >= 0.0)) t = 0.0;
+    return t > 1.0 ? 1.0 : t;
+}
+
+// ----------------------------------------------------------------------------- physics
+
+// flux f(u) . e_dir  (eq. claws; Euler eq. Euler, Euler-2)
+template <int PHYS, int DIM>
+__device__ __forceinline__ void flux_dir(const Params &P, const double *u, int dir, double *f) {
+    if constexpr (PHYS == PH_ADV) {
+        f[0] = (dir == 0 ? P.velx : P.vely) * u[0];
+    } else if constexpr (PHYS == PH_BURG) {
+        f[0] = 0.5 * u[0] * u[0];
+    } else if constexpr (DIM == 1) {
+        double ri = 1.0 / u[0];
+        double w = u[1] * ri;
+        double p = (P.gamma - 1.0) * (u[2] - 0.5 * u[1] * w);
+        f[0] = u[1];
+        f[1] = u[1] * w + p;
+        f[2] = (u[2] + p) * w;
+    } else {
+        double ri = 1.0 / u[0];
+        double wx = u[1] * ri, wy = u[2] * ri;
+        double p = (P.gamma - 1.0) * (u[3] - 0.5 * (u[1] * wx + u[2] * wy));
+        double wd = dir == 0 ? wx : wy;
+        f[0] = u[1 + dir];
+        f[1] = u[1] * wd + (dir == 0 ? p : 0.0);
+        f[2] = u[2] * wd + (dir == 1 ? p : 0.0);
+        f[3] = (u[3] + p) * wd;
+    }
+}
+
+// both directions with one reciprocal (2D)
+template <int PHYS>
+__device__ __forceinline__ void flux_xy(const Params &P, const double *u, double *fx, double *fy) {
+    if constexpr (PHYS == PH_ADV) {
+        fx[0] = P.velx * u[0];
+        fy[0] = P.vely * u[0];
+    } else if constexpr (PHYS == PH_BURG) {
+        fx[0] = fy[0] = 0.5 * u[0] * u[0];
+    } else {
+        double ri = 1.0 / u[0];
+        double wx = u[1] * ri, wy = u[2] * ri;
+        double p = (P.gamma - 1.0) * (u[3] - 0.5 * (u[1] * wx + u[2] * wy));
+        double ep = u[3] + p;
+        fx[0] = u[1];
+        fx[1] = u[1] * wx + p;
+        fx[2] = u[2] * wx;
+        fx[3] = ep * wx;
+        fy[0] = u[2];
+        fy[1] = u[1] * wy;
+        fy[2] = u[2] * wy + p;
+        fy[3] = ep * wy;
+    }
+}
+
+// spectral radius of df/du . e_dir (alpha of the LF flux, a0 of Sec. 2.1)
+template <int PHYS, int DIM>
+__device__ __forceinline__ double speed_dir(const Params &P, const double *u, int dir) {
+    if constexpr (PHYS == PH_ADV) {
+        return fabs(dir == 0 ? P.velx : P.vely);
+    } else if constexpr (PHYS == PH_BURG) {
+        return fabs(u[0]);
+    } else {
+        double ri = 1.0 / u[0];
+        double kin = DIM == 1 ? u[1] * u[1] : u[1] * u[1] + u[2] * u[2];
+        double p = (P.gamma - 1.0) * (u[DIM + 1] - 0.5 * kin * ri);
+        double c2 = P.gamma * p * ri;
+        double c = c2 > 0.0 ? sqrt(c2) : 0.0;
+        return fabs(u[1 + dir] * ri) + c;
+    }
+}
+
+// rho e = E - |m|^2 / (2 rho)   (eq. Euler-limiter2)
+template <int DIM>
+__device__ __forceinline__ double rho_e(const double *u) {
+    double kin = DIM == 1 ? u[1] * u[1] : u[1] * u[1] + u[2] * u[2];
+    return u[DIM + 1] - 0.5 * kin / u[0];
+}
+
+// averages in B (scalar) or B^eps (Euler, rho >= eps and rho e >= eps); NaN fails
+template <int PHYS, int DIM>
+__device__ __forceinline__ bool admissible(const Params &P, const double *ub) {
+    if constexpr (PHYS == PH_EULER) {
+        return ub[0] >= P.eps && rho_e<DIM>(ub) >= P.eps;
+    } else {
+        return ub[0] >= P.lo && ub[0] <= P.hi;
+    }
+}
+
+// exterior trace on a boundary side (final stage only)
+template <int PHYS, int DIM>
+__device__ __forceinline__ void boundary_state(const Params &P, int side, const double *ui, double *ue) {
+    constexpr int M = ncomp(PHYS, DIM);
+    int bc = P.bc[side];
+    if (bc == BC_DIRICHLET) {
+#pragma unroll
+        for (int c = 0; c < M; ++c) ue[c] = P.bcs[side][c];
+    } else {
+#pragma unroll
+        for (int c = 0; c < M; ++c) ue[c] = ui[c];
+        if constexpr (PHYS == PH_EULER) {
+            if (bc == BC_REFLECT) ue[1 + side / 2] = -ui[1 + side / 2];
+        }
+    }
+}
+
+// neighbour across side (0 L, 1 R, 2 B, 3 T), or -1 on a non-periodic boundary
+__device__ __forceinline__ int neighbour(const Params &P, int cell, int side) {
+    int cx = cell % P.nx, cy = cell / P.nx;
+    switch (side) {
+    case 0: return cx > 0 ? cell - 1 : (P.bc[0] == BC_PERIODIC ? cell + P.nx - 1 : -1);
+    case 1: return cx < P.nx - 1 ? cell + 1 : (P.bc[1] == BC_PERIODIC ? cell - P.nx + 1 : -1);
+    case 2: return cy > 0 ? cell - P.nx : (P.bc[2] == BC_PERIODIC ? cell + (P.ny - 1) * P.nx : -1);
+    default: return cy < P.ny - 1 ? cell + P.nx : (P.bc[3] == BC_PERIODIC ? cell - (P.ny - 1) * P.nx : -1);
+    }
+}
+
+// ----------------------------------------------------------------------------- block layout
+
+template <int DIM, int N, int PHYS>
+struct Cfg {
+    static constexpr int D = DIM;
+    static constexpr int M = ncomp(PHYS, DIM);
+    static constexpr int NN = DIM == 2 ? N * N : N;       // nodes per cell
+    static constexpr int NF = DIM == 2 ? N : 1;           // quadrature points per face
+    static constexpr int NTR = 2 * DIM * NF;              // face points per cell
+    static constexpr int L = nlob(N);                     // Gauss--Lobatto points
+    static constexpr int NSK = DIM == 2 ? 2 * N * L : L;  // |S_K|
+    static constexpr int NCB = cells_per_block(DIM, N);  // cells per block
+    static constexpr int NT = NCB * NN;                   // threads per block (multiple of 32)
+    static constexpr int PPT = (NSK + NN - 1) / NN;       // S_K points per thread
+    static constexpr int FPT = (NTR + NN - 1) / NN;       // face points per thread
+};
+
+template <class C>
+struct Smem {
+    double u[C::NCB][C::M][C::NN];
+    double f[C::D][C::NCB][C::M][C::NN];
+    double tf[C::NCB][C::NTR][C::M];
+    double avg[C::NCB][C::M];
+    union {  // the limiter's reductions and the final kernel's edge speeds never overlap
+        double red[C::NCB][C::NN][2];
+        double al[C::NCB][C::NTR];
+    };
+    double th[C::NCB][2];
+    int bad[C::NCB];
+};
+
+// value of every component at S_K point p of the cell whose nodes are su
+template <int DIM, int N, int M, int NN>
+__device__ __forceinline__ void sk_eval(const double (&su)[M][NN], int p, double *v) {
+    const NodalTables &T = c_tab[N - 2];
+    constexpr int L = nlob(N);
+    if constexpr (DIM == 1) {
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            double s = 0.0;
+#pragma unroll
+            for (int a = 0; a < N; ++a) s = fma(T.Igl[p][a], su[c][a], s);
+            v[c] = s;
+        }
+    } else {
+        if (p < N * L) {  // (x^GL_alpha, y^G_beta): interpolate along row beta
+            int beta = p / L, al = p - beta * L;
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                double s = 0.0;
+#pragma unroll
+                for (int a = 0; a < N; ++a) s = fma(T.Igl[al][a], su[c][beta * N + a], s);
+                v[c] = s;
+            }
+        } else {  // (x^G_beta, y^GL_alpha): interpolate along column beta
+            int q = p - N * L;
+            int beta = q / L, al = q - beta * L;
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                double s = 0.0;
+#pragma unroll
+                for (int b = 0; b < N; ++b) s = fma(T.Igl[al][b], su[c][b * N + beta], s);
+                v[c] = s;
+            }
+        }
+    }
+}
+
+// S_K bound predicate used by the limiter's verification and by the margins
+template <int PHYS, int DIM>
+__device__ __forceinline__ bool point_ok(const Params &P, const double *v) {
+    if constexpr (PHYS == PH_EULER) {
+        return v[0] >= P.eps && rho_e<DIM>(v) >= P.eps;
+    } else {
+        return v[0] >= P.lo && v[0] <= P.hi;
+    }
+}
+
+// ----------------------------------------------------------------------------- limiter
+
+// shrink factors of the rounding safety rule: 1-2^-40, 1-2^-30, 1-2^-20, 1-2^-10
+__device__ __forceinline__ double shrink_factor(int attempt) {
+    switch (attempt) {
+    case 1: return 1.0 - 9.094947017729282e-13;
+    case 2: return 1.0 - 9.313225746154785e-10;
+    case 3: return 1.0 - 9.5367431640625e-07;
+    case 4: return 1.0 - 0.0009765625;
+    default: return 0.0;
+    }
+}
+
+// Scaling limiter of one stage (Prop. 2.4 scalar, eq. Euler-limiter1/2), block
+// collective.  u: this thread's node values (in/out).  pts: on return the values
+// at this thread's S_K points of the limited polynomial.  With check_avg the
+// admissibility of the cell average sets *B.flag (Sec. 4.1 restart test).
+template <int DIM, int N, int PHYS>
+__device__ void limit_block(const Params &P, const Bufs &B, Smem<Cfg<DIM, N, PHYS>> &S, int lc,
+                            int node, bool active, double *u,
+                            double (&pts)[Cfg<DIM, N, PHYS>::PPT][ncomp(PHYS, DIM)], bool check_avg,
+                            bool stats) {
+    using C = Cfg<DIM, N, PHYS>;
+    constexpr int M = C::M, NN = C::NN, NSK = C::NSK, PPT = C::PPT;
+    const NodalTables &T = c_tab[N - 2];
+
+    // 1. publish node values
+#pragma unroll
+    for (int c = 0; c < M; ++c) S.u[lc][c][node] = u[c];
+    __syncthreads();
+    // 2. cell averages (Gauss weights; the mass matrix is exact)
+    for (int c = node; c < M; c += NN) {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < NN; ++q) s = fma(DIM == 2 ? T.w2[q] : T.w1[q], S.u[lc][c][q], s);
+        S.avg[lc][c] = s;
+    }
+    __syncthreads();
+    // 3. values at S_K and this thread's extremes
+    double pmin = INFINITY, pmax = -INFINITY;
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+        int p = node + j * NN;
+        if (p < NSK) {
+            sk_eval<DIM, N, M, NN>(S.u[lc], p, pts[j]);
+            pmin = fmin(pmin, pts[j][0]);
+            pmax = fmax(pmax, pts[j][0]);
+            if (!(pts[j][0] == pts[j][0])) pmin = -INFINITY;  // NaN counts as a violation
+        }
+    }
+    S.red[lc][node][0] = pmin;
+    S.red[lc][node][1] = pmax;
+    double ub[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) ub[c] = S.avg[lc][c];
+    __syncthreads();
+    // 4. leader: admissibility of the average and theta (theta_1 for Euler)
+    if (node == 0) {
+        double mn = INFINITY, mx = -INFINITY;
+        for (int q = 0; q < NN; ++q) {
+            mn = fmin(mn, S.red[lc][q][0]);
+            mx = fmax(mx, S.red[lc][q][1]);
+        }
+        if (check_avg && active && !admissible<PHYS, DIM>(P, ub)) atomicOr(B.flag, 1);
+        double th = 1.0;
+        if constexpr (PHYS == PH_EULER) {
+            if (mn < P.eps) th = ratio01(ub[0] - P.eps, ub[0] - mn);
+        } else {
+            if (mx > P.hi) th = fmin(th, ratio01(P.hi - ub[0], mx - ub[0]));
+            if (mn < P.lo) th = fmin(th, ratio01(ub[0] - P.lo, ub[0] - mn));
+        }
+        S.th[lc][0] = th;
+        S.th[lc][1] = 1.0;
+        S.bad[lc] = 0;
+    }
+    __syncthreads();
+    double th1 = S.th[lc][0];
+    double th2 = 1.0;
+    if constexpr (PHYS == PH_EULER) {
+        // 5. rho e at S_K with the density already scaled by theta_1
+        double pm = INFINITY;
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            int p = node + j * NN;
+            if (p < NSK) {
+                double v[M];
+#pragma unroll
+                for (int c = 0; c < M; ++c) v[c] = pts[j][c];
+                if (th1 < 1.0) v[0] = th1 * (v[0] - ub[0]) + ub[0];
+                double re = rho_e<DIM>(v);
+                pm = (re == re) ? fmin(pm, re) : -INFINITY;  // NaN counts as a violation
+            }
+        }
+        S.red[lc][node][1] = pm;
+        __syncthreads();
+        if (node == 0) {
+            double mn = INFINITY;
+            for (int q = 0; q < NN; ++q) mn = fmin(mn, S.red[lc][q][1]);
+            double reb = rho_e<DIM>(ub);
+            S.th[lc][1] = (mn >= P.eps) ? 1.0 : ratio01(reb - P.eps, reb - mn);
+        }
+        __syncthreads();
+        th2 = S.th[lc][1];
+    }
+    // 6. rescale towards the average
+    bool limited = (th1 < 1.0) || (th2 < 1.0);
+    double uo[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) uo[c] = u[c];
+    auto apply = [&](double t2) {
+        if constexpr (PHYS == PH_EULER) {
+            double r = th1 < 1.0 ? th1 * (uo[0] - ub[0]) + ub[0] : uo[0];
+            u[0] = t2 < 1.0 ? t2 * (r - ub[0]) + ub[0] : r;
+#pragma unroll
+            for (int c = 1; c < M; ++c) u[c] = t2 < 1.0 ? t2 * (uo[c] - ub[c]) + ub[c] : uo[c];
+        } else {
+            double t = th1 * t2;
+            u[0] = t < 1.0 ? t * (uo[0] - ub[0]) + ub[0] : uo[0];
+        }
+    };
+    double tfin = th2;
+    if (limited) apply(th2);
+    // 7. verify the limited cells on S_K with the same interpolation; shrink on a
+    //    rounding violation (the final scaling factor towards the average)
+    bool any_limited = __syncthreads_or(limited);
+    if (any_limited) {
+        for (int attempt = 0; attempt <= 5; ++attempt) {
+#pragma unroll
+            for (int c = 0; c < M; ++c) S.u[lc][c][node] = u[c];
+            __syncthreads();
+            bool viol = false;
+            if (limited) {
+#pragma unroll
+                for (int j = 0; j < PPT; ++j) {
+                    int p = node + j * NN;
+                    if (p < NSK) {
+                        sk_eval<DIM, N, M, NN>(S.u[lc], p, pts[j]);
+                        if (!point_ok<PHYS, DIM>(P, pts[j])) viol = true;
+                    }
+                }
+            }
+            if (viol) S.bad[lc] = 1;
+            bool again = __syncthreads_or(viol);
+            if (!again || attempt == 5) break;
+            bool mine = S.bad[lc] != 0;
+            __syncthreads();
+            if (node == 0) S.bad[lc] = 0;
+            if (mine) {
+                double f = shrink_factor(attempt + 1);
+                if constexpr (PHYS == PH_EULER) {
+                    tfin = th2 * f;
+                    apply(tfin);
+                } else {
+                    tfin = th2 * f;  // th2 == 1 for scalars: the factor multiplies theta
+                    apply(tfin);
+                }
+            }
+        }
+    }
+    if (stats && active && node == 0 && limited) {
+        double tr = PHYS == PH_EULER ? fmin(th1, tfin) : th1 * tfin;
+        atomicAdd(B.nlim, 1ull);
+        atomicMin(B.thmin, dbits(tr > 0.0 ? tr : 0.0));
+    }
+}
+
+// ----------------------------------------------------------------------------- G
+
+// G(u) at this thread's node (block collective).  trs receives the interior
+// trace states of this thread's face points.
+template <int DIM, int N, int PHYS>
+__device__ void eval_G(const Params &P, Smem<Cfg<DIM, N, PHYS>> &S, int lc, int node, const double *u,
+                       double *g, double (&trs)[Cfg<DIM, N, PHYS>::FPT][ncomp(PHYS, DIM)]) {
+    using C = Cfg<DIM, N, PHYS>;
+    constexpr int M = C::M, NN = C::NN, NF = C::NF, NTR = C::NTR, FPT = C::FPT;
+    const NodalTables &T = c_tab[N - 2];
+    const int a = node % N, b = DIM == 2 ? node / N : 0;
+    // 1. flux at the node
+    {
+        double fx[M], fy[M];
+        if constexpr (DIM == 2) {
+            flux_xy<PHYS>(P, u, fx, fy);
+        } else {
+            flux_dir<PHYS, DIM>(P, u, 0, fx);
+        }
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            S.u[lc][c][node] = u[c];
+            S.f[0][lc][c][node] = fx[c];
+            if constexpr (DIM == 2) S.f[1][lc][c][node] = fy[c];
+        }
+    }
+    __syncthreads();
+    // 2. volume term and interior traces
+    double vx[M], vy[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < N; ++q) s = fma(T.Dhat[a][q], S.f[0][lc][c][b * N + q], s);
+        vx[c] = s;
+        if constexpr (DIM == 2) {
+            double t = 0.0;
+#pragma unroll
+            for (int r = 0; r < N; ++r) t = fma(T.Dhat[b][r], S.f[1][lc][c][r * N + a], t);
+            vy[c] = t;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < FPT; ++j) {
+        int fp = node + j * NN;
+        if (fp < NTR) {
+            int face = fp / NF, pos = fp - face * NF;
+            const double *l = (face & 1) ? T.lp : T.lm;
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                double s = 0.0;
+                if (DIM == 1 || face < 2) {
+#pragma unroll
+                    for (int q = 0; q < N; ++q) s = fma(l[q], S.u[lc][c][pos * N + q], s);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < N; ++q) s = fma(l[q], S.u[lc][c][q * N + pos], s);
+                }
+                trs[j][c] = s;
+            }
+            double f[M];
+            flux_dir<PHYS, DIM>(P, trs[j], face >> 1, f);
+#pragma unroll
+            for (int c = 0; c < M; ++c) S.tf[lc][fp][c] = f[c];
+        }
+    }
+    __syncthreads();
+    // 3. lift the interior-trace edge terms
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+        double gx = vx[c] - T.liftp[a] * S.tf[lc][NF + b][c] + T.liftm[a] * S.tf[lc][b][c];
+        double gv = P.rhx * gx;
+        if constexpr (DIM == 2) {
+            double gy = vy[c] - T.liftp[b] * S.tf[lc][3 * NF + a][c] + T.liftm[b] * S.tf[lc][2 * NF + a][c];
+            gv = fma(P.rhy, gy, gv);
+        }
+        g[c] = gv;
+    }
+}
+
+// ----------------------------------------------------------------------------- kernels
+
+template <int DIM, int N, int PHYS>
+__device__ __forceinline__ void load_node(const Params &P, const double *src, int cell, int node, bool active,
+                                          double *u) {
+    using C = Cfg<DIM, N, PHYS>;
+#pragma unroll
+    for (int c = 0; c < C::M; ++c) {
+        if (active) {
+            u[c] = src[((size_t)c * P.ncell + cell) * C::NN + node];
+        } else {  // benign padding state for idle threads of the last block
+            u[c] = (PHYS == PH_EULER && (c == 0 || c == C::M - 1)) ? 1.0 : (PHYS == PH_EULER ? 0.0 : 0.5 * (P.lo + P.hi));
+        }
+    }
+}
+
+template <int DIM, int N, int PHYS>
+__device__ __forceinline__ void store_node(const Params &P, double *dst, int cell, int node, bool active,
+                                           const double *u) {
+    using C = Cfg<DIM, N, PHYS>;
+    if (!active) return;
+#pragma unroll
+    for (int c = 0; c < C::M; ++c) dst[((size_t)c * P.ncell + cell) * C::NN + node] = u[c];
+}
+
+// Inner stages (cell-local, no neighbour data): for i = 1..s
+//   u^(i) = u^n + dt sum_{j<i} a_ij G(u~^(j)),  u~^(i) = L(u^(i))   (eq. rkdg-lim)
+// and the accumulation u* = u^n + dt sum_i b_i G(u~^(i)); the traces of every
+// u~^(i) with b_i != 0 go to B.tr for the final kernel.
+template <int DIM, int N, int PHYS>
+__global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_inner(Params P, Bufs B) {
+    using C = Cfg<DIM, N, PHYS>;
+    constexpr int M = C::M, NN = C::NN, NTR = C::NTR, FPT = C::FPT;
+    __shared__ Smem<C> S;
+    const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
+    const int cell = blockIdx.x * C::NCB + lc;
+    const bool active = cell < P.ncell;
+    double un[M], cur[M], acc[M], gh[MAXS][M];
+    load_node<DIM, N, PHYS>(P, B.un, cell, node, active, un);
+#pragma unroll
+    for (int c = 0; c < M; ++c) cur[c] = acc[c] = un[c];
+#pragma unroll
+    for (int i = 0; i < MAXS; ++i) {
+        if (i >= P.s) break;
+        if (i > 0) {
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                double v = un[c];
+#pragma unroll
+                for (int j = 0; j < i; ++j)
+                    if (P.A[i][j] != 0.0) v = fma(P.dt * P.A[i][j], gh[j][c], v);
+                cur[c] = v;
+            }
+            double pts[C::PPT][M];
+            limit_block<DIM, N, PHYS>(P, B, S, lc, node, active, cur, pts, true, true);
+        }
+        double trs[FPT][M];
+        eval_G<DIM, N, PHYS>(P, S, lc, node, cur, gh[i], trs);
+        if (P.mode == MODE_OP_G) {
+#pragma unroll
+            for (int c = 0; c < M; ++c) acc[c] = gh[i][c];
+        } else if (P.b[i] != 0.0) {
+#pragma unroll
+            for (int c = 0; c < M; ++c) acc[c] = fma(P.dt * P.b[i], gh[i][c], acc[c]);
+        }
+        if (P.slot[i] >= 0 && active) {
+            double *dst = B.tr + (size_t)P.slot[i] * M * P.ncell * NTR;
+#pragma unroll
+            for (int j = 0; j < FPT; ++j) {
+                int fp = node + j * NN;
+                if (fp < NTR) {
+#pragma unroll
+                    for (int c = 0; c < M; ++c) dst[((size_t)c * P.ncell + cell) * NTR + fp] = trs[j][c];
+                }
+            }
+        }
+    }
+    store_node<DIM, N, PHYS>(P, B.ustar, cell, node, active, acc);
+}
+
+// Final stage: u^{n+1} = u* + dt lift( sum_i b_i (fhat^(i) - f(u_int^(i))) ), then the
+// limiter, the admissibility test and a0 of the new state.  Each face flux is
+// evaluated from the same ordered pair (lower side, upper side) by both cells
+// sharing the face, so the update is conservative to round-off.
+template <int DIM, int N, int PHYS>
+__global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_final(Params P, Bufs B) {
+    using C = Cfg<DIM, N, PHYS>;
+    constexpr int M = C::M, NN = C::NN, NF = C::NF, NTR = C::NTR, FPT = C::FPT;
+    __shared__ Smem<C> S;
+    const NodalTables &T = c_tab[N - 2];
+    const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
+    const int cell = blockIdx.x * C::NCB + lc;
+    const bool active = cell < P.ncell;
+    const int a = node % N, b = DIM == 2 ? node / N : 0;
+    double u[M];
+    load_node<DIM, N, PHYS>(P, B.ustar, cell, node, active, u);
+
+    double dc[FPT][M];
+#pragma unroll
+    for (int j = 0; j < FPT; ++j)
+#pragma unroll
+        for (int c = 0; c < M; ++c) dc[j][c] = 0.0;
+
+    for (int i = 0; i < P.s; ++i) {
+        if (P.slot[i] < 0) continue;
+        const double *tr = B.tr + (size_t)P.slot[i] * M * P.ncell * NTR;
+        double uL[FPT][M], uR[FPT][M];
+#pragma unroll
+        for (int j = 0; j < FPT; ++j) {
+            int fp = node + j * NN;
+            if (fp < NTR && active) {
+                int face = fp / NF, pos = fp - face * NF;
+                double ui[M], ue[M];
+#pragma unroll
+                for (int c = 0; c < M; ++c) ui[c] = tr[((size_t)c * P.ncell + cell) * NTR + fp];
+                int nb = neighbour(P, cell, face);
+                if (nb >= 0) {
+                    int ofp = (face ^ 1) * NF + pos;
+#pragma unroll
+                    for (int c = 0; c < M; ++c) ue[c] = tr[((size_t)c * P.ncell + nb) * NTR + ofp];
+                } else {
+                    boundary_state<PHYS, DIM>(P, face, ui, ue);
+                }
+                bool upper = face & 1;  // R or T: the cell is on the lower side of the face
+#pragma unroll
+                for (int c = 0; c < M; ++c) {
+                    uL[j][c] = upper ? ui[c] : ue[c];
+                    uR[j][c] = upper ? ue[c] : ui[c];
+                }
+                int dir = face >> 1;
+                S.al[lc][fp] = fmax(speed_dir<PHYS, DIM>(P, uL[j], dir), speed_dir<PHYS, DIM>(P, uR[j], dir));
+            } else if (fp < NTR) {
+                S.al[lc][fp] = 0.0;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < FPT; ++j) {
+            int fp = node + j * NN;
+            if (fp < NTR && active) {
+                int face = fp / NF;
+                int dir = face >> 1;
+                double alpha = 0.0;  // per-edge LF viscosity: max over the edge's points
+#pragma unroll
+                for (int q = 0; q < NF; ++q) alpha = fmax(alpha, S.al[lc][face * NF + q]);
+                double fL[M], fR[M];
+                flux_dir<PHYS, DIM>(P, uL[j], dir, fL);
+                flux_dir<PHYS, DIM>(P, uR[j], dir, fR);
+                bool upper = face & 1;
+#pragma unroll
+                for (int c = 0; c < M; ++c) {
+                    double fhat = 0.5 * (fL[c] + fR[c]) - 0.5 * alpha * (uR[j][c] - uL[j][c]);
+                    double fint = upper ? fL[c] : fR[c];
+                    dc[j][c] = fma(P.b[i], fhat - fint, dc[j][c]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < FPT; ++j) {
+        int fp = node + j * NN;
+        if (fp < NTR)
+#pragma unroll
+            for (int c = 0; c < M; ++c) S.tf[lc][fp][c] = dc[j][c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+        double cx = -T.liftp[a] * S.tf[lc][NF + b][c] + T.liftm[a] * S.tf[lc][b][c];
+        double corr = P.rhx * cx;
+        if constexpr (DIM == 2) {
+            double cy = -T.liftp[b] * S.tf[lc][3 * NF + a][c] + T.liftm[b] * S.tf[lc][2 * NF + a][c];
+            corr = fma(P.rhy, cy, corr);
+        }
+        u[c] = fma(P.dt, corr, u[c]);
+    }
+    if (P.mode == MODE_OP_F) {
+        store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
+        return;
+    }
+    double pts[C::PPT][M];
+    limit_block<DIM, N, PHYS>(P, B, S, lc, node, active, u, pts, true, true);
+    // a0 of the new state over its S_K points (next trial step, eq. numerical_experiment:CFL)
+    double amax = 0.0;
+#pragma unroll
+    for (int j = 0; j < C::PPT; ++j) {
+        int p = node + j * NN;
+        if (p < C::NSK && active)
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) amax = fmax(amax, speed_dir<PHYS, DIM>(P, pts[j], d));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if ((threadIdx.x & 31) == 0 && amax > 0.0) atomicMax(B.a0, dbits(amax));
+    store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
+}
+
+// Limiter applied to a state (set-up projection, operator checks): un -> unew.
+template <int DIM, int N, int PHYS>
+__global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_limit(Params P, Bufs B) {
+    using C = Cfg<DIM, N, PHYS>;
+    __shared__ Smem<C> S;
+    const int lc = threadIdx.x / C::NN, node = threadIdx.x - lc * C::NN;
+    const int cell = blockIdx.x * C::NCB + lc;
+    const bool active = cell < P.ncell;
+    double u[C::M], pts[C::PPT][C::M];
+    load_node<DIM, N, PHYS>(P, B.un, cell, node, active, u);
+    limit_block<DIM, N, PHYS>(P, B, S, lc, node, active, u, pts, false, false);
+    store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
+}
+
+// a0 over the S_K points of un, and the two smallest bound margins.
+template <int DIM, int N, int PHYS>
+__global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_scan(Params P, Bufs B) {
+    using C = Cfg<DIM, N, PHYS>;
+    constexpr int M = C::M, NN = C::NN;
+    __shared__ Smem<C> S;
+    const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
+    const int cell = blockIdx.x * C::NCB + lc;
+    const bool active = cell < P.ncell;
+    double u[M];
+    load_node<DIM, N, PHYS>(P, B.un, cell, node, active, u);
+#pragma unroll
+    for (int c = 0; c < M; ++c) S.u[lc][c][node] = u[c];
+    __syncthreads();
+    double amax = 0.0, m0 = INFINITY, m1 = INFINITY;
+#pragma unroll
+    for (int j = 0; j < C::PPT; ++j) {
+        int p = node + j * NN;
+        if (p < C::NSK && active) {
+            double v[M];
+            sk_eval<DIM, N, M, NN>(S.u[lc], p, v);
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) amax = fmax(amax, speed_dir<PHYS, DIM>(P, v, d));
+            double a0m, a1m;
+            if constexpr (PHYS == PH_EULER) {
+                a0m = v[0] - P.eps;
+                a1m = rho_e<DIM>(v) - P.eps;
+            } else {
+                a0m = v[0] - P.lo;
+                a1m = P.hi - v[0];
+            }
+            m0 = (a0m == a0m) ? fmin(m0, a0m) : -INFINITY;
+            m1 = (a1m == a1m) ? fmin(m1, a1m) : -INFINITY;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        m0 = fmin(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+        m1 = fmin(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (amax > 0.0) atomicMax(B.a0, dbits(amax));
+        atomicMin(&B.ord[0], ordbits(m0));
+        atomicMin(&B.ord[1], ordbits(m1));
+    }
+}
+
+// Cell averages of un -> aux[cell][m]
+template <int DIM, int N, int PHYS>
+__global__ void k_avg(Params P, Bufs B) {
+    using C = Cfg<DIM, N, PHYS>;
+    const NodalTables &T = c_tab[N - 2];
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P.ncell * C::M) return;
+    int cell = t / C::M, c = t - cell * C::M;
+    const double *u = B.un + ((size_t)c * P.ncell + cell) * C::NN;
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < C::NN; ++q) s = fma(DIM == 2 ? T.w2[q] : T.w1[q], u[q], s);
+    B.aux[t] = s;
+}
+
+template <int DIM, int N, int PHYS>
+cudaError_t launch_one(int kernel, int nblocks, cudaStream_t st, const Params &P, const Bufs &B) {
+    using C = Cfg<DIM, N, PHYS>;
+    switch (kernel) {
+    case K_INNER: k_inner<DIM, N, PHYS><<<nblocks, C::NT, 0, st>>>(P, B); break;
+    case K_FINAL: k_final<DIM, N, PHYS><<<nblocks, C::NT, 0, st>>>(P, B); break;
+    case K_LIMIT: k_limit<DIM, N, PHYS><<<nblocks, C::NT, 0, st>>>(P, B); break;
+    case K_A0:
+    case K_MARGINS: k_scan<DIM, N, PHYS><<<nblocks, C::NT, 0, st>>>(P, B); break;
+    case K_AVG: {
+        int tot = P.ncell * C::M;
+        k_avg<DIM, N, PHYS><<<(tot + 255) / 256, 256, 0, st>>>(P, B);
+        break;
+    }
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int DIM>
+cudaError_t launch_dim(int kernel, int n, int phys, int nblocks, cudaStream_t st, const Params &P,
+                       const Bufs &B) {
+#define CRKDG_CASE(NV, PV) \
+    if (n == NV && phys == PV) return launch_one<DIM, NV, PV>(kernel, nblocks, st, P, B);
+    CRKDG_CASE(2, PH_ADV) CRKDG_CASE(2, PH_BURG) CRKDG_CASE(2, PH_EULER)
+    CRKDG_CASE(3, PH_ADV) CRKDG_CASE(3, PH_BURG) CRKDG_CASE(3, PH_EULER)
+    CRKDG_CASE(4, PH_ADV) CRKDG_CASE(4, PH_BURG) CRKDG_CASE(4, PH_EULER)
+#undef CRKDG_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace crkdg

@@ -1,0 +1,90 @@
+// dg_types.h -- plain data shared by the host API and the kernels of the cRKDG
+// library (no device code here).  Nodal Q^k tables, step parameters and the
+// device buffer set one launch works on.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace crkdg {
+
+constexpr int MAXN = 4;  // nodes per direction (k <= 3)
+constexpr int MAXM = 4;  // conservative components (2D Euler)
+constexpr int MAXS = 4;  // Runge--Kutta stages
+
+enum Phys { PH_ADV = 0, PH_BURG = 1, PH_EULER = 2 };
+enum Bc { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECT = 2, BC_DIRICHLET = 3 };
+
+// Operator modes of the inner / final kernels.
+enum Mode {
+    MODE_STEP = 0,   // one limited cRKDG step (Scheme 1L)
+    MODE_OP_G = 1,   // inner kernel writes G(u) instead of the stage accumulation
+    MODE_OP_F = 2,   // final kernel adds the face correction only (no limiter, no checks)
+};
+
+__host__ __device__ constexpr int ncomp(int phys, int dim) { return phys == PH_EULER ? dim + 2 : 1; }
+// Gauss--Lobatto points of S_K: L = ceil((k+3)/2), the smallest rule exact for degree k.
+__host__ __device__ constexpr int nlob(int n) { return (n + 3) / 2; }
+__host__ __device__ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+// Cells per block of the thread-per-node kernels: whole warps of whole cells,
+// at least 128 threads.
+__host__ __device__ constexpr int warp_cells(int nn) { return nn * 32 / gcd_c(nn, 32); }  // lcm(nn, 32)
+__host__ __device__ constexpr int cells_per_block(int dim, int n) {
+    return (warp_cells(dim == 2 ? n * n : n) / (dim == 2 ? n * n : n)) *
+           (warp_cells(dim == 2 ? n * n : n) >= 128 ? 1 : 128 / warp_cells(dim == 2 ? n * n : n));
+}
+
+// One-dimensional nodal tables for n = k+1 Gauss points on [-1, 1].
+struct NodalTables {
+    double xg[MAXN], wg[MAXN];  // Gauss--Legendre nodes / weights (sum 2)
+    double xl[MAXN], wl[MAXN];  // Gauss--Lobatto nodes / weights
+    double Dhat[MAXN][MAXN];    // Dhat[a][q] = w_q l_a'(x_q) / w_a  (volume term)
+    double lm[MAXN], lp[MAXN];  // l_a(-1), l_a(+1)                 (traces)
+    double liftm[MAXN], liftp[MAXN];  // l_a(-1)/w_a, l_a(+1)/w_a    (lift)
+    double Igl[MAXN][MAXN];     // Igl[alpha][a] = l_a(xl_alpha)   (S_K interpolation)
+    double w1[MAXN];            // w_a / 2                          (1D average weights)
+    double w2[MAXN * MAXN];     // (w_a/2)(w_b/2) at node b*n+a      (2D average weights)
+};
+
+struct Params {
+    int nx, ny, ncell;
+    double rhx, rhy;  // 2/hx, 2/hy
+    double gamma, velx, vely;
+    double lo, hi, eps;
+    int bc[4];
+    double bcs[4][MAXM];
+    int s;
+    double A[MAXS][MAXS];
+    double b[MAXS];
+    int slot[MAXS];  // trace slot of stage i, -1 when b_i = 0
+    int nslot;
+    double dt;
+    int mode;
+};
+
+struct Bufs {
+    const double *un;   // u^n (nodal, state layout)
+    double *ustar;      // u^n + dt sum_i b_i G(u~^(i))   (or G(u) in MODE_OP_G)
+    double *unew;       // u^{n+1}
+    double *tr;         // face traces of u~^(i): [slot][m][cell][face point]
+    int *flag;          // set when a stage average leaves B
+    unsigned long long *nlim;   // limited cells
+    unsigned long long *thmin;  // bits of the smallest theta (non-negative double)
+    unsigned long long *a0;     // bits of the largest spectral radius (non-negative double)
+    double *aux;        // per-cell output of the utility kernels
+    unsigned long long *ord;    // two order-preserving mins (margins)
+};
+
+enum KernelId { K_INNER = 0, K_FINAL = 1, K_LIMIT = 2, K_A0 = 3, K_MARGINS = 4, K_AVG = 5 };
+
+}  // namespace crkdg
+
+// Per-dimension launchers (defined in dg_1d.cu / dg_2d.cu).
+extern "C++" {
+cudaError_t crkdg_upload_tables_1d(const crkdg::NodalTables *t);
+cudaError_t crkdg_upload_tables_2d(const crkdg::NodalTables *t);
+cudaError_t crkdg_launch_1d(int kernel, int n, int phys, int nblocks, cudaStream_t st,
+                            const crkdg::Params &P, const crkdg::Bufs &B);
+cudaError_t crkdg_launch_2d(int kernel, int n, int phys, int nblocks, cudaStream_t st,
+                            const crkdg::Params &P, const crkdg::Bufs &B);
+}

@@ -113,13 +113,11 @@ def euler_blast_tube(nx=4096, k=2, cfl=0.178, t_end=6.0, gamma=GAMMA):
 
 def sedov(n=2048, k=3, cfl=0.103, t_end=1.0, gamma=GAMMA, p_ambient=1e-13):
     dom = (0.0, 1.1, 0.0, 1.1)
-    X, Y = node_coords(2, n, n, k, dom)
     dx = 1.1 / n
-    rho = np.ones_like(X)
-    E = np.full_like(X, p_ambient / (gamma - 1.0))
-    E[0, 0] = 0.244816 / (dx * dx)
-    zero = np.zeros_like(X)
-    U = np.stack([rho, zero, zero, E])
+    U = np.zeros((4, n, n, k + 1, k + 1))
+    U[0] = 1.0
+    U[3] = p_ambient / (gamma - 1.0)
+    U[3, 0, 0] = 0.244816 / (dx * dx)  # the corner cell carries the blast energy
     return Workload("sedov2d", 2, n, n, k, dom, "euler",
                     ("reflect", "outflow", "reflect", "outflow"), np.ascontiguousarray(U),
                     gamma=gamma, eps=1e-13, cfl=cfl, t_end=t_end,

@@ -1,0 +1,75 @@
+"""The C-ABI library builds, loads and exports every entry point declared in include/*.h.
+No compute calls (no GPU needed)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(crkdg_[a-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2412_16002_gb300 import build
+
+    path = build()
+    return ctypes.CDLL(path)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 14
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header():
+    from paper_2412_16002_gb300 import _lib
+
+    assert _declared() <= set(_lib.SYMBOLS), _declared() - set(_lib.SYMBOLS)
+
+
+def test_product_package_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2412_16002_gb300")
+    for path in glob.glob(os.path.join(pkg, "**", "*"), recursive=True):
+        if path.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+            text = open(path).read()
+            assert "import oracle" not in text and "from oracle" not in text, path
+            assert "crkdg_oracle" not in text and "liborc" not in text, path
+
+
+def test_options_default_and_create_argument_checks(lib):
+    """Host-side validation runs before any device call."""
+    from paper_2412_16002_gb300 import _lib as L
+
+    L._lib = None
+    lib2 = L.load()
+    opt = L.Options()
+    lib2.crkdg_options_default(ctypes.byref(opt))
+    assert opt.max_halvings == 20 and opt.precision == 0 and abs(opt.tvb_M - 10.0) < 1e-15
+    h = ctypes.c_void_p()
+    mesh = L.Mesh()
+    mesh.dim, mesh.nx, mesh.ny, mesh.x0, mesh.x1 = 1, 8, 1, 0.0, 1.0
+    fl = L.Flux(L.FLUX["euler"], 1.4, (ctypes.c_double * 2)(0.0, 0.0))
+    bd = L.Bounds(0.0, 1.0, 1e-13)
+    # wrong m for 1D Euler, k out of range, bad periodic pairing
+    assert lib2.crkdg_create(ctypes.byref(mesh), 2, 4, ctypes.byref(fl), ctypes.byref(bd), None, ctypes.byref(h)) == L.E_ARG
+    assert lib2.crkdg_create(ctypes.byref(mesh), 4, 3, ctypes.byref(fl), ctypes.byref(bd), None, ctypes.byref(h)) == L.E_UNSUPPORTED
+    assert lib2.crkdg_create(ctypes.byref(mesh), 0, 3, ctypes.byref(fl), ctypes.byref(bd), None, ctypes.byref(h)) == L.E_ARG
+    mesh.bc[0], mesh.bc[1] = 0, 1
+    assert lib2.crkdg_create(ctypes.byref(mesh), 2, 3, ctypes.byref(fl), ctypes.byref(bd), None, ctypes.byref(h)) == L.E_ARG
+    assert lib2.crkdg_destroy(None) == L.OK
+    assert lib2.crkdg_state_size(None) == 0
