@@ -24,10 +24,13 @@
  *   - the LF viscosity alpha on an edge is the maximum over that edge's
  *     quadrature points of the spectral radius of both traces;
  *   - a0 (Sec. 2.1 notation) is the maximum over all S_K points;
- *   - theta is only computed from a bound that is violated (0/0 avoided), and
- *     after scaling the limited polynomial is re-evaluated on S_K; if rounding
- *     left a point outside the bound, theta is shrunk by (1-2^-40), (1-2^-30),
- *     (1-2^-20), (1-2^-10) in turn and finally set to 0;
+ *   - theta is only computed from a bound that is violated (0/0 avoided); every
+ *     theta below 1 is multiplied by (1-2^-40), a relative safety margin so that
+ *     the rescaled polynomial stays inside the bound after rounding; the limited
+ *     polynomial is then re-evaluated on S_K and, if rounding still left a point
+ *     outside, the final scaling towards the average (theta, or theta_2 applied
+ *     to every component for Euler) is multiplied by (1-2^-30), (1-2^-20),
+ *     (1-2^-10) in turn and finally set to 0;
  *   - the Euler energy limiter enforces rho*e >= eps, exactly as eq.
  *     (Euler-limiter2) is written, and the admissibility test of the cell
  *     averages uses the same predicate.
@@ -491,11 +494,13 @@ static void scale_cell(const orc_problem *P, const double *src, double *dst, int
     for (int i = 1; i < P->nmodes; ++i) b[i] = theta * a[i];
 }
 
-static const double shrink_factors[4] = {
-    1.0 - 9.094947017729282e-13, /* 1 - 2^-40 */
+/* safety margin applied to every theta < 1, then the retry factors */
+static const double margin_factor = 1.0 - 9.094947017729282e-13; /* 1 - 2^-40 */
+static const double retry_factors[4] = {
     1.0 - 9.313225746154785e-10, /* 1 - 2^-30 */
     1.0 - 9.5367431640625e-07,   /* 1 - 2^-20 */
     1.0 - 0.0009765625,          /* 1 - 2^-10 */
+    0.0,
 };
 
 static double safe_ratio(double num, double den) {
@@ -527,9 +532,10 @@ long long orc_limit(const orc_problem *P, double *c, double *theta_out) {
             if (Mk > P->hi) { double t1 = safe_ratio(P->hi - ub, Mk - ub); if (t1 < th) th = t1; }
             if (mk < P->lo) { double t2 = safe_ratio(ub - P->lo, ub - mk); if (t2 < th) th = t2; }
             if (th < 1.0) {
+                th *= margin_factor;
                 double tha = th;
-                for (int attempt = 0; attempt <= 5; ++attempt) {
-                    tha = attempt == 0 ? th : (attempt <= 4 ? th * shrink_factors[attempt - 1] : 0.0);
+                for (int attempt = 0; attempt <= 4; ++attempt) {
+                    tha = attempt == 0 ? th : th * retry_factors[attempt - 1];
                     scale_cell(P, c, trial, cell, 0, tha);
                     int ok = 1;
                     for (int p = 0; p < np && ok; ++p) {
@@ -553,20 +559,8 @@ long long orc_limit(const orc_problem *P, double *c, double *theta_out) {
             }
             double th1 = 1.0;
             if (rmin < eps) {
-                th1 = safe_ratio(rb - eps, rb - rmin);
-                double tha = th1;
-                for (int attempt = 0; attempt <= 5; ++attempt) {
-                    tha = attempt == 0 ? th1 : (attempt <= 4 ? th1 * shrink_factors[attempt - 1] : 0.0);
-                    scale_cell(P, c, trial, cell, 0, tha);
-                    int ok = 1;
-                    for (int p = 0; p < np && ok; ++p) {
-                        double v = eval_modal(P, cell_coef(P, trial, cell, 0), xs[p], ys[p]);
-                        if (!(v >= eps)) ok = 0;
-                    }
-                    if (ok) break;
-                }
-                scale_cell(P, c, c, cell, 0, tha);
-                th1 = tha;
+                th1 = safe_ratio(rb - eps, rb - rmin) * margin_factor;
+                scale_cell(P, c, c, cell, 0, th1);
             }
             /* eq. (Euler-limiter2): internal energy rho*e with the limited density */
             double ubar[ORC_MAXM];
@@ -580,11 +574,12 @@ long long orc_limit(const orc_problem *P, double *c, double *theta_out) {
                 if (!(re >= remin)) remin = re; /* NaN propagates as a violation */
             }
             double th2 = 1.0;
-            if (!(remin >= eps)) {
-                th2 = safe_ratio(reb - eps, reb - remin);
+            if (!(remin >= eps)) th2 = safe_ratio(reb - eps, reb - remin) * margin_factor;
+            if (th1 < 1.0 || th2 < 1.0) {
+                /* verify rho >= eps and rho e >= eps on S_K; shrink the final scaling */
                 double tha = th2;
-                for (int attempt = 0; attempt <= 5; ++attempt) {
-                    tha = attempt == 0 ? th2 : (attempt <= 4 ? th2 * shrink_factors[attempt - 1] : 0.0);
+                for (int attempt = 0; attempt <= 4; ++attempt) {
+                    tha = attempt == 0 ? th2 : th2 * retry_factors[attempt - 1];
                     for (int comp = 0; comp < m; ++comp) scale_cell(P, c, trial, cell, comp, tha);
                     int ok = 1;
                     for (int p = 0; p < np && ok; ++p) {

@@ -240,13 +240,16 @@ __device__ __forceinline__ bool point_ok(const Params &P, const double *v) {
 
 // ----------------------------------------------------------------------------- limiter
 
-// shrink factors of the rounding safety rule: 1-2^-40, 1-2^-30, 1-2^-20, 1-2^-10
-__device__ __forceinline__ double shrink_factor(int attempt) {
+// Rounding safety of the limiter: every theta below 1 is multiplied by
+// (1-2^-40) so the rescaled polynomial lands strictly inside the bound; if the
+// re-evaluation on S_K still finds a point outside, the final scaling towards
+// the average is multiplied by the retry factors 1-2^-30, 1-2^-20, 1-2^-10, 0.
+constexpr double kMargin = 1.0 - 9.094947017729282e-13;
+__device__ __forceinline__ double retry_factor(int attempt) {
     switch (attempt) {
-    case 1: return 1.0 - 9.094947017729282e-13;
-    case 2: return 1.0 - 9.313225746154785e-10;
-    case 3: return 1.0 - 9.5367431640625e-07;
-    case 4: return 1.0 - 0.0009765625;
+    case 1: return 1.0 - 9.313225746154785e-10;
+    case 2: return 1.0 - 9.5367431640625e-07;
+    case 3: return 1.0 - 0.0009765625;
     default: return 0.0;
     }
 }
@@ -309,7 +312,7 @@ __device__ void limit_block(const Params &P, const Bufs &B, Smem<Cfg<DIM, N, PHY
             if (mx > P.hi) th = fmin(th, ratio01(P.hi - ub[0], mx - ub[0]));
             if (mn < P.lo) th = fmin(th, ratio01(ub[0] - P.lo, ub[0] - mn));
         }
-        S.th[lc][0] = th;
+        S.th[lc][0] = th < 1.0 ? th * kMargin : th;
         S.th[lc][1] = 1.0;
         S.bad[lc] = 0;
     }
@@ -337,7 +340,7 @@ __device__ void limit_block(const Params &P, const Bufs &B, Smem<Cfg<DIM, N, PHY
             double mn = INFINITY;
             for (int q = 0; q < NN; ++q) mn = fmin(mn, S.red[lc][q][1]);
             double reb = rho_e<DIM>(ub);
-            S.th[lc][1] = (mn >= P.eps) ? 1.0 : ratio01(reb - P.eps, reb - mn);
+            S.th[lc][1] = (mn >= P.eps) ? 1.0 : ratio01(reb - P.eps, reb - mn) * kMargin;
         }
         __syncthreads();
         th2 = S.th[lc][1];
@@ -364,7 +367,7 @@ __device__ void limit_block(const Params &P, const Bufs &B, Smem<Cfg<DIM, N, PHY
     //    rounding violation (the final scaling factor towards the average)
     bool any_limited = __syncthreads_or(limited);
     if (any_limited) {
-        for (int attempt = 0; attempt <= 5; ++attempt) {
+        for (int attempt = 0; attempt <= 4; ++attempt) {
 #pragma unroll
             for (int c = 0; c < M; ++c) S.u[lc][c][node] = u[c];
             __syncthreads();
@@ -381,19 +384,14 @@ __device__ void limit_block(const Params &P, const Bufs &B, Smem<Cfg<DIM, N, PHY
             }
             if (viol) S.bad[lc] = 1;
             bool again = __syncthreads_or(viol);
-            if (!again || attempt == 5) break;
+            if (!again || attempt == 4) break;
             bool mine = S.bad[lc] != 0;
             __syncthreads();
             if (node == 0) S.bad[lc] = 0;
             if (mine) {
-                double f = shrink_factor(attempt + 1);
-                if constexpr (PHYS == PH_EULER) {
-                    tfin = th2 * f;
-                    apply(tfin);
-                } else {
-                    tfin = th2 * f;  // th2 == 1 for scalars: the factor multiplies theta
-                    apply(tfin);
-                }
+                // Euler: theta_2 (all components); scalars: th2 == 1 so the factor multiplies theta
+                tfin = th2 * retry_factor(attempt + 1);
+                apply(tfin);
             }
         }
     }

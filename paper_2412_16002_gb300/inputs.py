@@ -124,6 +124,36 @@ def sedov(n=2048, k=3, cfl=0.103, t_end=1.0, gamma=GAMMA, p_ambient=1e-13):
                     tableau="rk4" if k == 3 else "heun3")
 
 
+def scenario2(n=16, k=2, gamma=GAMMA):
+    """Smooth exact Euler solution rho = 0.99 sin(pi(x+y)) + 1, w = (1,1), p = 1 (Example 4.2,
+    scenario II) on the periodic square [0,2]^2, where it is periodic."""
+    dom = (0.0, 2.0, 0.0, 2.0)
+    X, Y = node_coords(2, n, n, k, dom)
+    rho = 0.99 * np.sin(np.pi * (X + Y)) + 1.0
+    U = prim_to_cons(rho, (1.0, 1.0), np.ones_like(rho), gamma)
+    return Workload("euler2d_scenario2", 2, n, n, k, dom, "euler", ("periodic",) * 4, np.ascontiguousarray(U),
+                    gamma=gamma, eps=1e-13, cfl=0.1, t_end=0.1024, tableau="rk4" if k == 3 else "heun3")
+
+
+def sedov_shell(n=2048, k=3, radius=0.3, gamma=GAMMA, p_ambient=1e-13):
+    """Sedov-type blast some time after ignition: a dense shell of radius `radius` around the
+    corner with hot low-density gas inside and the cold ambient state (p = 1e-13) outside,
+    flowing radially; same domain and boundaries as ``sedov``."""
+    dom = (0.0, 1.1, 0.0, 1.1)
+    X, Y = node_coords(2, n, n, k, dom)
+    r = np.sqrt(X * X + Y * Y)
+    inside = r < radius
+    shell = np.exp(-((r - radius) / (0.03 * radius)) ** 2)
+    rho = np.where(inside, 0.2 + 5.0 * shell, 1.0 + 4.0 * shell)
+    p = np.where(inside, 0.5 * (1.0 + shell), p_ambient + 0.5 * shell)
+    speed = 1.5 * shell * (r / radius)
+    rr = np.maximum(r, 1e-12)
+    U = prim_to_cons(rho, (speed * X / rr, speed * Y / rr), p, gamma)
+    return Workload("sedov2d_shell", 2, n, n, k, dom, "euler", ("reflect", "outflow", "reflect", "outflow"),
+                    np.ascontiguousarray(U), gamma=gamma, eps=1e-13, cfl=0.103, t_end=1.0,
+                    tableau="rk4" if k == 3 else "heun3")
+
+
 def riemann_states(seed):
     """Four quadrant states (rho, wx, wy, p): rho~U[0.1,2], p~U[0.01,2], |w|<1 (disc)."""
     rng = np.random.default_rng(seed)
