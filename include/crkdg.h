@@ -183,6 +183,41 @@ size_t crkdg_state_size(crkdg_t h);
 /* Human-readable description of the last error on h (static string if h is NULL). */
 const char *crkdg_last_error(crkdg_t h);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free DG operator.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc -- code that runs while a
+ * CUDA graph is being captured or inside another framework's memory pool,
+ * plug-ins whose host forbids allocation after start-up, and real-time loops
+ * where an allocation could stall or fail.  It needs no handle.
+ *
+ * out_dev = F(in_dev) (the DG operator with the Lax--Friedrichs flux and the
+ * mesh's boundary conditions), exactly what crkdg_apply_operator(h,
+ * CRKDG_OP_F, ...) returns for the same mesh, k and flux.  in_dev and out_dev
+ * are caller-owned device arrays in the state layout; they may not alias.
+ *
+ * Scratch: the interior-trace accumulation and the face traces live in one
+ * library-owned static device array of CRKDG_NOALLOC_SCRATCH_DOUBLES doubles
+ * (32 MiB), which every GPU that loads the library keeps until the process
+ * exits.  A mesh needing more than m * cells * (n^dim + 2*dim*n^(dim-1))
+ * doubles beyond that limit is rejected with CRKDG_E_ARG (e.g. 2D Euler Q^3
+ * fits up to 32768 cells, 1D Euler P^2 up to 279620 cells).  Every word of the
+ * scratch that a call reads is written earlier in the same call, so nothing
+ * needs clearing; the array keeps the last call's contents.  All calls share
+ * the one array: calls whose kernels overlap on the GPU (on different streams
+ * or from different threads without ordering) race and give wrong results.
+ *
+ * The first call on each device does a one-time set-up with that device
+ * current: it looks up the array's device address (cudaGetSymbolAddress) and
+ * uploads the nodal tables (cudaMemcpyToSymbol).  Make that first call before
+ * any stream capture.  Afterwards the call only enqueues two kernels on
+ * cuda_stream (NULL: the legacy default stream) and returns without
+ * synchronising.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ * Errors: CRKDG_E_ARG (bad mesh, kinds, pointers, or beyond the scratch size),
+ * CRKDG_E_UNSUPPORTED (k > 3), CRKDG_E_CUDA (set-up or launch failed). */
+#define CRKDG_NOALLOC_SCRATCH_DOUBLES (1 << 22)
+crkdg_status crkdg_apply_F_noalloc(const crkdg_mesh *mesh, int k, int m, const crkdg_flux *flux,
+                                   const double *in_dev, double *out_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

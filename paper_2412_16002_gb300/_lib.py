@@ -76,6 +76,8 @@ SYMBOLS = {
     "crkdg_kernel_times": (C.c_int, [_H, _dp, C.POINTER(C.c_longlong)]),
     "crkdg_state_size": (C.c_size_t, [_H]),
     "crkdg_last_error": (C.c_char_p, [_H]),
+    "crkdg_apply_F_noalloc": (C.c_int, [C.POINTER(Mesh), C.c_int, C.c_int, C.POINTER(Flux), C.c_void_p,
+                                        C.c_void_p, C.c_void_p]),
 }
 
 
