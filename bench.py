@@ -36,6 +36,7 @@ WORKLOADS = {
     "euler1d_blast_tube_4096_p2": dict(kind="euler1d", nx=4096, k=2),
     "burgers_sine_200_p2": dict(kind="burgers", nx=200, k=2),
     "sedov_2048_q3": dict(kind="sedov", nx=2048, k=3),
+    "sedov_512_q3": dict(kind="sedov", nx=512, k=3),
     "riemann_1024_q2": dict(kind="riemann", nx=1024, k=2),
 }
 DEFAULT = "euler1d_blast_tube_4096_p2"

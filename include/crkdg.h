@@ -135,9 +135,12 @@ crkdg_status crkdg_set_state(crkdg_t h, const double *nodal, size_t count, int o
 /* Copy the current nodal state out (host or device pointer). */
 crkdg_status crkdg_get_state(crkdg_t h, double *nodal, size_t count, int on_device);
 
-/* Trial step of eq. (numerical_experiment:CFL): *dt = cfl * dx / a0, with a0
- * the largest spectral radius |w.nu| + c (|u| for Burgers, |a.nu| for
- * advection) over all S_K points of the current state. */
+/* Trial step of eq. (numerical_experiment:CFL), *dt = cfl * dx / a0, written for
+ * Cartesian meshes as *dt = cfl / max_{S_K} sum_d lambda_d / h_d, where
+ * lambda_d = |w_d| + c (|u| for Burgers, |a_d| for advection) is the spectral
+ * radius in direction d at an S_K point of the current state and h_d the cell
+ * size (in 1D exactly cfl*dx/a0; in 2D the form under which the stability CFL
+ * numbers of the Remark in Sec. 3.2 keep the scheme linearly stable). */
 crkdg_status crkdg_max_dt(crkdg_t h, double cfl, double *dt);
 
 /* One limited cRKDG step of size dt (restarting with dt/2 while any stage's

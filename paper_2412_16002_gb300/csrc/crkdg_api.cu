@@ -416,13 +416,8 @@ crkdg_status crkdg_max_dt(crkdg_t h, double cfl, double *dt) {
             crkdg_status s = compute_a0(h);
             if (s) return s;
         }
-        double hx = (h->mesh.x1 - h->mesh.x0) / h->mesh.nx;
-        double dx = hx;
-        if (h->dim == 2) {
-            double hy = (h->mesh.y1 - h->mesh.y0) / h->mesh.ny;
-            if (hy < dx) dx = hy;
-        }
-        *dt = h->a0 > 0.0 ? cfl * dx / h->a0 : INFINITY;
+        // h->a0 holds max over S_K points of sum_d lambda_d / h_d
+        *dt = h->a0 > 0.0 ? cfl / h->a0 : INFINITY;
         return CRKDG_OK;
     } catch (...) {
         return CRKDG_E_OOM;

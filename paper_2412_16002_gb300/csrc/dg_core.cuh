@@ -115,6 +115,15 @@ __device__ __forceinline__ double speed_dir(const Params &P, const double *u, in
     }
 }
 
+// Trial-step rate at one point: sum over directions of lambda_d / h_d, so that
+// dt = CFL / max rate (eq. numerical_experiment:CFL, directional radii summed in 2D).
+template <int PHYS, int DIM>
+__device__ __forceinline__ double sk_rate(const Params &P, const double *u) {
+    double r = speed_dir<PHYS, DIM>(P, u, 0) * (0.5 * P.rhx);
+    if constexpr (DIM == 2) r = fma(speed_dir<PHYS, DIM>(P, u, 1), 0.5 * P.rhy, r);
+    return r;
+}
+
 // rho e = E - |m|^2 / (2 rho)   (eq. Euler-limiter2)
 template <int DIM>
 __device__ __forceinline__ double rho_e(const double *u) {
@@ -665,14 +674,12 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_final(Params P, Bufs 
     }
     double pts[C::PPT][M];
     limit_block<DIM, N, PHYS>(P, B, S, lc, node, active, u, pts, true, true);
-    // a0 of the new state over its S_K points (next trial step, eq. numerical_experiment:CFL)
+    // wave-speed rate of the new state over its S_K points (next trial step)
     double amax = 0.0;
 #pragma unroll
     for (int j = 0; j < C::PPT; ++j) {
         int p = node + j * NN;
-        if (p < C::NSK && active)
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) amax = fmax(amax, speed_dir<PHYS, DIM>(P, pts[j], d));
+        if (p < C::NSK && active) amax = fmax(amax, sk_rate<PHYS, DIM>(P, pts[j]));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
@@ -716,7 +723,7 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_scan(Params P, Bufs B
             double v[M];
             sk_eval<DIM, N, M, NN>(S.u[lc], p, v);
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) amax = fmax(amax, speed_dir<PHYS, DIM>(P, v, d));
+            amax = fmax(amax, sk_rate<PHYS, DIM>(P, v));
             double a0m, a1m;
             if constexpr (PHYS == PH_EULER) {
                 a0m = v[0] - P.eps;

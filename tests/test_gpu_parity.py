@@ -115,14 +115,17 @@ def _run_pair(g, o, steps, cfl, tab, t_end=math.inf):
     return t
 
 
-@pytest.mark.parametrize("name", ["burgers200", "euler1d_4096", "scenario2_q2", "scenario2_q3"])
+@pytest.mark.parametrize("name", ["burgers200", "euler1d_4096", "scenario2_q2", "scenario2_q3", "riemann32_q2"])
 def test_hundred_steps(name):
     """100 steps (Burgers 200 P2 and the 4096-cell 1D blast tube at full size; smooth 2D
-    Euler): rel L-inf <= 1e-10, bounds exact at every step, identical restarts."""
+    Euler; a 32x32 four-quadrant Riemann problem): rel L-inf <= 1e-10, bounds exact at
+    every step, identical restarts."""
     if name == "burgers200":
         wl = inputs.burgers_sine(200, 2)
     elif name == "euler1d_4096":
         wl = inputs.euler_blast_tube(4096, 2)
+    elif name == "riemann32_q2":
+        wl = inputs.riemann_quadrants(0, 32, 2)
     else:
         wl = inputs.scenario2(12, 2 if name.endswith("q2") else 3)
     g, o = pair_from_workload(wl)
@@ -137,13 +140,13 @@ def test_hundred_steps(name):
             assert abs(g.mass(c) - m0[c]) < 1e-13 * max(1.0, abs(m0[c]))
 
 
-@pytest.mark.parametrize("name,horizon,total", [("sedov32_q3", 15, 40), ("riemann32_q2", 12, 60)])
+@pytest.mark.parametrize("name,horizon,total", [("sedov32_q3", 20, 60)])
 def test_shock_workloads_horizon_and_envelope(name, horizon, total):
-    """The 2D shock workloads (no anti-oscillation limiter, near-vacuum states) are chaotic
-    under rounding: the oracle against itself with a 1e-16 relative input perturbation
-    departs beyond 1e-10 after ~15-20 steps.  Parity is therefore 1e-10 up to the horizon;
-    afterwards the GPU-oracle gap must stay inside 100x that self-perturbation envelope,
-    with exact bounds and identical restarts at every step."""
+    """The Sedov-type blast (a single hot cell in a near-vacuum-energy ambient state, no
+    anti-oscillation limiter) is sensitive to rounding: the oracle against itself with a
+    1e-16 relative input perturbation reaches ~1e-10 by step 30 and stays there.  Parity
+    is 1e-10 up to step 20; afterwards the GPU-oracle gap must stay inside 100x that
+    self-perturbation envelope, with exact bounds and identical restarts at every step."""
     from gpu_helpers import ORACLE_TABS
     from oracle import Oracle
 
