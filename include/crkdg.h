@@ -97,6 +97,22 @@ typedef struct {
     const double *b;
 } crkdg_tableau;
 
+/* Precision.  CRKDG_PREC_FP64: every operation in FP64.  CRKDG_PREC_MIXED: the
+ * state is kept as FP64 cell averages plus FP32 nodal deviations; every operator
+ * (flux, volume term, traces, Lax--Friedrichs flux, lift) is evaluated in FP32,
+ * while the cell-average updates (FP64 sums of the face fluxes, so conservation
+ * holds to FP64 round-off), the admissibility test of the averages, the limiter's
+ * theta (FP32-screened with a rigorous rounding margin, FP64 where the screen
+ * cannot clear a cell) and the time step stay FP64.  Bounds are exact under the
+ * FP64 evaluation ubar + (double)(FP32 interpolation of the deviations). */
+/* Troubled-cell indicator (optional; the paper applies no anti-oscillation
+ * limiter, Sec. 4).  CRKDG_IND_TVB: once per step, after the final stage and
+ * before the scaling limiter (so inner stages stay compact), every cell whose
+ * face-averaged trace deviations a TVB-modified minmod (threshold tvb_M h^2, per
+ * conservative component and direction, against the differences of the
+ * neighbouring averages) would change is replaced by its average plus minmod-
+ * limited first Legendre moments; averages are kept, and the scaling limiter
+ * follows unchanged.  Euler, FP64 path. */
 typedef struct {
     int precision;      /* CRKDG_PREC_FP64 (default) or CRKDG_PREC_MIXED */
     int max_halvings;   /* restart cap of the Sec. 4.1 loop (default 20) */
@@ -148,11 +164,21 @@ crkdg_status crkdg_max_dt(crkdg_t h, double cfl, double *dt);
  * CRKDG_E_BOUNDS leaves the state at u^n. */
 crkdg_status crkdg_step(crkdg_t h, double dt, const crkdg_tableau *tab, crkdg_step_info *info);
 
-/* Run up to nsteps steps, each of size min(cfl*dx/a0, t_end - *t), advancing
- * *t; stops early when *t reaches t_end.  *steps_done (nullable) receives the
- * number of accepted steps and *restarts (nullable) the total halvings. */
+/* Run up to nsteps steps, each of size min(trial step of crkdg_max_dt, t_end - *t),
+ * advancing *t; stops early when *t reaches t_end.  *steps_done (nullable)
+ * receives the number of accepted steps and *restarts (nullable) the total
+ * halvings.  On 1D meshes the whole loop (steps, restarts, trial steps) runs in
+ * one persistent cooperative kernel launch with one grid-wide barrier per
+ * attempt; CRKDG_E_TIMEOUT reports an expired barrier wait (2 s bound) and
+ * CRKDG_E_BOUNDS leaves the state at the last accepted step. */
 crkdg_status crkdg_advance(crkdg_t h, int nsteps, double cfl, double t_end,
                            const crkdg_tableau *tab, double *t, int *steps_done, int *restarts);
+
+/* As crkdg_advance with the fixed trial step dt for every step (the step is
+ * still halved and redone while a stage's averages leave B; the next step
+ * starts again from dt), as in the convergence tests of Sec. 4.2. */
+crkdg_status crkdg_advance_fixed(crkdg_t h, int nsteps, double dt, double t_end, const crkdg_tableau *tab,
+                                 double *t, int *steps_done, int *restarts);
 
 /* Operator evaluation on device arrays in the state layout, for verification:
  * op 0: out = G(in) (Sec. 2.1), op 1: out = F(in) (eq. dxDG; boundary data at
@@ -160,6 +186,41 @@ crkdg_status crkdg_advance(crkdg_t h, int nsteps, double cfl, double t_end,
  * test).  in and out are device pointers of state size; they may not alias. */
 enum { CRKDG_OP_G = 0, CRKDG_OP_F = 1, CRKDG_OP_LIMIT = 2 };
 crkdg_status crkdg_apply_operator(crkdg_t h, int op, const double *in_dev, double *out_dev);
+
+/* Troubled-cell flags of the last accepted step (one int per cell, row-major
+ * [ny][nx]; host or device pointer).  CRKDG_E_ARG if the indicator is off. */
+crkdg_status crkdg_troubled_flags(crkdg_t h, int *flags, int on_device);
+
+/* ------------------------------------------------------------------------
+ * Learned troubled-cell indicator (CRKDG_IND_MLP; not part of the paper).  A
+ * 44 -> 64 -> 64 -> 1 ReLU network with a sigmoid output classifies a cell from
+ * its features: per conservative component the 3x3 neighbourhood of cell
+ * averages normalised by the stencil mean and range, and the cell's first
+ * Legendre moments over the same range (2D Euler).  A cell is troubled when the
+ * probability exceeds 0.6, smooth below 0.4, and takes the plain TVB decision in
+ * between; the shock limiter and the scaling limiter then act as for the plain
+ * indicator.  Parameters are FP32, layout W1[64][44], b1[64], W2[64][64], b2[64],
+ * w3[64], b3 (CRKDG_MLP_NPARAM floats).  All pointers below are device pointers. */
+#define CRKDG_MLP_NIN 44
+#define CRKDG_MLP_NH 64
+#define CRKDG_MLP_NPARAM 7105
+
+/* prob[r] = network(X[r]) for the n rows of X ([n][44]); enqueued on stream. */
+crkdg_status crkdg_mlp_forward(const float *params, const float *X, int n, float *prob, void *stream);
+/* grad += d loss / d params and *loss += loss, for the mean binary cross-entropy
+ * of the n labelled rows (y in {0,1}); the caller zeroes grad and loss. */
+crkdg_status crkdg_mlp_grad(const float *params, const float *X, const float *y, int n, float *grad, float *loss,
+                            void *stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8); step is the 1-based count. */
+crkdg_status crkdg_mlp_adam(float *params, float *m, float *v, const float *grad, int step, float lr, void *stream);
+
+/* Copy the network the CRKDG_IND_MLP indicator of h uses (params: device). */
+crkdg_status crkdg_set_mlp(crkdg_t h, const float *params);
+/* While on (indicator on), every step also keeps the features of the unlimited
+ * final-stage state on which its indicator decided; crkdg_last_features copies
+ * them ([ny][nx][44] floats), matching crkdg_troubled_flags of the same step. */
+crkdg_status crkdg_set_harvest(crkdg_t h, int on);
+crkdg_status crkdg_last_features(crkdg_t h, float *feat, int on_device);
 
 /* Cell averages of the current state, [ny][nx][m] doubles (host or device). */
 crkdg_status crkdg_cell_averages(crkdg_t h, double *avg, int on_device);
@@ -173,12 +234,20 @@ crkdg_status crkdg_bound_margins(crkdg_t h, double margins[2]);
 crkdg_status crkdg_total_mass(crkdg_t h, int comp, double *mass);
 
 /* Kernel timing for measurement.  While on, crkdg_step brackets its
- * inner-stage and final-stage launches with CUDA events on the library's
- * stream and accumulates their durations; crkdg_kernel_times returns the
- * milliseconds {inner, final} and the launch counts since profiling was last
+ * inner-stage and final-stage launches, and crkdg_advance on 1D meshes its
+ * persistent step-loop launch, with CUDA events on the library's stream and
+ * accumulates their durations; crkdg_kernel_times returns the milliseconds
+ * {inner, final, step loop} and the launch counts since profiling was last
  * switched on.  Off by default; switching on resets the totals. */
 crkdg_status crkdg_set_profiling(crkdg_t h, int on);
-crkdg_status crkdg_kernel_times(crkdg_t h, double ms[2], long long launches[2]);
+crkdg_status crkdg_kernel_times(crkdg_t h, double ms[3], long long launches[3]);
+
+/* Testing aid for the failure path of the device-resident loop: with extra > 0
+ * the grid barrier of crkdg_advance (1D) waits for `extra` blocks that never
+ * arrive, so every block's bounded wait expires after 2 s and the call returns
+ * CRKDG_E_TIMEOUT with the state at the last accepted step (nothing faults or
+ * hangs).  0 (the default) restores normal operation. */
+crkdg_status crkdg_set_barrier_test(crkdg_t h, int extra);
 
 /* Number of doubles of the state. */
 size_t crkdg_state_size(crkdg_t h);

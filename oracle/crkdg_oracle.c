@@ -35,6 +35,20 @@
  *   - the Euler energy limiter enforces rho*e >= eps, exactly as eq.
  *     (Euler-limiter2) is written, and the admissibility test of the cell
  *     averages uses the same predicate.
+ *
+ * Optional, not part of the paper's method (which applies no anti-oscillation
+ * limiter, Sec. 4): a plain troubled-cell indicator and shock limiter, applied
+ * once per step after the final stage and before the scaling limiter so that the
+ * inner stages stay compact:
+ *   - per conservative component and direction, with face-averaged traces
+ *     ut_R = avg_face(u_R) - ubar and ut_L = ubar - avg_face(u_L) and the neighbour
+ *     differences D+ = ubar_{K+1} - ubar_K, D- = ubar_K - ubar_{K-1}, the cell is
+ *     troubled if the TVB-modified minmod m~(a, D+, D-) (= a when |a| <= M h^2,
+ *     else minmod) changes ut_R or ut_L;
+ *   - a troubled cell is replaced by ubar + minmod(c_x, D+x, D-x) P_1(xi)
+ *     + minmod(c_y, D+y, D-y) P_1(eta) (its first Legendre moments limited, every
+ *     higher mode dropped), which keeps the average;
+ *   - neighbour averages across the boundary follow the boundary condition.
  */
 #include "crkdg_oracle.h"
 
@@ -159,6 +173,8 @@ orc_problem *orc_create(int dim, int nx, int ny, int k, double x0, double x1, do
     }
     P->limiter_on = 1;
     P->max_halvings = 20;
+    P->indicator = 0;
+    P->tvb_M = 10.0;
     orc_gauss_legendre(P->n, P->xg, P->wg);
     orc_gauss_lobatto(P->L, P->xl, P->wl);
     return P;
@@ -174,6 +190,11 @@ void orc_set_exact(orc_problem *P, orc_exact_fn fn, void *ctx) {
 void orc_set_options(orc_problem *P, int limiter_on, int max_halvings) {
     P->limiter_on = limiter_on;
     P->max_halvings = max_halvings;
+}
+
+void orc_set_indicator(orc_problem *P, int on, double tvb_M) {
+    P->indicator = on;
+    P->tvb_M = tvb_M;
 }
 
 size_t orc_state_size(const orc_problem *P) { return (size_t)P->ncell * P->m * P->nmodes; }
@@ -676,6 +697,88 @@ double orc_max_dt(const orc_problem *P, const double *c, double cfl) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* troubled-cell indicator and shock limiter (optional; not in the paper)    */
+/* ------------------------------------------------------------------------ */
+
+static double minmod3(double a, double b, double c) {
+    if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(a, fmin(b, c));
+    if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
+    return 0.0;
+}
+
+/* average of the neighbour across side s, following the boundary condition */
+static void neighbour_average(const orc_problem *P, const double *c, int cell, int s, double *ub) {
+    int nb = neighbour(P, cell, s);
+    int m = P->m;
+    if (nb >= 0) {
+        for (int comp = 0; comp < m; ++comp) ub[comp] = cell_coef(P, c, nb, comp)[0];
+        return;
+    }
+    double own[ORC_MAXM];
+    for (int comp = 0; comp < m; ++comp) own[comp] = cell_coef(P, c, cell, comp)[0];
+    exterior_state(P, s, own, 0.0, 0.0, 0.0, ub);
+}
+
+long long orc_troubled_cells(const orc_problem *P, const double *c, int *flags) {
+    int n = P->n, m = P->m;
+    long long count = 0;
+    for (int cell = 0; cell < P->ncell; ++cell) {
+        int troubled = 0;
+        for (int dir = 0; dir < P->dim && !troubled; ++dir) {
+            double h = dir == 0 ? P->hx : P->hy;
+            double ulo[ORC_MAXM], uhi[ORC_MAXM];
+            neighbour_average(P, c, cell, 2 * dir, ulo);
+            neighbour_average(P, c, cell, 2 * dir + 1, uhi);
+            for (int comp = 0; comp < m && !troubled; ++comp) {
+                const double *a = cell_coef(P, c, cell, comp);
+                /* face averages of the traces: only the modes constant along the face survive */
+                double fp = 0.0, fm = 0.0;
+                for (int i = 1; i < n; ++i) {
+                    double ci = dir == 0 ? a[i] : a[i * n];
+                    fp += ci;                       /* P_i(+1) = 1 */
+                    fm += (i % 2 ? -1.0 : 1.0) * ci; /* P_i(-1) = (-1)^i */
+                }
+                double utR = fp, utL = -fm;
+                double dp = uhi[comp] - a[0], dm = a[0] - ulo[comp];
+                double thr = P->tvb_M * h * h;
+                double mR = fabs(utR) <= thr ? utR : minmod3(utR, dp, dm);
+                double mL = fabs(utL) <= thr ? utL : minmod3(utL, dp, dm);
+                if (mR != utR || mL != utL) troubled = 1;
+            }
+        }
+        flags[cell] = troubled;
+        count += troubled;
+    }
+    return count;
+}
+
+void orc_shock_limit(const orc_problem *P, double *c, const int *flags) {
+    int n = P->n, m = P->m;
+    double *out = (double *)malloc(sizeof(double) * orc_state_size(P));
+    memcpy(out, c, sizeof(double) * orc_state_size(P));
+    for (int cell = 0; cell < P->ncell; ++cell) {
+        if (!flags[cell]) continue;
+        double nbr[4][ORC_MAXM];
+        for (int s = 0; s < 2 * P->dim; ++s) neighbour_average(P, c, cell, s, nbr[s]);
+        for (int comp = 0; comp < m; ++comp) {
+            const double *a = cell_coef(P, c, cell, comp);
+            double *b = cell_coef_w(P, out, cell, comp);
+            double ub = a[0];
+            double cx = n > 1 ? a[1] : 0.0;
+            double newx = minmod3(cx, nbr[1][comp] - ub, ub - nbr[0][comp]);
+            double newy = 0.0;
+            if (P->dim == 2) newy = minmod3(a[n], nbr[3][comp] - ub, ub - nbr[2][comp]);
+            for (int q = 0; q < P->nmodes; ++q) b[q] = 0.0;
+            b[0] = ub;
+            b[1] = newx;
+            if (P->dim == 2) b[n] = newy;
+        }
+    }
+    memcpy(c, out, sizeof(double) * orc_state_size(P));
+    free(out);
+}
+
+/* ------------------------------------------------------------------------ */
 /* time stepping: Scheme 1L                                                  */
 /* ------------------------------------------------------------------------ */
 
@@ -731,6 +834,12 @@ static int attempt_step(const orc_problem *P, const double *cn, double dt, int s
         if (!orc_averages_admissible(P, u)) {
             fail = s + 1;
         } else {
+            if (P->indicator) {
+                int *flags = (int *)malloc(sizeof(int) * P->ncell);
+                orc_troubled_cells(P, u, flags);
+                orc_shock_limit(P, u, flags);
+                free(flags);
+            }
             if (P->limiter_on) {
                 *nlim += orc_limit(P, u, theta);
                 for (int q = 0; q < P->ncell; ++q) if (theta[q] < *thmin) *thmin = theta[q];

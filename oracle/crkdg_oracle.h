@@ -43,6 +43,8 @@ typedef struct orc_problem {
     int bc[4];               /* sides: 0 left, 1 right, 2 bottom, 3 top */
     double bc_state[4][ORC_MAXM];
     int limiter_on;          /* 1: scaling limiter after every stage */
+    int indicator;           /* 1: TVB troubled-cell indicator + minmod shock limiter after the final stage */
+    double tvb_M;            /* TVB constant of the indicator */
     int max_halvings;
     orc_exact_fn exact;
     void *exact_ctx;
@@ -95,6 +97,12 @@ long long orc_limit(const orc_problem *P, double *c, double *theta_out);
 int orc_averages_admissible(const orc_problem *P, const double *c); /* 1 if all in B^eps */
 /* minimum over S_K of each bound margin: scalar [u-lo, hi-u]; Euler [rho-eps, rhoe-eps] */
 void orc_min_margins(const orc_problem *P, const double *c, double *margins2);
+
+/* plain troubled-cell indicator (TVB-modified minmod on face-averaged traces, per component
+ * and direction) and minmod shock limiter; flags[cell] = 1 for a troubled cell */
+void orc_set_indicator(orc_problem *P, int on, double tvb_M);
+long long orc_troubled_cells(const orc_problem *P, const double *c, int *flags);
+void orc_shock_limit(const orc_problem *P, double *c, const int *flags);
 
 /* a0 = max over S_K points and directions of the spectral radius (Sec. 2.1 notation) */
 double orc_a0(const orc_problem *P, const double *c);

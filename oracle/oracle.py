@@ -95,6 +95,10 @@ def _load():
     lib.orc_limit.restype = C.c_longlong
     lib.orc_averages_admissible.argtypes = [V, _dp]
     lib.orc_min_margins.argtypes = [V, _dp, _dp]
+    lib.orc_set_indicator.argtypes = [V, C.c_int, C.c_double]
+    lib.orc_troubled_cells.argtypes = [V, _dp, C.POINTER(C.c_int)]
+    lib.orc_troubled_cells.restype = C.c_longlong
+    lib.orc_shock_limit.argtypes = [V, _dp, C.POINTER(C.c_int)]
     lib.orc_a0.argtypes = [V, _dp]
     lib.orc_a0.restype = C.c_double
     lib.orc_max_dt.argtypes = [V, _dp, C.c_double]
@@ -150,7 +154,7 @@ class Oracle:
 
     def __init__(self, dim, nx, ny, k, domain, flux, gamma=1.4, velocity=(1.0, 0.0),
                  bounds=(0.0, 1.0), eps=1e-13, bc=("periodic",) * 4, bc_state=None,
-                 exact=None, limiter=True, max_halvings=20):
+                 exact=None, limiter=True, max_halvings=20, indicator=False, tvb_M=10.0):
         lib = _load()
         self.lib = lib
         x0, x1, y0, y1 = (tuple(domain) + (0.0, 1.0))[:4]
@@ -183,6 +187,7 @@ class Oracle:
             self._exact_c = _EXACT_FN(cb)
             lib.orc_set_exact(self.h, self._exact_c, None)
         lib.orc_set_options(self.h, 1 if limiter else 0, max_halvings)
+        lib.orc_set_indicator(self.h, 1 if indicator else 0, tvb_M)
         self.c = np.zeros(self.N)
 
     def __del__(self):
@@ -254,6 +259,18 @@ class Oracle:
         out = np.zeros(2)
         self.lib.orc_min_margins(self.h, _p(modal), _p(out))
         return out
+
+    def troubled(self, modal=None):
+        """TVB troubled-cell flags of a state (int array per cell)."""
+        modal = self.c if modal is None else modal
+        flags = np.zeros(self.nx * self.ny, dtype=np.int32)
+        self.lib.orc_troubled_cells(self.h, _p(modal), flags.ctypes.data_as(C.POINTER(C.c_int)))
+        return flags
+
+    def shock_limit(self, flags, modal=None):
+        target = self.c if modal is None else modal
+        flags = np.ascontiguousarray(flags, dtype=np.int32)
+        self.lib.orc_shock_limit(self.h, _p(target), flags.ctypes.data_as(C.POINTER(C.c_int)))
 
     def flux_at(self, u, direction=0):
         u = np.ascontiguousarray(u, dtype=np.float64)

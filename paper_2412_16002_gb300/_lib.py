@@ -16,6 +16,7 @@ STATUS = {0: "OK", 1: "E_ARG", 2: "E_CUDA", 3: "E_OOM", 4: "E_BOUNDS", 5: "E_TIM
 BC = {"periodic": 0, "outflow": 1, "reflect": 2, "dirichlet": 3}
 FLUX = {"advection": 0, "burgers": 1, "euler": 2}
 PREC = {"fp64": 0, "mixed": 1}
+INDICATOR = {"off": 0, "tvb": 1, "mlp": 2}
 OPS = {"G": 0, "F": 1, "limit": 2}
 
 
@@ -68,11 +69,21 @@ SYMBOLS = {
     "crkdg_step": (C.c_int, [_H, C.c_double, C.POINTER(Tableau), C.POINTER(StepInfo)]),
     "crkdg_advance": (C.c_int, [_H, C.c_int, C.c_double, C.c_double, C.POINTER(Tableau), _dp,
                                 C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "crkdg_advance_fixed": (C.c_int, [_H, C.c_int, C.c_double, C.c_double, C.POINTER(Tableau), _dp,
+                                      C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "crkdg_apply_operator": (C.c_int, [_H, C.c_int, C.c_void_p, C.c_void_p]),
+    "crkdg_troubled_flags": (C.c_int, [_H, C.c_void_p, C.c_int]),
     "crkdg_cell_averages": (C.c_int, [_H, C.c_void_p, C.c_int]),
+    "crkdg_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "crkdg_mlp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "crkdg_mlp_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.c_void_p]),
+    "crkdg_set_mlp": (C.c_int, [_H, C.c_void_p]),
+    "crkdg_set_harvest": (C.c_int, [_H, C.c_int]),
+    "crkdg_last_features": (C.c_int, [_H, C.c_void_p, C.c_int]),
     "crkdg_bound_margins": (C.c_int, [_H, _dp]),
     "crkdg_total_mass": (C.c_int, [_H, C.c_int, _dp]),
     "crkdg_set_profiling": (C.c_int, [_H, C.c_int]),
+    "crkdg_set_barrier_test": (C.c_int, [_H, C.c_int]),
     "crkdg_kernel_times": (C.c_int, [_H, _dp, C.POINTER(C.c_longlong)]),
     "crkdg_state_size": (C.c_size_t, [_H]),
     "crkdg_last_error": (C.c_char_p, [_H]),

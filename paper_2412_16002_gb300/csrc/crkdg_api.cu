@@ -23,6 +23,7 @@ struct DevScal {
     unsigned long long thmin;
     unsigned long long a0;
     unsigned long long ord[2];
+    unsigned long long ntrb;
 };
 
 uint64_t bits_of(double x) {
@@ -109,6 +110,18 @@ void build_tables(NodalTables *tab) {
         }
         for (int b = 0; b < n; ++b)
             for (int a = 0; a < n; ++a) T.w2[b * n + a] = 0.25 * T.wg[a] * T.wg[b];
+        for (int a = 0; a < MAXN; ++a) {
+            for (int q = 0; q < MAXN; ++q) {
+                T.Dhatf[a][q] = (float)T.Dhat[a][q];
+                T.Iglf[a][q] = (float)T.Igl[a][q];
+            }
+            T.lmf[a] = (float)T.lm[a];
+            T.lpf[a] = (float)T.lp[a];
+            T.liftmf[a] = (float)T.liftm[a];
+            T.liftpf[a] = (float)T.liftp[a];
+            T.w1f[a] = (float)T.w1[a];
+        }
+        for (int q = 0; q < MAXN * MAXN; ++q) T.w2f[q] = (float)T.w2[q];
     }
 }
 
@@ -132,8 +145,24 @@ struct crkdg_ctx {
     double a0 = 0.0;
     bool prof = false;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    double prof_ms[2] = {0.0, 0.0};
-    long long prof_n[2] = {0, 0};
+    double prof_ms[3] = {0.0, 0.0, 0.0};
+    long long prof_n[3] = {0, 0, 0};
+    // split-precision state (CRKDG_PREC_MIXED): FP64 averages + FP32 deviations
+    bool mixed = false;
+    double *xub[2] = {nullptr, nullptr};
+    float *xdv[2] = {nullptr, nullptr};
+    float *xdvs = nullptr;
+    float *xtr = nullptr;
+    int xtr_slots = 0;
+    int xcur = 0;
+    int *tflags = nullptr;   // troubled-cell flags of the last step (indicator on)
+    float *feat = nullptr;   // MLP features [cell][44]
+    float *prob = nullptr;   // MLP probabilities [cell]
+    float *mlp = nullptr;    // MLP parameters of the learned indicator
+    bool harvest = false;
+    int barrier_extra = 0;   // testing aid (crkdg_set_barrier_test)
+    RunCtl *ctl = nullptr;   // device control block of the 1D step loop
+    RunCtl *hctl = nullptr;  // pinned host copy
     std::string err;
 };
 
@@ -166,6 +195,7 @@ Params base_params(const crkdg_ctx *h) {
     P.lo = h->bounds.lo;
     P.hi = h->bounds.hi;
     P.eps = h->bounds.eps;
+    P.tvb_M = h->opt.tvb_M;
     for (int s = 0; s < 4; ++s) {
         P.bc[s] = (h->dim == 1 && s >= 2) ? BC_OUTFLOW : h->mesh.bc[s];
         for (int c = 0; c < MAXM; ++c) P.bcs[s][c] = h->mesh.bc_state[s][c];
@@ -186,6 +216,10 @@ Bufs base_bufs(const crkdg_ctx *h) {
     B.a0 = &h->scal->a0;
     B.aux = h->aux;
     B.ord = h->scal->ord;
+    B.tflags = h->tflags;
+    B.ntrb = &h->scal->ntrb;
+    B.feat = h->feat;
+    B.prob = h->prob;
     return B;
 }
 
@@ -194,6 +228,31 @@ cudaError_t launch(crkdg_ctx *h, int kernel, const Params &P, const Bufs &B) {
     int nblocks = (h->ncell + ncb - 1) / ncb;
     if (h->dim == 1) return crkdg_launch_1d(kernel, h->n, h->phys, nblocks, h->st, P, B);
     return crkdg_launch_2d(kernel, h->n, h->phys, nblocks, h->st, P, B);
+}
+
+MixBufs base_xbufs(const crkdg_ctx *h) {
+    MixBufs X;
+    memset(&X, 0, sizeof(X));
+    X.ub = h->xub[h->xcur];
+    X.dv = h->xdv[h->xcur];
+    X.dv_s = h->xdvs;
+    X.ub_n = h->xub[1 - h->xcur];
+    X.dv_n = h->xdv[1 - h->xcur];
+    X.tr = h->xtr;
+    X.flag = &h->scal->flag;
+    X.nlim = &h->scal->nlim;
+    X.thmin = &h->scal->thmin;
+    X.a0 = &h->scal->a0;
+    X.ord = h->scal->ord;
+    X.aux = h->aux;
+    return X;
+}
+
+cudaError_t launch_x(crkdg_ctx *h, int kernel, const Params &P, const MixBufs &X) {
+    int ncb = cells_per_block(h->dim, h->n);
+    int nblocks = (h->ncell + ncb - 1) / ncb;
+    if (h->dim == 1) return crkdg_launch_mx_1d(kernel, h->n, h->phys, nblocks, h->st, P, X);
+    return crkdg_launch_mx_2d(kernel, h->n, h->phys, nblocks, h->st, P, X);
 }
 
 crkdg_status reset_scalars(crkdg_ctx *h) {
@@ -218,6 +277,16 @@ crkdg_status ensure_traces(crkdg_ctx *h, int slots) {
     return CRKDG_OK;
 }
 
+crkdg_status ensure_traces_x(crkdg_ctx *h, int slots) {
+    if (slots <= h->xtr_slots) return CRKDG_OK;
+    if (h->xtr) cudaFree(h->xtr);
+    h->xtr = nullptr;
+    h->xtr_slots = 0;
+    CK(h, cudaMalloc(&h->xtr, (size_t)slots * h->m * h->ncell * h->ntr * sizeof(float)));
+    h->xtr_slots = slots;
+    return CRKDG_OK;
+}
+
 crkdg_status check_tableau(crkdg_t h, const crkdg_tableau *tab) {
     if (!tab || !tab->A || !tab->b) return fail(h, CRKDG_E_ARG, "tableau: NULL");
     if (tab->s < 1 || tab->s > MAXS) return fail(h, CRKDG_E_ARG, "tableau: need 1 <= s <= 4");
@@ -232,12 +301,27 @@ crkdg_status check_tableau(crkdg_t h, const crkdg_tableau *tab) {
     return CRKDG_OK;
 }
 
+void fill_tableau(Params &P, const crkdg_tableau *tab) {
+    P.s = tab->s;
+    int ns = 0;
+    for (int i = 0; i < tab->s; ++i) {
+        P.b[i] = tab->b[i];
+        for (int j = 0; j < tab->s; ++j) P.A[i][j] = tab->A[i * tab->s + j];
+        P.slot[i] = tab->b[i] != 0.0 ? ns++ : -1;
+    }
+    P.nslot = ns;
+}
+
 crkdg_status compute_a0(crkdg_ctx *h) {
     crkdg_status s = reset_scalars(h);
     if (s) return s;
     Params P = base_params(h);
-    Bufs B = base_bufs(h);
-    CK(h, launch(h, K_A0, P, B));
+    if (h->mixed) {
+        CK(h, launch_x(h, KX_SCAN, P, base_xbufs(h)));
+    } else {
+        Bufs B = base_bufs(h);
+        CK(h, launch(h, K_A0, P, B));
+    }
     s = read_scalars(h);
     if (s) return s;
     h->a0 = from_bits(h->hs->a0);
@@ -284,7 +368,11 @@ crkdg_status crkdg_create(const crkdg_mesh *mesh, int k, int m, const crkdg_flux
     crkdg_options_default(&o);
     if (opt) o = *opt;
     if (o.max_halvings < 0 || o.max_halvings > 60) return CRKDG_E_ARG;
-    if (o.precision != CRKDG_PREC_FP64) return CRKDG_E_UNSUPPORTED;
+    if (o.precision != CRKDG_PREC_FP64 && o.precision != CRKDG_PREC_MIXED) return CRKDG_E_ARG;
+    if (o.indicator < CRKDG_IND_OFF || o.indicator > CRKDG_IND_MLP || !(o.tvb_M >= 0.0)) return CRKDG_E_ARG;
+    if (o.indicator != CRKDG_IND_OFF && (o.precision != CRKDG_PREC_FP64 || flux->kind != CRKDG_FLUX_EULER))
+        return CRKDG_E_UNSUPPORTED;
+    if (o.indicator == CRKDG_IND_MLP && mesh->dim != 2) return CRKDG_E_UNSUPPORTED;
 
     crkdg_ctx *h = new (std::nothrow) crkdg_ctx();
     if (!h) return CRKDG_E_OOM;
@@ -322,6 +410,25 @@ crkdg_status crkdg_create(const crkdg_mesh *mesh, int k, int m, const crkdg_flux
         if (s == CRKDG_OK) chk(cudaMalloc(&h->scal, sizeof(DevScal)), "cudaMalloc scalars");
         if (s == CRKDG_OK) chk(cudaMallocHost(&h->hs, sizeof(DevScal)), "cudaMallocHost");
         if (s == CRKDG_OK) chk(cudaMallocHost(&h->hinit, sizeof(DevScal)), "cudaMallocHost");
+        h->mixed = o.precision == CRKDG_PREC_MIXED;
+        if (s == CRKDG_OK && h->mixed) {
+            size_t nb = (size_t)h->ncell * h->m;
+            for (int i = 0; i < 2 && s == CRKDG_OK; ++i) {
+                chk(cudaMalloc(&h->xub[i], nb * sizeof(double)), "cudaMalloc averages");
+                if (s == CRKDG_OK) chk(cudaMalloc(&h->xdv[i], h->nstate * sizeof(float)), "cudaMalloc deviations");
+            }
+            if (s == CRKDG_OK) chk(cudaMalloc(&h->xdvs, h->nstate * sizeof(float)), "cudaMalloc deviations");
+            if (s == CRKDG_OK) chk(cudaMemsetAsync(h->xub[0], 0, nb * sizeof(double), h->st), "cudaMemset");
+            if (s == CRKDG_OK) chk(cudaMemsetAsync(h->xdv[0], 0, h->nstate * sizeof(float), h->st), "cudaMemset");
+        }
+        if (s == CRKDG_OK && o.indicator != CRKDG_IND_OFF)
+            chk(cudaMalloc(&h->tflags, (size_t)h->ncell * sizeof(int)), "cudaMalloc flags");
+        if (s == CRKDG_OK && o.indicator != CRKDG_IND_OFF && h->dim == 2) {
+            chk(cudaMalloc(&h->feat, (size_t)h->ncell * CRKDG_MLP_NIN * sizeof(float)), "cudaMalloc features");
+            if (s == CRKDG_OK) chk(cudaMalloc(&h->prob, (size_t)h->ncell * sizeof(float)), "cudaMalloc prob");
+            if (s == CRKDG_OK) chk(cudaMalloc(&h->mlp, CRKDG_MLP_NPARAM * sizeof(float)), "cudaMalloc mlp");
+            if (s == CRKDG_OK) chk(cudaMemsetAsync(h->mlp, 0, CRKDG_MLP_NPARAM * sizeof(float), h->st), "cudaMemset");
+        }
         if (s == CRKDG_OK) chk(cudaMemsetAsync(h->u, 0, bytes, h->st), "cudaMemset");
         if (s == CRKDG_OK) chk(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
         if (s != CRKDG_OK) {
@@ -352,6 +459,18 @@ crkdg_status crkdg_destroy(crkdg_t h) {
     cudaFree(h->scal);
     cudaFreeHost(h->hs);
     cudaFreeHost(h->hinit);
+    cudaFree(h->ctl);
+    cudaFreeHost(h->hctl);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(h->xub[i]);
+        cudaFree(h->xdv[i]);
+    }
+    cudaFree(h->xdvs);
+    cudaFree(h->xtr);
+    cudaFree(h->tflags);
+    cudaFree(h->feat);
+    cudaFree(h->prob);
+    cudaFree(h->mlp);
     delete h;
     return CRKDG_OK;
 }
@@ -363,17 +482,25 @@ crkdg_status crkdg_set_profiling(crkdg_t h, int on) {
     if (on && !h->ev[0])
         for (int i = 0; i < 3; ++i) CK(h, cudaEventCreate(&h->ev[i]));
     h->prof = on != 0;
-    h->prof_ms[0] = h->prof_ms[1] = 0.0;
-    h->prof_n[0] = h->prof_n[1] = 0;
+    for (int i = 0; i < 3; ++i) {
+        h->prof_ms[i] = 0.0;
+        h->prof_n[i] = 0;
+    }
     return CRKDG_OK;
 }
 
-crkdg_status crkdg_kernel_times(crkdg_t h, double ms[2], long long launches[2]) {
+crkdg_status crkdg_set_barrier_test(crkdg_t h, int extra) {
+    if (!h || extra < 0) return CRKDG_E_ARG;
+    h->barrier_extra = extra;
+    return CRKDG_OK;
+}
+
+crkdg_status crkdg_kernel_times(crkdg_t h, double ms[3], long long launches[3]) {
     if (!h || !ms || !launches) return CRKDG_E_ARG;
-    ms[0] = h->prof_ms[0];
-    ms[1] = h->prof_ms[1];
-    launches[0] = h->prof_n[0];
-    launches[1] = h->prof_n[1];
+    for (int i = 0; i < 3; ++i) {
+        ms[i] = h->prof_ms[i];
+        launches[i] = h->prof_n[i];
+    }
     return CRKDG_OK;
 }
 
@@ -386,11 +513,22 @@ crkdg_status crkdg_set_state(crkdg_t h, const double *nodal, size_t count, int o
         CK(h, cudaMemcpyAsync(h->unew, nodal, count * sizeof(double),
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
         Params P = base_params(h);
-        Bufs B = base_bufs(h);
-        B.un = h->unew;
-        B.unew = h->u;
         CK(h, reset_scalars(h) == CRKDG_OK ? cudaSuccess : cudaErrorUnknown);
-        CK(h, launch(h, K_LIMIT, P, B));
+        if (h->mixed) {
+            MixBufs X = base_xbufs(h);
+            X.nod_in = h->unew;
+            X.ub_n = h->xub[h->xcur];
+            X.dv_n = h->xdv[h->xcur];
+            CK(h, launch_x(h, KX_SPLIT, P, X));
+            X = base_xbufs(h);
+            X.dv_n = h->xdv[h->xcur];
+            CK(h, launch_x(h, KX_LIMIT, P, X));
+        } else {
+            Bufs B = base_bufs(h);
+            B.un = h->unew;
+            B.unew = h->u;
+            CK(h, launch(h, K_LIMIT, P, B));
+        }
         CK(h, cudaStreamSynchronize(h->st));
         h->a0_valid = false;
         return CRKDG_OK;
@@ -402,6 +540,11 @@ crkdg_status crkdg_set_state(crkdg_t h, const double *nodal, size_t count, int o
 crkdg_status crkdg_get_state(crkdg_t h, double *nodal, size_t count, int on_device) {
     if (!h) return CRKDG_E_ARG;
     if (!nodal || count != h->nstate) return fail(h, CRKDG_E_ARG, "get_state: count must equal the state size");
+    if (h->mixed) {
+        MixBufs X = base_xbufs(h);
+        X.nod_out = h->u;
+        CK(h, launch_x(h, KX_MERGE, base_params(h), X));
+    }
     CK(h, cudaMemcpyAsync(nodal, h->u, count * sizeof(double),
                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
     CK(h, cudaStreamSynchronize(h->st));
@@ -433,6 +576,8 @@ crkdg_status crkdg_step(crkdg_t h, double dt, const crkdg_tableau *tab, crkdg_st
         Params P = base_params(h);
         P.s = tab->s;
         P.mode = MODE_STEP;
+        const bool ind = h->opt.indicator != CRKDG_IND_OFF;
+        P.defer_limit = ind ? 1 : 0;
         int ns = 0;
         for (int i = 0; i < tab->s; ++i) {
             P.b[i] = tab->b[i];
@@ -440,7 +585,7 @@ crkdg_status crkdg_step(crkdg_t h, double dt, const crkdg_tableau *tab, crkdg_st
             P.slot[i] = tab->b[i] != 0.0 ? ns++ : -1;
         }
         P.nslot = ns;
-        s = ensure_traces(h, ns > 0 ? ns : 1);
+        s = h->mixed ? ensure_traces_x(h, ns > 0 ? ns : 1) : ensure_traces(h, ns > 0 ? ns : 1);
         if (s) return s;
         Bufs B = base_bufs(h);
         for (int r = 0; r <= h->opt.max_halvings; ++r) {
@@ -450,9 +595,34 @@ crkdg_status crkdg_step(crkdg_t h, double dt, const crkdg_tableau *tab, crkdg_st
             s = reset_scalars(h);
             if (s) return s;
             if (h->prof) CK(h, cudaEventRecord(h->ev[0], h->st));
-            CK(h, launch(h, K_INNER, P, B));
+            if (h->mixed) {
+                CK(h, launch_x(h, KX_INNER, P, base_xbufs(h)));
+            } else {
+                CK(h, launch(h, K_INNER, P, B));
+            }
             if (h->prof) CK(h, cudaEventRecord(h->ev[1], h->st));
-            CK(h, launch(h, K_FINAL, P, B));
+            if (h->mixed) {
+                CK(h, launch_x(h, KX_FINAL, P, base_xbufs(h)));
+            } else {
+                CK(h, launch(h, K_FINAL, P, B));
+                if (ind) {
+                    const bool learned = h->opt.indicator == CRKDG_IND_MLP;
+                    if (learned || h->harvest) {
+                        P.ind_stage = 1;  // plain decision of the unlimited state
+                        CK(h, launch(h, K_TROUBLE, P, B));
+                        if (h->feat) CK(h, launch(h, K_FEATURES, P, B));
+                        if (learned) {
+                            if (crkdg_mlp_forward(h->mlp, h->feat, h->ncell, h->prob, h->st) != CRKDG_OK)
+                                return fail(h, CRKDG_E_CUDA, "step: MLP forward failed");
+                            CK(h, launch(h, K_COMBINE, P, B));
+                        }
+                        P.ind_stage = 2;  // limit the flagged cells
+                    } else {
+                        P.ind_stage = 0;
+                    }
+                    CK(h, launch(h, K_TROUBLE, P, B));
+                }
+            }
             if (h->prof) CK(h, cudaEventRecord(h->ev[2], h->st));
             s = read_scalars(h);
             if (s) return s;
@@ -466,9 +636,13 @@ crkdg_status crkdg_step(crkdg_t h, double dt, const crkdg_tableau *tab, crkdg_st
                 h->prof_n[1] += 1;
             }
             if (h->hs->flag == 0) {
-                double *t = h->u;
-                h->u = h->unew;
-                h->unew = t;
+                if (h->mixed) {
+                    h->xcur = 1 - h->xcur;
+                } else {
+                    double *t = h->u;
+                    h->u = h->unew;
+                    h->unew = t;
+                }
                 h->a0 = from_bits(h->hs->a0);
                 h->a0_valid = true;
                 if (info) {
@@ -476,7 +650,7 @@ crkdg_status crkdg_step(crkdg_t h, double dt, const crkdg_tableau *tab, crkdg_st
                     info->restarts = r;
                     info->cells_limited = (long long)h->hs->nlim;
                     info->theta_min = from_bits(h->hs->thmin);
-                    info->troubled = 0;
+                    info->troubled = (long long)h->hs->ntrb;
                     info->mass_drift = 0.0;
                 }
                 return CRKDG_OK;
@@ -489,9 +663,79 @@ crkdg_status crkdg_step(crkdg_t h, double dt, const crkdg_tableau *tab, crkdg_st
     }
 }
 
+// 1D meshes: one persistent cooperative launch runs the whole step loop.
+// cfl > 0: adaptive trial steps; cfl <= 0: the fixed trial step dt_fixed every step.
+static crkdg_status advance_1d(crkdg_t h, int nsteps, double cfl, double dt_fixed, double t_end,
+                               const crkdg_tableau *tab, double *t, int *steps_done, int *restarts) {
+    crkdg_status s = check_tableau(h, tab);
+    if (s) return s;
+    if (steps_done) *steps_done = 0;
+    if (restarts) *restarts = 0;
+    if (nsteps <= 0 || !(*t < t_end)) return CRKDG_OK;
+    if (!h->ctl) {
+        CK(h, cudaMalloc(&h->ctl, sizeof(RunCtl)));
+        CK(h, cudaMallocHost(&h->hctl, sizeof(RunCtl)));
+    }
+    if (cfl > 0.0 && !h->a0_valid) {
+        s = compute_a0(h);
+        if (s) return s;
+    }
+    Params P = base_params(h);
+    fill_tableau(P, tab);
+    P.mode = MODE_STEP;
+    RunCtl *c = h->hctl;
+    memset(c, 0, sizeof(RunCtl));
+    c->t = *t;
+    c->t_end = t_end;
+    c->dt0 = cfl > 0.0 ? (h->a0 > 0.0 ? cfl / h->a0 : INFINITY) : dt_fixed;
+    c->cfl = cfl > 0.0 ? cfl : 0.0;
+    c->nsteps = nsteps;
+    c->max_halvings = h->opt.max_halvings;
+    c->cur = 0;
+    c->extra_arrivals = h->barrier_extra;
+    for (int i = 0; i < 3; ++i) c->slot[i].thmin = bits_of(1.0);
+    CK(h, cudaMemcpyAsync(h->ctl, c, sizeof(RunCtl), cudaMemcpyHostToDevice, h->st));
+    int nb = 0;
+    if (h->prof) CK(h, cudaEventRecord(h->ev[0], h->st));
+    CK(h, crkdg_run_1d(h->n, h->phys, h->st, P, h->u, h->unew, h->ctl, &nb));
+    if (h->prof) CK(h, cudaEventRecord(h->ev[1], h->st));
+    CK(h, cudaMemcpyAsync(c, h->ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    if (h->prof) {
+        float ms = 0.f;
+        CK(h, cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+        h->prof_ms[2] += ms;
+        h->prof_n[2] += 1;
+    }
+    if (c->cur_out) {
+        double *tmp = h->u;
+        h->u = h->unew;
+        h->unew = tmp;
+    }
+    *t = c->t_out;
+    if (steps_done) *steps_done = c->steps;
+    if (restarts) *restarts = c->restarts;
+    if (c->steps > 0 && c->rate_out >= 0.0) {
+        h->a0 = c->rate_out;
+        h->a0_valid = true;
+    }
+    if (c->status == RUN_BOUNDS)
+        return fail(h, CRKDG_E_BOUNDS, "advance: cell averages left the admissible set after max_halvings restarts");
+    if (c->status == RUN_TIMEOUT) return fail(h, CRKDG_E_TIMEOUT, "advance: grid barrier wait expired");
+    return CRKDG_OK;
+}
+
 crkdg_status crkdg_advance(crkdg_t h, int nsteps, double cfl, double t_end, const crkdg_tableau *tab,
                            double *t, int *steps_done, int *restarts) {
     if (!h || !t) return CRKDG_E_ARG;
+    if (!(cfl > 0.0)) return fail(h, CRKDG_E_ARG, "advance: cfl must be > 0");
+    if (h->dim == 1 && !h->mixed && h->opt.indicator == CRKDG_IND_OFF) {
+        try {
+            return advance_1d(h, nsteps, cfl, 0.0, t_end, tab, t, steps_done, restarts);
+        } catch (...) {
+            return CRKDG_E_OOM;
+        }
+    }
     int done = 0, rs = 0;
     crkdg_status s = CRKDG_OK;
     for (int i = 0; i < nsteps; ++i) {
@@ -512,6 +756,35 @@ crkdg_status crkdg_advance(crkdg_t h, int nsteps, double cfl, double t_end, cons
     return s;
 }
 
+crkdg_status crkdg_advance_fixed(crkdg_t h, int nsteps, double dt, double t_end, const crkdg_tableau *tab,
+                                 double *t, int *steps_done, int *restarts) {
+    if (!h || !t) return CRKDG_E_ARG;
+    if (!(dt > 0.0) || !isfinite(dt)) return fail(h, CRKDG_E_ARG, "advance_fixed: dt must be finite and > 0");
+    if (h->dim == 1 && !h->mixed && h->opt.indicator == CRKDG_IND_OFF) {
+        try {
+            return advance_1d(h, nsteps, 0.0, dt, t_end, tab, t, steps_done, restarts);
+        } catch (...) {
+            return CRKDG_E_OOM;
+        }
+    }
+    int done = 0, rs = 0;
+    crkdg_status s = CRKDG_OK;
+    for (int i = 0; i < nsteps; ++i) {
+        if (!(*t < t_end)) break;
+        double d = dt < t_end - *t ? dt : t_end - *t;
+        crkdg_step_info info;
+        s = crkdg_step(h, d, tab, &info);
+        if (s) break;
+        *t += info.dt_taken;
+        if (t_end - *t <= 1e-14 * fabs(t_end)) *t = t_end;
+        ++done;
+        rs += info.restarts;
+    }
+    if (steps_done) *steps_done = done;
+    if (restarts) *restarts = rs;
+    return s;
+}
+
 crkdg_status crkdg_apply_operator(crkdg_t h, int op, const double *in_dev, double *out_dev) {
     if (!h) return CRKDG_E_ARG;
     if (!in_dev || !out_dev || in_dev == out_dev) return fail(h, CRKDG_E_ARG, "apply_operator: bad pointers");
@@ -521,6 +794,39 @@ crkdg_status crkdg_apply_operator(crkdg_t h, int op, const double *in_dev, doubl
         P.s = 1;
         P.dt = 1.0;
         P.b[0] = 1.0;
+        if (h->mixed) {
+            if (op != CRKDG_OP_G && op != CRKDG_OP_F && op != CRKDG_OP_LIMIT)
+                return fail(h, CRKDG_E_ARG, "apply_operator: unknown op");
+            crkdg_status s = ensure_traces_x(h, 1);
+            if (s) return s;
+            // split the input into the spare (averages, deviations) pair
+            MixBufs X = base_xbufs(h);
+            X.nod_in = in_dev;
+            CK(h, launch_x(h, KX_SPLIT, P, X));
+            MixBufs Y = base_xbufs(h);
+            Y.ub = h->xub[1 - h->xcur];
+            Y.dv = h->xdv[1 - h->xcur];
+            Y.dv_n = h->xdv[1 - h->xcur];
+            if (op == CRKDG_OP_LIMIT) {
+                CK(h, launch_x(h, KX_LIMIT, P, Y));
+                Y.nod_out = out_dev;
+                CK(h, launch_x(h, KX_MERGE, P, Y));
+            } else {
+                P.mode = MODE_OP_G;
+                P.slot[0] = op == CRKDG_OP_F ? 0 : -1;
+                P.nslot = op == CRKDG_OP_F ? 1 : 0;
+                Y.nod_out = op == CRKDG_OP_F ? h->ustar : out_dev;
+                CK(h, launch_x(h, KX_INNER, P, Y));
+                if (op == CRKDG_OP_F) {
+                    P.mode = MODE_OP_F;
+                    Y.nod_in = h->ustar;
+                    Y.nod_out = out_dev;
+                    CK(h, launch_x(h, KX_FINAL, P, Y));
+                }
+            }
+            CK(h, cudaStreamSynchronize(h->st));
+            return CRKDG_OK;
+        }
         if (op == CRKDG_OP_G) {
             P.mode = MODE_OP_G;
             B.un = in_dev;
@@ -553,11 +859,48 @@ crkdg_status crkdg_apply_operator(crkdg_t h, int op, const double *in_dev, doubl
     }
 }
 
+crkdg_status crkdg_troubled_flags(crkdg_t h, int *flags, int on_device) {
+    if (!h || !flags) return CRKDG_E_ARG;
+    if (!h->tflags) return fail(h, CRKDG_E_ARG, "troubled_flags: the indicator is off");
+    CK(h, cudaMemcpyAsync(flags, h->tflags, (size_t)h->ncell * sizeof(int),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    return CRKDG_OK;
+}
+
+crkdg_status crkdg_set_mlp(crkdg_t h, const float *params) {
+    if (!h || !params) return CRKDG_E_ARG;
+    if (!h->mlp) return fail(h, CRKDG_E_ARG, "set_mlp: needs a 2D handle with an indicator");
+    CK(h, cudaMemcpyAsync(h->mlp, params, CRKDG_MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    return CRKDG_OK;
+}
+
+crkdg_status crkdg_set_harvest(crkdg_t h, int on) {
+    if (!h) return CRKDG_E_ARG;
+    if (on && !h->feat) return fail(h, CRKDG_E_ARG, "set_harvest: needs a 2D handle with an indicator");
+    h->harvest = on != 0;
+    return CRKDG_OK;
+}
+
+crkdg_status crkdg_last_features(crkdg_t h, float *feat, int on_device) {
+    if (!h || !feat) return CRKDG_E_ARG;
+    if (!h->feat) return fail(h, CRKDG_E_ARG, "last_features: needs a 2D handle with an indicator");
+    CK(h, cudaMemcpyAsync(feat, h->feat, (size_t)h->ncell * CRKDG_MLP_NIN * sizeof(float),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    return CRKDG_OK;
+}
+
 crkdg_status crkdg_cell_averages(crkdg_t h, double *avg, int on_device) {
     if (!h || !avg) return CRKDG_E_ARG;
     Params P = base_params(h);
-    Bufs B = base_bufs(h);
-    CK(h, launch(h, K_AVG, P, B));
+    if (h->mixed) {
+        CK(h, launch_x(h, KX_AVG, P, base_xbufs(h)));
+    } else {
+        Bufs B = base_bufs(h);
+        CK(h, launch(h, K_AVG, P, B));
+    }
     CK(h, cudaMemcpyAsync(avg, h->aux, (size_t)h->ncell * h->m * sizeof(double),
                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
     CK(h, cudaStreamSynchronize(h->st));
@@ -569,8 +912,12 @@ crkdg_status crkdg_bound_margins(crkdg_t h, double margins[2]) {
     crkdg_status s = reset_scalars(h);
     if (s) return s;
     Params P = base_params(h);
-    Bufs B = base_bufs(h);
-    CK(h, launch(h, K_MARGINS, P, B));
+    if (h->mixed) {
+        CK(h, launch_x(h, KX_SCAN, P, base_xbufs(h)));
+    } else {
+        Bufs B = base_bufs(h);
+        CK(h, launch(h, K_MARGINS, P, B));
+    }
     s = read_scalars(h);
     if (s) return s;
     margins[0] = from_ordbits(h->hs->ord[0]);

@@ -89,6 +89,18 @@ void tables(NodalTables *tab) {
         }
         for (int b = 0; b < n; ++b)
             for (int a = 0; a < n; ++a) T.w2[b * n + a] = 0.25 * T.wg[a] * T.wg[b];
+        for (int a = 0; a < MAXN; ++a) {
+            for (int q = 0; q < MAXN; ++q) {
+                T.Dhatf[a][q] = (float)T.Dhat[a][q];
+                T.Iglf[a][q] = (float)T.Igl[a][q];
+            }
+            T.lmf[a] = (float)T.lm[a];
+            T.lpf[a] = (float)T.lp[a];
+            T.liftmf[a] = (float)T.liftm[a];
+            T.liftpf[a] = (float)T.liftp[a];
+            T.w1f[a] = (float)T.w1[a];
+        }
+        for (int q = 0; q < MAXN * MAXN; ++q) T.w2f[q] = (float)T.w2[q];
     }
 }
 

@@ -174,6 +174,8 @@ __device__ __forceinline__ int neighbour(const Params &P, int cell, int side) {
 template <int DIM, int N, int PHYS>
 struct Cfg {
     static constexpr int D = DIM;
+    static constexpr int NP = N;
+    static constexpr int PH = PHYS;
     static constexpr int M = ncomp(PHYS, DIM);
     static constexpr int NN = DIM == 2 ? N * N : N;       // nodes per cell
     static constexpr int NF = DIM == 2 ? N : 1;           // quadrature points per face
@@ -267,12 +269,10 @@ __device__ __forceinline__ double retry_factor(int attempt) {
 // collective.  u: this thread's node values (in/out).  pts: on return the values
 // at this thread's S_K points of the limited polynomial.  With check_avg the
 // admissibility of the cell average sets *B.flag (Sec. 4.1 restart test).
-template <int DIM, int N, int PHYS>
-__device__ void limit_block(const Params &P, const Bufs &B, Smem<Cfg<DIM, N, PHYS>> &S, int lc,
-                            int node, bool active, double *u,
-                            double (&pts)[Cfg<DIM, N, PHYS>::PPT][ncomp(PHYS, DIM)], bool check_avg,
-                            bool stats) {
-    using C = Cfg<DIM, N, PHYS>;
+template <class C>
+__device__ void limit_block(const Params &P, const Bufs &B, Smem<C> &S, int lc, int node, bool active,
+                            double *u, double (&pts)[C::PPT][C::M], bool check_avg, bool stats) {
+    constexpr int DIM = C::D, N = C::NP, PHYS = C::PH;
     constexpr int M = C::M, NN = C::NN, NSK = C::NSK, PPT = C::PPT;
     const NodalTables &T = c_tab[N - 2];
 
@@ -415,10 +415,10 @@ __device__ void limit_block(const Params &P, const Bufs &B, Smem<Cfg<DIM, N, PHY
 
 // G(u) at this thread's node (block collective).  trs receives the interior
 // trace states of this thread's face points.
-template <int DIM, int N, int PHYS>
-__device__ void eval_G(const Params &P, Smem<Cfg<DIM, N, PHYS>> &S, int lc, int node, const double *u,
-                       double *g, double (&trs)[Cfg<DIM, N, PHYS>::FPT][ncomp(PHYS, DIM)]) {
-    using C = Cfg<DIM, N, PHYS>;
+template <class C>
+__device__ void eval_G(const Params &P, Smem<C> &S, int lc, int node, const double *u, double *g,
+                       double (&trs)[C::FPT][C::M]) {
+    constexpr int DIM = C::D, N = C::NP, PHYS = C::PH;
     constexpr int M = C::M, NN = C::NN, NF = C::NF, NTR = C::NTR, FPT = C::FPT;
     const NodalTables &T = c_tab[N - 2];
     const int a = node % N, b = DIM == 2 ? node / N : 0;
@@ -545,10 +545,10 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_inner(Params P, Bufs 
                 cur[c] = v;
             }
             double pts[C::PPT][M];
-            limit_block<DIM, N, PHYS>(P, B, S, lc, node, active, cur, pts, true, true);
+            limit_block(P, B, S, lc, node, active, cur, pts, true, true);
         }
         double trs[FPT][M];
-        eval_G<DIM, N, PHYS>(P, S, lc, node, cur, gh[i], trs);
+        eval_G(P, S, lc, node, cur, gh[i], trs);
         if (P.mode == MODE_OP_G) {
 #pragma unroll
             for (int c = 0; c < M; ++c) acc[c] = gh[i][c];
@@ -672,8 +672,24 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_final(Params P, Bufs 
         store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
         return;
     }
+    if (P.defer_limit) {  // averages and their admissibility here; limiters in k_trouble
+#pragma unroll
+        for (int c = 0; c < M; ++c) S.u[lc][c][node] = u[c];
+        __syncthreads();
+        for (int c = node; c < M; c += NN) {
+            double s = 0.0;
+#pragma unroll
+            for (int q = 0; q < NN; ++q) s = fma(DIM == 2 ? T.w2[q] : T.w1[q], S.u[lc][c][q], s);
+            S.avg[lc][c] = s;
+            if (active) B.aux[(size_t)cell * M + c] = s;
+        }
+        __syncthreads();
+        if (node == 0 && active && !admissible<PHYS, DIM>(P, S.avg[lc])) atomicOr(B.flag, 1);
+        store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
+        return;
+    }
     double pts[C::PPT][M];
-    limit_block<DIM, N, PHYS>(P, B, S, lc, node, active, u, pts, true, true);
+    limit_block(P, B, S, lc, node, active, u, pts, true, true);
     // wave-speed rate of the new state over its S_K points (next trial step)
     double amax = 0.0;
 #pragma unroll
@@ -697,7 +713,7 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_limit(Params P, Bufs 
     const bool active = cell < P.ncell;
     double u[C::M], pts[C::PPT][C::M];
     load_node<DIM, N, PHYS>(P, B.un, cell, node, active, u);
-    limit_block<DIM, N, PHYS>(P, B, S, lc, node, active, u, pts, false, false);
+    limit_block(P, B, S, lc, node, active, u, pts, false, false);
     store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
 }
 
@@ -764,6 +780,202 @@ __global__ void k_avg(Params P, Bufs B) {
     B.aux[t] = s;
 }
 
+__device__ __forceinline__ double minmod3d(double a, double b, double c) {
+    if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(a, fmin(b, c));
+    if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
+    return 0.0;
+}
+
+// Plain troubled-cell indicator and shock limiter, then the scaling limiter (an
+// optional anti-oscillation stage outside the paper's method, run once per step
+// after the final stage so the inner stages stay compact).  Per component and
+// direction: face-averaged trace deviations ut_R = avg_face(u_R) - ubar,
+// ut_L = ubar - avg_face(u_L) against D+ / D- of the cell averages (neighbours
+// across a boundary follow its condition); the cell is troubled if the
+// TVB-modified minmod changes either deviation.  A troubled cell becomes
+// ubar + minmod(c_x, D+x, D-x) xi + minmod(c_y, D+y, D-y) eta, with c_x, c_y its
+// first Legendre moments.  Reads unew and the averages in aux; writes unew.
+template <int DIM, int N, int PHYS>
+__global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_trouble(Params P, Bufs B) {
+    using C = Cfg<DIM, N, PHYS>;
+    constexpr int M = C::M, NN = C::NN;
+    __shared__ Smem<C> S;
+    __shared__ double sP1[C::NCB][2][M];
+    __shared__ int sTr[C::NCB];
+    const NodalTables &T = c_tab[N - 2];
+    const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
+    const int cell = blockIdx.x * C::NCB + lc;
+    const bool active = cell < P.ncell;
+    const int a = node % N, b = DIM == 2 ? node / N : 0;
+    double u[M];
+    load_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
+#pragma unroll
+    for (int c = 0; c < M; ++c) S.u[lc][c][node] = u[c];
+    if (node == 0) sTr[lc] = 0;
+    __syncthreads();
+    if (node < DIM && active) {  // thread d handles direction d for every component (decision and limited slopes)
+        const int d = node;
+        const double h = 2.0 / (d == 0 ? P.rhx : P.rhy);
+        const double thr = P.tvb_M * h * h;
+        double own[M], lo[M], hi[M];
+#pragma unroll
+        for (int c = 0; c < M; ++c) own[c] = B.aux[(size_t)cell * M + c];
+        int nl = neighbour(P, cell, 2 * d), nh = neighbour(P, cell, 2 * d + 1);
+        if (nl >= 0) {
+#pragma unroll
+            for (int c = 0; c < M; ++c) lo[c] = B.aux[(size_t)nl * M + c];
+        } else {
+            boundary_state<PHYS, DIM>(P, 2 * d, own, lo);
+        }
+        if (nh >= 0) {
+#pragma unroll
+            for (int c = 0; c < M; ++c) hi[c] = B.aux[(size_t)nh * M + c];
+        } else {
+            boundary_state<PHYS, DIM>(P, 2 * d + 1, own, hi);
+        }
+        int trouble = 0;
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            double fr = 0.0, fl = 0.0, p1 = 0.0;
+            for (int q = 0; q < NN; ++q) {
+                int qa = q % N, qb = DIM == 2 ? q / N : 0;
+                int along = d == 0 ? qa : qb, across = d == 0 ? qb : qa;
+                double wa = DIM == 2 ? T.w1[across] : 1.0;
+                double v = S.u[lc][c][q];
+                fr = fma(wa * T.lp[along], v, fr);
+                fl = fma(wa * T.lm[along], v, fl);
+                p1 = fma(3.0 * T.w1[qa] * (DIM == 2 ? T.w1[qb] : 1.0) * T.xg[along], v, p1);
+            }
+            double utR = fr - own[c], utL = own[c] - fl;
+            double dp = hi[c] - own[c], dm = own[c] - lo[c];
+            double mR = fabs(utR) <= thr ? utR : minmod3d(utR, dp, dm);
+            double mL = fabs(utL) <= thr ? utL : minmod3d(utL, dp, dm);
+            if (mR != utR || mL != utL) trouble = 1;
+            sP1[lc][d][c] = minmod3d(p1, dp, dm);
+        }
+        if (trouble) atomicOr(&sTr[lc], 1);
+    }
+    __syncthreads();
+    if (P.ind_stage == 1) {  // decision only: the flags go to memory
+        if (node == 0 && active) B.tflags[cell] = sTr[lc] != 0 ? 1 : 0;
+        return;
+    }
+    const bool troubled = active && (P.ind_stage == 2 ? B.tflags[cell] != 0 : sTr[lc] != 0);
+    if (troubled) {
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            double v = fma(sP1[lc][0][c], T.xg[a], B.aux[(size_t)cell * M + c]);
+            if constexpr (DIM == 2) v = fma(sP1[lc][1][c], T.xg[b], v);
+            u[c] = v;
+        }
+    }
+    if (node == 0 && active) {
+        if (B.tflags && P.ind_stage == 0) B.tflags[cell] = troubled ? 1 : 0;
+        if (troubled) atomicAdd(B.ntrb, 1ull);
+    }
+    double pts[C::PPT][M];
+    limit_block(P, B, S, lc, node, active, u, pts, false, true);
+    double amax = 0.0;
+#pragma unroll
+    for (int j = 0; j < C::PPT; ++j) {
+        int p = node + j * NN;
+        if (p < C::NSK && active) amax = fmax(amax, sk_rate<PHYS, DIM>(P, pts[j]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if ((threadIdx.x & 31) == 0 && amax > 0.0) atomicMax(B.a0, dbits(amax));
+    store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
+}
+
+// MLP features of every cell (2D Euler): per component, the 3x3 neighbourhood of
+// cell averages (neighbours across a boundary follow its condition) normalised by the
+// stencil mean and range, and the cell's first Legendre moments over the same range.
+// Layout [cell][44]: 36 normalised averages ([comp][9], row-major, centre 4), then
+// 8 normalised moments ([comp][x, y]).  Reads unew and the averages in aux.
+template <int DIM, int N, int PHYS>
+__global__ void k_features(Params P, Bufs B) {
+    constexpr int M = ncomp(PHYS, DIM);
+    constexpr int NN = DIM == 2 ? N * N : N;
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if constexpr (DIM != 2 || PHYS != PH_EULER) {
+        return;
+    } else {
+        if (cell >= P.ncell) return;
+        const NodalTables &T = c_tab[N - 2];
+        // 3x3 stencil; a position outside the domain takes the nearest in-domain cell's
+        // average with the boundary state of each crossed side applied (x side first)
+        double v[9][M];
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                int cx = cell;
+                bool xout = false, yout = false;
+                if (dx != 0) {
+                    int nb = neighbour(P, cell, dx < 0 ? 0 : 1);
+                    if (nb >= 0) cx = nb; else xout = true;
+                }
+                int cy = cx;
+                if (dy != 0) {
+                    int nb = neighbour(P, cx, dy < 0 ? 2 : 3);
+                    if (nb >= 0) cy = nb; else yout = true;
+                }
+                double val[M], tmp[M];
+#pragma unroll
+                for (int c = 0; c < M; ++c) val[c] = B.aux[(size_t)cy * M + c];
+                if (xout) {
+                    boundary_state<PHYS, DIM>(P, dx < 0 ? 0 : 1, val, tmp);
+#pragma unroll
+                    for (int c = 0; c < M; ++c) val[c] = tmp[c];
+                }
+                if (yout) {
+                    boundary_state<PHYS, DIM>(P, dy < 0 ? 2 : 3, val, tmp);
+#pragma unroll
+                    for (int c = 0; c < M; ++c) val[c] = tmp[c];
+                }
+#pragma unroll
+                for (int c = 0; c < M; ++c) v[(dy + 1) * 3 + (dx + 1)][c] = val[c];
+            }
+        float *f = B.feat + (size_t)cell * 44;
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            double mean = 0.0, mx = -INFINITY, mn = INFINITY, amax = 0.0;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                mean += v[q][c];
+                mx = fmax(mx, v[q][c]);
+                mn = fmin(mn, v[q][c]);
+                amax = fmax(amax, fabs(v[q][c]));
+            }
+            mean /= 9.0;
+            double scale = 1.0 / ((mx - mn) + (1e-12 * amax + 1e-30));
+#pragma unroll
+            for (int q = 0; q < 9; ++q) f[c * 9 + q] = (float)((v[q][c] - mean) * scale);
+            const double *u = B.unew + ((size_t)c * P.ncell + cell) * NN;
+            double cx = 0.0, cy = 0.0;
+#pragma unroll
+            for (int q = 0; q < NN; ++q) {
+                int qa = q % N, qb = q / N;
+                double w = 3.0 * T.w1[qa] * T.w1[qb] * u[q];
+                cx = fma(w, T.xg[qa], cx);
+                cy = fma(w, T.xg[qb], cy);
+            }
+            f[36 + 2 * c] = (float)(cx * scale);
+            f[37 + 2 * c] = (float)(cy * scale);
+        }
+    }
+}
+
+// Learned flags: troubled when the probability is above 0.6, smooth below 0.4, and the
+// plain indicator's decision (already in tflags) in between.
+static __global__ void k_combine(Params P, Bufs B) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= P.ncell) return;
+    float p = B.prob[cell];
+    if (p > 0.6f) B.tflags[cell] = 1;
+    else if (p < 0.4f) B.tflags[cell] = 0;
+}
+
 template <int DIM, int N, int PHYS>
 cudaError_t launch_one(int kernel, int nblocks, cudaStream_t st, const Params &P, const Bufs &B) {
     using C = Cfg<DIM, N, PHYS>;
@@ -771,6 +983,9 @@ cudaError_t launch_one(int kernel, int nblocks, cudaStream_t st, const Params &P
     case K_INNER: k_inner<DIM, N, PHYS><<<nblocks, C::NT, 0, st>>>(P, B); break;
     case K_FINAL: k_final<DIM, N, PHYS><<<nblocks, C::NT, 0, st>>>(P, B); break;
     case K_LIMIT: k_limit<DIM, N, PHYS><<<nblocks, C::NT, 0, st>>>(P, B); break;
+    case K_TROUBLE: k_trouble<DIM, N, PHYS><<<nblocks, C::NT, 0, st>>>(P, B); break;
+    case K_FEATURES: k_features<DIM, N, PHYS><<<(P.ncell + 127) / 128, 128, 0, st>>>(P, B); break;
+    case K_COMBINE: k_combine<<<(P.ncell + 255) / 256, 256, 0, st>>>(P, B); break;
     case K_A0:
     case K_MARGINS: k_scan<DIM, N, PHYS><<<nblocks, C::NT, 0, st>>>(P, B); break;
     case K_AVG: {

@@ -1,0 +1,970 @@
+// dg_mixed.cuh -- split-precision cRKDG path: FP64 cell averages, FP32 nodal
+// deviations, every operator evaluated in FP32.
+//
+// State of a cell: ubar (FP64, one value per component) and dev (FP32, one per
+// node); the polynomial is ubar + (dev - dbar)(x) with dbar the Gauss-weighted
+// mean of dev, so the cell average is exactly ubar.
+//
+// Per stage:
+//   * G is evaluated in FP32 (flux, volume term, traces, lift); its deviation part
+//     G32 - mean(G32) updates dev, and its average (eq. Gbar, the weighted sum of the
+//     FP32 interior-trace fluxes) increments the FP64 stage average of the cell.
+//   * The final stage updates ubar with the FP64 sum over the cell's face points of
+//     sum_i b_i fhat^(i) (local conservation, Sec. 3.2); each face value is computed
+//     identically by both cells, so the global sum is conserved to FP64 round-off.
+//   * The scaling limiter keeps FP64 where bounds are decided: the S_K values are
+//     screened in FP32 with a rigorous rounding margin, and only cells that the
+//     screen cannot clear are evaluated as ubar + (double)(FP32 interpolation) in
+//     FP64, where theta is solved and the result verified (the same rounding safety
+//     rule as the FP64 path).
+#pragma once
+
+#include "dg_core.cuh"
+
+namespace crkdg {
+
+// ----------------------------------------------------------------------------- FP32 physics
+
+template <int PHYS, int DIM>
+__device__ __forceinline__ void flux_dir_f(const Params &P, const float *u, int dir, float *f) {
+    if constexpr (PHYS == PH_ADV) {
+        f[0] = (float)(dir == 0 ? P.velx : P.vely) * u[0];
+    } else if constexpr (PHYS == PH_BURG) {
+        f[0] = 0.5f * u[0] * u[0];
+    } else if constexpr (DIM == 1) {
+        float ri = 1.0f / u[0];
+        float w = u[1] * ri;
+        float p = (float)(P.gamma - 1.0) * (u[2] - 0.5f * u[1] * w);
+        f[0] = u[1];
+        f[1] = u[1] * w + p;
+        f[2] = (u[2] + p) * w;
+    } else {
+        float ri = 1.0f / u[0];
+        float wx = u[1] * ri, wy = u[2] * ri;
+        float p = (float)(P.gamma - 1.0) * (u[3] - 0.5f * (u[1] * wx + u[2] * wy));
+        float wd = dir == 0 ? wx : wy;
+        f[0] = u[1 + dir];
+        f[1] = u[1] * wd + (dir == 0 ? p : 0.0f);
+        f[2] = u[2] * wd + (dir == 1 ? p : 0.0f);
+        f[3] = (u[3] + p) * wd;
+    }
+}
+
+template <int PHYS>
+__device__ __forceinline__ void flux_xy_f(const Params &P, const float *u, float *fx, float *fy) {
+    if constexpr (PHYS == PH_ADV) {
+        fx[0] = (float)P.velx * u[0];
+        fy[0] = (float)P.vely * u[0];
+    } else if constexpr (PHYS == PH_BURG) {
+        fx[0] = fy[0] = 0.5f * u[0] * u[0];
+    } else {
+        float ri = 1.0f / u[0];
+        float wx = u[1] * ri, wy = u[2] * ri;
+        float p = (float)(P.gamma - 1.0) * (u[3] - 0.5f * (u[1] * wx + u[2] * wy));
+        float ep = u[3] + p;
+        fx[0] = u[1];
+        fx[1] = u[1] * wx + p;
+        fx[2] = u[2] * wx;
+        fx[3] = ep * wx;
+        fy[0] = u[2];
+        fy[1] = u[1] * wy;
+        fy[2] = u[2] * wy + p;
+        fy[3] = ep * wy;
+    }
+}
+
+template <int PHYS, int DIM>
+__device__ __forceinline__ float speed_dir_f(const Params &P, const float *u, int dir) {
+    if constexpr (PHYS == PH_ADV) {
+        return fabsf((float)(dir == 0 ? P.velx : P.vely));
+    } else if constexpr (PHYS == PH_BURG) {
+        return fabsf(u[0]);
+    } else {
+        float ri = 1.0f / u[0];
+        float kin = DIM == 1 ? u[1] * u[1] : u[1] * u[1] + u[2] * u[2];
+        float g = (float)P.gamma;
+        float p = (g - 1.0f) * (u[DIM + 1] - 0.5f * kin * ri);
+        float c2 = g * p * ri;
+        float c = c2 > 0.0f ? sqrtf(c2) : 0.0f;
+        return fabsf(u[1 + dir] * ri) + c;
+    }
+}
+
+template <int PHYS, int DIM>
+__device__ __forceinline__ void boundary_state_f(const Params &P, int side, const float *ui, float *ue) {
+    constexpr int M = ncomp(PHYS, DIM);
+    int bc = P.bc[side];
+    if (bc == BC_DIRICHLET) {
+#pragma unroll
+        for (int c = 0; c < M; ++c) ue[c] = (float)P.bcs[side][c];
+    } else {
+#pragma unroll
+        for (int c = 0; c < M; ++c) ue[c] = ui[c];
+        if constexpr (PHYS == PH_EULER) {
+            if (bc == BC_REFLECT) ue[1 + side / 2] = -ui[1 + side / 2];
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------- block storage
+
+template <class C>
+struct SmemX {
+    float u[C::NCB][C::M][C::NN];     // node values (or deviations in the limiter)
+    float f[C::D][C::NCB][C::M][C::NN];
+    float tf[C::NCB][C::NTR][C::M];   // trace fluxes / face corrections
+    float fh[C::NCB][C::NTR][C::M];   // sum_i b_i fhat^(i) at the face points
+    float w[C::NCB][C::M][C::NN];     // weighted values for the per-cell FP32 means
+    float ubf[C::NCB][C::M];          // FP32 copy of the averages
+    float mean[C::NCB][C::M];
+    double gb[C::NCB][C::M];          // FP64 face sums
+    double ubd[C::NCB][C::M];         // FP64 averages of the current stage
+    float gbf[C::NCB][C::M];          // FP32 average of G (eq. Gbar)
+    double kap[C::NTR];               // face-sum weights -sgn * w_pos / h_dir
+    float kapf[C::NTR];
+    union {  // never live at the same time
+        double redd[C::NCB][C::NN][2];
+        float al[C::NCB][C::NTR];
+        double term[C::NCB][C::NTR][C::M];
+    };
+    double th[C::NCB][2];
+    int fl[C::NCB][C::NN];
+    int unsafe[C::NCB];
+    int bad[C::NCB];
+};
+
+// Gauss weight of node q (normalised: the weights of a cell sum to 1)
+template <int DIM, int N>
+__device__ __forceinline__ float wnode_f(int q) {
+    const NodalTables &T = c_tab[N - 2];
+    return DIM == 2 ? T.w2f[q] : T.w1f[q];
+}
+
+template <class C>
+__device__ __forceinline__ void init_kappa(const Params &P, SmemX<C> &S) {
+    const NodalTables &T = c_tab[C::NP - 2];
+    for (int fp = threadIdx.x; fp < C::NTR; fp += blockDim.x) {
+        int face = fp / C::NF, pos = fp - face * C::NF;
+        double wbar = C::D == 2 ? T.w1[pos] : 1.0;
+        double rh = face < 2 ? P.rhx : P.rhy;
+        S.kap[fp] = ((face & 1) ? -0.5 : 0.5) * wbar * rh;  // -sgn(face) * wbar / h
+        S.kapf[fp] = (float)S.kap[fp];
+    }
+}
+
+// FP32 interpolation of node data q[c][node] of one cell to S_K point p
+template <int DIM, int N, int M, int NN>
+__device__ __forceinline__ void sk_eval_f(const float (&q)[M][NN], int p, float *v) {
+    const NodalTables &T = c_tab[N - 2];
+    constexpr int L = nlob(N);
+    if constexpr (DIM == 1) {
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            float s = 0.0f;
+#pragma unroll
+            for (int a = 0; a < N; ++a) s = fmaf(T.Iglf[p][a], q[c][a], s);
+            v[c] = s;
+        }
+    } else if (p < N * L) {
+        int beta = p / L, al = p - beta * L;
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            float s = 0.0f;
+#pragma unroll
+            for (int a = 0; a < N; ++a) s = fmaf(T.Iglf[al][a], q[c][beta * N + a], s);
+            v[c] = s;
+        }
+    } else {
+        int r = p - N * L;
+        int beta = r / L, al = r - beta * L;
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            float s = 0.0f;
+#pragma unroll
+            for (int b = 0; b < N; ++b) s = fmaf(T.Iglf[al][b], q[c][b * N + beta], s);
+            v[c] = s;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------- G in FP32
+
+// gd: deviation part of G at this node (FP32, cell mean removed); gb: the cell
+// average of G as the FP64 sum of the FP32 interior-trace fluxes (eq. Gbar).
+template <class C>
+__device__ void eval_G_x(const Params &P, SmemX<C> &S, int lc, int node, const float *dv, float *gd,
+                         float (&trs)[C::FPT][C::M]) {
+    constexpr int DIM = C::D, N = C::NP, PHYS = C::PH;
+    constexpr int M = C::M, NN = C::NN, NF = C::NF, NTR = C::NTR, FPT = C::FPT;
+    const NodalTables &T = c_tab[N - 2];
+    const int a = node % N, b = DIM == 2 ? node / N : 0;
+    // S.ubf holds the FP32 copy of the stage averages (written by the caller)
+    {
+        float u[M], fx[M], fy[M];
+#pragma unroll
+        for (int c = 0; c < M; ++c) u[c] = S.ubf[lc][c] + dv[c];
+        if constexpr (DIM == 2) {
+            flux_xy_f<PHYS>(P, u, fx, fy);
+        } else {
+            flux_dir_f<PHYS, DIM>(P, u, 0, fx);
+        }
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            S.u[lc][c][node] = u[c];
+            S.f[0][lc][c][node] = fx[c];
+            if constexpr (DIM == 2) S.f[1][lc][c][node] = fy[c];
+        }
+    }
+    __syncthreads();
+    float vx[M], vy[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+        float s = 0.0f;
+#pragma unroll
+        for (int q = 0; q < N; ++q) s = fmaf(T.Dhatf[a][q], S.f[0][lc][c][b * N + q], s);
+        vx[c] = s;
+        if constexpr (DIM == 2) {
+            float t = 0.0f;
+#pragma unroll
+            for (int r = 0; r < N; ++r) t = fmaf(T.Dhatf[b][r], S.f[1][lc][c][r * N + a], t);
+            vy[c] = t;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < FPT; ++j) {
+        int fp = node + j * NN;
+        if (fp < NTR) {
+            int face = fp / NF, pos = fp - face * NF;
+            const float *l = (face & 1) ? T.lpf : T.lmf;
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                float s = 0.0f;
+                if (DIM == 1 || face < 2) {
+#pragma unroll
+                    for (int q = 0; q < N; ++q) s = fmaf(l[q], S.u[lc][c][pos * N + q], s);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < N; ++q) s = fmaf(l[q], S.u[lc][c][q * N + pos], s);
+                }
+                trs[j][c] = s;
+            }
+            float f[M];
+            flux_dir_f<PHYS, DIM>(P, trs[j], face >> 1, f);
+#pragma unroll
+            for (int c = 0; c < M; ++c) S.tf[lc][fp][c] = f[c];
+        }
+    }
+    __syncthreads();
+    const float rhx = (float)P.rhx, rhy = (float)P.rhy;
+    float g32[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+        float gx = vx[c] - T.liftpf[a] * S.tf[lc][NF + b][c] + T.liftmf[a] * S.tf[lc][b][c];
+        float gv = rhx * gx;
+        if constexpr (DIM == 2) {
+            float gy = vy[c] - T.liftpf[b] * S.tf[lc][3 * NF + a][c] + T.liftmf[b] * S.tf[lc][2 * NF + a][c];
+            gv = fmaf(rhy, gy, gv);
+        }
+        g32[c] = gv;
+        S.w[lc][c][node] = wnode_f<DIM, N>(node) * gv;
+    }
+    __syncthreads();
+    for (int c = node; c < M; c += NN) {
+        float m = 0.0f, g = 0.0f;
+        for (int q = 0; q < NN; ++q) m += S.w[lc][c][q];
+        for (int fp = 0; fp < NTR; ++fp) g = fmaf(S.kapf[fp], S.tf[lc][fp][c], g);
+        S.mean[lc][c] = m;
+        S.gbf[lc][c] = g;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < M; ++c) gd[c] = g32[c] - S.mean[lc][c];
+}
+
+// ----------------------------------------------------------------------------- limiter
+
+// The FP64 evaluation of the represented polynomial at S_K point p:
+// ubar + (double)(FP32 interpolation of dev - dbar).  Defines "in the bounds".
+template <class C>
+__device__ __forceinline__ void eval64_x(SmemX<C> &S, int lc, int p, const double *ub, double *v, float *v32) {
+    constexpr int M = C::M;
+    float s[M];
+    sk_eval_f<C::D, C::NP, M, C::NN>(S.u[lc], p, s);
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+        float d = s[c] - S.mean[lc][c];
+        v[c] = ub[c] + (double)d;
+        v32[c] = S.ubf[lc][c] + d;
+    }
+}
+
+// Publishes dev of every node of the block and the FP32 mean of each cell.
+template <class C>
+__device__ __forceinline__ void publish_dev(const double *ub, const float *dv, SmemX<C> &S, int lc, int node) {
+    constexpr int M = C::M, NN = C::NN;
+    (void)ub;  // S.ubf already holds the FP32 copy of the averages
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+        S.u[lc][c][node] = dv[c];
+        S.w[lc][c][node] = wnode_f<C::D, C::NP>(node) * dv[c];
+    }
+    __syncthreads();
+    for (int c = node; c < M; c += NN) {
+        float m = 0.0f;
+        for (int q = 0; q < NN; ++q) m += S.w[lc][c][q];
+        S.mean[lc][c] = m;
+    }
+    __syncthreads();
+}
+
+// Scaling limiter of the split representation (block collective).  ub is not
+// changed (the limiter keeps averages); dv is rescaled in place.  pts receives
+// FP32 values at this thread's S_K points of the limited polynomial.
+template <class C>
+__device__ void limit_x(const Params &P, const Bufs &B, SmemX<C> &S, int lc, int node, bool active,
+                        const double *ub, float *dv, bool check_avg, bool stats, float (&pts)[C::PPT][C::M]) {
+    constexpr int DIM = C::D, PHYS = C::PH;
+    constexpr int M = C::M, NN = C::NN, NSK = C::NSK, PPT = C::PPT;
+    const float tiny_rel = 2.384185791015625e-07f;  // 2^-22: margin of the screen on a component
+    const float re_rel = 3.814697265625e-06f;       // 2^-18: margin of the screen on rho*e
+    publish_dev(ub, dv, S, lc, node);
+    // 1. FP32 screen of the S_K values with a rounding margin
+    int unsafe = 0;
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+        int p = node + j * NN;
+        if (p < NSK) {
+            float s[M];
+            sk_eval_f<DIM, C::NP, M, NN>(S.u[lc], p, s);
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                float d = s[c] - S.mean[lc][c];
+                pts[j][c] = S.ubf[lc][c] + d;
+            }
+            if constexpr (PHYS == PH_EULER) {
+                // |FP64 evaluation - FP32 value| <= 2^-23 (|v| + |vbar|) per component (doubled
+                // here); propagate to rho e = E - |m|^2 / (2 rho) to first order plus the
+                // FP32 rounding of the formula itself
+                const float *v = pts[j];
+                const float *vb = S.ubf[lc];
+                const float epsf = (float)P.eps * 1.0000002f;
+                float dr = tiny_rel * (fabsf(v[0]) + fabsf(vb[0]));
+                float kin = 0.0f, dkin = 0.0f;
+#pragma unroll
+                for (int d = 1; d <= DIM; ++d) {
+                    kin += v[d] * v[d];
+                    dkin += 2.0f * fabsf(v[d]) * tiny_rel * (fabsf(v[d]) + fabsf(vb[d]));
+                }
+                float de = tiny_rel * (fabsf(v[DIM + 1]) + fabsf(vb[DIM + 1]));
+                if (!(v[0] - dr >= epsf) || !(v[0] > 0.0f)) {
+                    unsafe = 1;
+                } else {
+                    float hk = 0.5f * kin / v[0];
+                    float re = v[DIM + 1] - hk;
+                    float dre = de + 0.5f * dkin / (v[0] - dr) + hk * dr / (v[0] - dr) +
+                                re_rel * (fabsf(v[DIM + 1]) + hk);
+                    if (!(re - dre >= epsf)) unsafe = 1;
+                }
+            } else {
+                float mr = tiny_rel * (fabsf(pts[j][0]) + fabsf(S.ubf[lc][0]));
+                if (!(pts[j][0] - mr >= (float)P.lo) || !(pts[j][0] + mr <= (float)P.hi)) unsafe = 1;
+            }
+        }
+    }
+    S.fl[lc][node] = unsafe;
+    __syncthreads();
+    if (node == 0) {
+        int any = 0;
+        for (int q = 0; q < NN; ++q) any |= S.fl[lc][q];
+        if (check_avg && active && !admissible<PHYS, DIM>(P, ub)) atomicOr(B.flag, 1);
+        S.unsafe[lc] = any;
+        S.bad[lc] = 0;
+    }
+    __syncthreads();
+    const bool cell_unsafe = S.unsafe[lc] != 0;
+    if (!__syncthreads_or(cell_unsafe)) return;
+
+    // 2. FP64 theta for the cells the screen could not clear
+    double th1 = 1.0, th2 = 1.0;
+    double pmin = INFINITY, pmax = -INFINITY;
+    if (cell_unsafe) {
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            int p = node + j * NN;
+            if (p < NSK) {
+                double v[M];
+                float v32[M];
+                eval64_x(S, lc, p, ub, v, v32);
+                pmin = (v[0] == v[0]) ? fmin(pmin, v[0]) : -INFINITY;
+                pmax = fmax(pmax, v[0]);
+            }
+        }
+    }
+    S.redd[lc][node][0] = pmin;
+    S.redd[lc][node][1] = pmax;
+    __syncthreads();
+    if (node == 0 && cell_unsafe) {
+        double mn = INFINITY, mx = -INFINITY;
+        for (int q = 0; q < NN; ++q) {
+            mn = fmin(mn, S.redd[lc][q][0]);
+            mx = fmax(mx, S.redd[lc][q][1]);
+        }
+        double th = 1.0;
+        if constexpr (PHYS == PH_EULER) {
+            if (mn < P.eps) th = ratio01(ub[0] - P.eps, ub[0] - mn);
+        } else {
+            if (mx > P.hi) th = fmin(th, ratio01(P.hi - ub[0], mx - ub[0]));
+            if (mn < P.lo) th = fmin(th, ratio01(ub[0] - P.lo, ub[0] - mn));
+        }
+        S.th[lc][0] = th < 1.0 ? th * kMargin : th;
+        S.th[lc][1] = 1.0;
+    }
+    __syncthreads();
+    if (cell_unsafe) th1 = S.th[lc][0];
+    if constexpr (PHYS == PH_EULER) {
+        double pm = INFINITY;
+        if (cell_unsafe) {
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                int p = node + j * NN;
+                if (p < NSK) {
+                    double v[M];
+                    float v32[M];
+                    eval64_x(S, lc, p, ub, v, v32);
+                    if (th1 < 1.0) v[0] = th1 * (v[0] - ub[0]) + ub[0];
+                    double re = rho_e<DIM>(v);
+                    pm = (re == re) ? fmin(pm, re) : -INFINITY;
+                }
+            }
+        }
+        S.redd[lc][node][1] = pm;
+        __syncthreads();
+        if (node == 0 && cell_unsafe) {
+            double mn = INFINITY;
+            for (int q = 0; q < NN; ++q) mn = fmin(mn, S.redd[lc][q][1]);
+            double reb = rho_e<DIM>(ub);
+            S.th[lc][1] = (mn >= P.eps) ? 1.0 : ratio01(reb - P.eps, reb - mn) * kMargin;
+        }
+        __syncthreads();
+        if (cell_unsafe) th2 = S.th[lc][1];
+    }
+    // 3. rescale the deviations towards the average; verify with the FP64 evaluation
+    const bool limited = cell_unsafe && (th1 < 1.0 || th2 < 1.0);
+    float dvo[M], dbar[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+        dvo[c] = dv[c];
+        dbar[c] = S.mean[lc][c];
+    }
+    auto apply = [&](double t2) {
+        if constexpr (PHYS == PH_EULER) {
+            float s0 = (float)(th1 * t2);
+            float s1 = (float)t2;
+            dv[0] = s0 * (dvo[0] - dbar[0]);
+#pragma unroll
+            for (int c = 1; c < M; ++c) dv[c] = s1 * (dvo[c] - dbar[c]);
+        } else {
+            dv[0] = (float)(th1 * t2) * (dvo[0] - dbar[0]);
+        }
+    };
+    double tfin = th2;
+    if (limited) apply(th2);
+    if (__syncthreads_or(limited)) {
+        for (int attempt = 0; attempt <= 4; ++attempt) {
+            publish_dev(ub, dv, S, lc, node);
+            bool viol = false;
+            if (limited) {
+#pragma unroll
+                for (int j = 0; j < PPT; ++j) {
+                    int p = node + j * NN;
+                    if (p < NSK) {
+                        double v[M];
+                        float v32[M];
+                        eval64_x(S, lc, p, ub, v, v32);
+#pragma unroll
+                        for (int c = 0; c < M; ++c) pts[j][c] = v32[c];
+                        if (!point_ok<PHYS, DIM>(P, v)) viol = true;
+                    }
+                }
+            }
+            if (viol) S.bad[lc] = 1;
+            bool again = __syncthreads_or(viol);
+            if (!again || attempt == 4) break;
+            bool mine = S.bad[lc] != 0;
+            __syncthreads();
+            if (node == 0) S.bad[lc] = 0;
+            if (mine) {
+                tfin = th2 * retry_factor(attempt + 1);
+                apply(tfin);
+            }
+        }
+    }
+    if (stats && active && node == 0 && limited) {
+        double tr = PHYS == PH_EULER ? fmin(th1, tfin) : th1 * tfin;
+        atomicAdd(B.nlim, 1ull);
+        atomicMin(B.thmin, dbits(tr > 0.0 ? tr : 0.0));
+    }
+}
+
+// ----------------------------------------------------------------------------- kernels
+
+template <class C>
+__device__ __forceinline__ Bufs scal_of(const MixBufs &X) {
+    Bufs B;
+    B.un = nullptr;
+    B.ustar = nullptr;
+    B.unew = nullptr;
+    B.tr = nullptr;
+    B.flag = X.flag;
+    B.nlim = X.nlim;
+    B.thmin = X.thmin;
+    B.a0 = X.a0;
+    B.aux = X.aux;
+    B.ord = X.ord;
+    return B;
+}
+
+template <class C>
+__device__ __forceinline__ void load_x(const Params &P, const MixBufs &X, int cell, int node, bool active, double *ub,
+                                       float *dv) {
+    constexpr int M = C::M;
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+        if (active) {
+            ub[c] = X.ub[(size_t)c * P.ncell + cell];
+            dv[c] = X.dv[((size_t)c * P.ncell + cell) * C::NN + node];
+        } else {
+            ub[c] = (C::PH == PH_EULER && (c == 0 || c == M - 1)) ? 1.0 : (C::PH == PH_EULER ? 0.0 : 0.5 * (P.lo + P.hi));
+            dv[c] = 0.0f;
+        }
+    }
+}
+
+// Inner stages of the split representation (cell-local).
+template <class C>
+__global__ void __launch_bounds__(C::NT) k_inner_x(Params P, MixBufs X) {
+    constexpr int M = C::M, NN = C::NN, NTR = C::NTR, FPT = C::FPT;
+    __shared__ SmemX<C> S;
+    const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
+    const int cell = blockIdx.x * C::NCB + lc;
+    const bool active = cell < P.ncell;
+    const Bufs B = scal_of<C>(X);
+    init_kappa<C>(P, S);
+    constexpr int CPT = (M + NN - 1) / NN;  // components owned by a component thread
+    double ub0[CPT];                         // u^n averages of the owned components (FP64)
+    float gbh[MAXS][CPT];                    // averages of G of the owned components (FP32)
+    float dv0[M], dvc[M], dacc[M], gd[MAXS][M];
+    {
+        double ubt[M];
+        load_x<C>(P, X, cell, node, active, ubt, dv0);
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            int c = node + k * NN;
+            ub0[k] = c < M ? ubt[c] : 0.0;
+            if (c < M) {
+                S.ubd[lc][c] = ub0[k];
+                S.ubf[lc][c] = (float)ub0[k];
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < M; ++c) dvc[c] = dacc[c] = dv0[c];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < MAXS; ++i) {
+        if (i >= P.s) break;
+        if (i > 0) {
+            // stage averages: FP64 average of u^n plus the FP32 increments (component threads)
+#pragma unroll
+            for (int k = 0; k < CPT; ++k) {
+                int c = node + k * NN;
+                if (c < M) {
+                    float inc = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < i; ++j)
+                        if (P.A[i][j] != 0.0) inc = fmaf((float)(P.dt * P.A[i][j]), gbh[j][k], inc);
+                    double v = ub0[k] + (double)inc;
+                    S.ubd[lc][c] = v;
+                    S.ubf[lc][c] = (float)v;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                float w = dv0[c];
+#pragma unroll
+                for (int j = 0; j < i; ++j)
+                    if (P.A[i][j] != 0.0) w = fmaf((float)(P.dt * P.A[i][j]), gd[j][c], w);
+                dvc[c] = w;
+            }
+            __syncthreads();
+            float pts[C::PPT][M];
+            limit_x(P, B, S, lc, node, active, S.ubd[lc], dvc, true, true, pts);
+        }
+        float trs[FPT][M];
+        eval_G_x(P, S, lc, node, dvc, gd[i], trs);
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            int c = node + k * NN;
+            gbh[i][k] = c < M ? S.gbf[lc][c] : 0.0f;
+        }
+        if (P.mode == MODE_OP_G) {
+            if (active)
+#pragma unroll
+                for (int c = 0; c < M; ++c)
+                    X.nod_out[((size_t)c * P.ncell + cell) * NN + node] = (double)S.gbf[lc][c] + (double)gd[i][c];
+        } else if (P.b[i] != 0.0) {
+#pragma unroll
+            for (int c = 0; c < M; ++c) dacc[c] = fmaf((float)(P.dt * P.b[i]), gd[i][c], dacc[c]);
+        }
+        if (P.slot[i] >= 0 && active) {
+            float *dst = X.tr + (size_t)P.slot[i] * M * P.ncell * NTR;
+#pragma unroll
+            for (int j = 0; j < FPT; ++j) {
+                int fp = node + j * NN;
+                if (fp < NTR)
+#pragma unroll
+                    for (int c = 0; c < M; ++c) dst[((size_t)c * P.ncell + cell) * NTR + fp] = trs[j][c];
+            }
+        }
+    }
+    if (P.mode != MODE_OP_G && active)
+#pragma unroll
+        for (int c = 0; c < M; ++c) X.dv_s[((size_t)c * P.ncell + cell) * NN + node] = dacc[c];
+}
+
+// Final stage of the split representation: averages from the FP64 sum of
+// sum_i b_i fhat^(i) over the face points, deviations from the FP32 lift of
+// sum_i b_i (fhat^(i) - f(u_int^(i))); then the limiter and the trial-step rate.
+template <class C>
+__global__ void __launch_bounds__(C::NT) k_final_x(Params P, MixBufs X) {
+    constexpr int DIM = C::D, N = C::NP, PHYS = C::PH;
+    constexpr int M = C::M, NN = C::NN, NF = C::NF, NTR = C::NTR, FPT = C::FPT;
+    __shared__ SmemX<C> S;
+    const NodalTables &T = c_tab[N - 2];
+    const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
+    const int cell = blockIdx.x * C::NCB + lc;
+    const bool active = cell < P.ncell;
+    const int a = node % N, b = DIM == 2 ? node / N : 0;
+    const Bufs B = scal_of<C>(X);
+    init_kappa<C>(P, S);
+    double ub0[M];
+    float dvs[M];
+    {
+        MixBufs Y = X;
+        Y.dv = X.dv_s;
+        load_x<C>(P, Y, cell, node, active, ub0, dvs);
+    }
+    float dcf[FPT][M], fhs[FPT][M];
+#pragma unroll
+    for (int j = 0; j < FPT; ++j)
+#pragma unroll
+        for (int c = 0; c < M; ++c) dcf[j][c] = fhs[j][c] = 0.0f;
+
+    for (int i = 0; i < P.s; ++i) {
+        if (P.slot[i] < 0) continue;
+        const float *tr = X.tr + (size_t)P.slot[i] * M * P.ncell * NTR;
+        const float bi = (float)P.b[i];
+        float uL[FPT][M], uR[FPT][M];
+#pragma unroll
+        for (int j = 0; j < FPT; ++j) {
+            int fp = node + j * NN;
+            if (fp < NTR && active) {
+                int face = fp / NF, pos = fp - face * NF;
+                float ui[M], ue[M];
+#pragma unroll
+                for (int c = 0; c < M; ++c) ui[c] = tr[((size_t)c * P.ncell + cell) * NTR + fp];
+                int nb = neighbour(P, cell, face);
+                if (nb >= 0) {
+                    int ofp = (face ^ 1) * NF + pos;
+#pragma unroll
+                    for (int c = 0; c < M; ++c) ue[c] = tr[((size_t)c * P.ncell + nb) * NTR + ofp];
+                } else {
+                    boundary_state_f<PHYS, DIM>(P, face, ui, ue);
+                }
+                bool upper = face & 1;
+#pragma unroll
+                for (int c = 0; c < M; ++c) {
+                    uL[j][c] = upper ? ui[c] : ue[c];
+                    uR[j][c] = upper ? ue[c] : ui[c];
+                }
+                int dir = face >> 1;
+                S.al[lc][fp] = fmaxf(speed_dir_f<PHYS, DIM>(P, uL[j], dir), speed_dir_f<PHYS, DIM>(P, uR[j], dir));
+            } else if (fp < NTR) {
+                S.al[lc][fp] = 0.0f;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < FPT; ++j) {
+            int fp = node + j * NN;
+            if (fp < NTR && active) {
+                int face = fp / NF;
+                int dir = face >> 1;
+                float alpha = 0.0f;
+#pragma unroll
+                for (int q = 0; q < NF; ++q) alpha = fmaxf(alpha, S.al[lc][face * NF + q]);
+                float fL[M], fR[M];
+                flux_dir_f<PHYS, DIM>(P, uL[j], dir, fL);
+                flux_dir_f<PHYS, DIM>(P, uR[j], dir, fR);
+                bool upper = face & 1;
+#pragma unroll
+                for (int c = 0; c < M; ++c) {
+                    float fhat = 0.5f * (fL[c] + fR[c]) - 0.5f * alpha * (uR[j][c] - uL[j][c]);
+                    float fint = upper ? fL[c] : fR[c];
+                    dcf[j][c] = fmaf(bi, fhat - fint, dcf[j][c]);
+                    fhs[j][c] = fmaf(bi, fhat, fhs[j][c]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < FPT; ++j) {
+        int fp = node + j * NN;
+        if (fp < NTR)
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                S.tf[lc][fp][c] = dcf[j][c];
+                S.fh[lc][fp][c] = fhs[j][c];
+            }
+    }
+    __syncthreads();
+    const float rhx = (float)P.rhx, rhy = (float)P.rhy;
+    float corr[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+        float cx = -T.liftpf[a] * S.tf[lc][NF + b][c] + T.liftmf[a] * S.tf[lc][b][c];
+        float cv = rhx * cx;
+        if constexpr (DIM == 2) {
+            float cy = -T.liftpf[b] * S.tf[lc][3 * NF + a][c] + T.liftmf[b] * S.tf[lc][2 * NF + a][c];
+            cv = fmaf(rhy, cy, cv);
+        }
+        corr[c] = cv;
+        S.w[lc][c][node] = wnode_f<DIM, N>(node) * cv;
+    }
+    if (P.mode == MODE_OP_F) {  // F = G + lift(fhat - f_int): nodal FP64 output, no limiter
+        if (active)
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                size_t k = ((size_t)c * P.ncell + cell) * NN + node;
+                X.nod_out[k] = X.nod_in[k] + (double)corr[c];
+            }
+        return;
+    }
+    // local conservation (Sec. 3.2): ubar^{n+1} = ubar^n - dt/|K| sum_faces sum_i b_i fhat^(i),
+    // each face point's FP64 term formed by its own thread, summed per cell in a fixed order
+#pragma unroll
+    for (int j = 0; j < FPT; ++j) {
+        int fp = node + j * NN;
+        if (fp < NTR)
+#pragma unroll
+            for (int c = 0; c < M; ++c) S.term[lc][fp][c] = S.kap[fp] * (double)fhs[j][c];
+    }
+    __syncthreads();
+    for (int c = node; c < M; c += NN) {
+        float m = 0.0f;
+        for (int q = 0; q < NN; ++q) m += S.w[lc][c][q];
+        S.mean[lc][c] = m;
+        double g = 0.0;
+        for (int fp = 0; fp < NTR; ++fp) g += S.term[lc][fp][c];
+        double v = fma(P.dt, g, ub0[c]);
+        S.ubd[lc][c] = v;
+        S.ubf[lc][c] = (float)v;
+    }
+    __syncthreads();
+    float dvn[M];
+    const float fdt = (float)P.dt;
+#pragma unroll
+    for (int c = 0; c < M; ++c) dvn[c] = fmaf(fdt, corr[c] - S.mean[lc][c], dvs[c]);
+    float pts[C::PPT][M];
+    limit_x(P, B, S, lc, node, active, S.ubd[lc], dvn, true, true, pts);
+    double ubn[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) ubn[c] = S.ubd[lc][c];
+    float amax = 0.0f;
+#pragma unroll
+    for (int j = 0; j < C::PPT; ++j) {
+        int p = node + j * NN;
+        if (p < C::NSK && active) {
+            float r = speed_dir_f<PHYS, DIM>(P, pts[j], 0) * (0.5f * rhx);
+            if constexpr (DIM == 2) r = fmaf(speed_dir_f<PHYS, DIM>(P, pts[j], 1), 0.5f * rhy, r);
+            amax = fmaxf(amax, r);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    // the rate is FP32-evaluated: widen by 2^-20 before it bounds the FP64 step
+    if ((threadIdx.x & 31) == 0 && amax > 0.0f) atomicMax(X.a0, dbits((double)amax * (1.0 + 9.5367431640625e-07)));
+    if (active) {
+        for (int c = node; c < M; c += NN) X.ub_n[(size_t)c * P.ncell + cell] = ubn[c];
+#pragma unroll
+        for (int c = 0; c < M; ++c) X.dv_n[((size_t)c * P.ncell + cell) * NN + node] = dvn[c];
+    }
+}
+
+// FP64 nodal -> (ubar, dev), then (optionally) the limiter.
+template <class C>
+__global__ void __launch_bounds__(C::NT) k_split_x(Params P, MixBufs X) {
+    constexpr int DIM = C::D, N = C::NP, M = C::M, NN = C::NN;
+    const NodalTables &T = c_tab[N - 2];
+    const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
+    const int cell = blockIdx.x * C::NCB + lc;
+    const bool active = cell < P.ncell;
+    double u[M];
+    __shared__ double su[C::NCB][M][NN];
+    __shared__ double sub[C::NCB][M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+        u[c] = active ? X.nod_in[((size_t)c * P.ncell + cell) * NN + node] : 1.0;
+        su[lc][c][node] = u[c];
+    }
+    __syncthreads();
+    for (int c = node; c < M; c += NN) {
+        double s = 0.0;
+        for (int q = 0; q < NN; ++q) s = fma(DIM == 2 ? T.w2[q] : T.w1[q], su[lc][c][q], s);
+        sub[lc][c] = s;
+    }
+    __syncthreads();
+    if (active) {
+        for (int c = node; c < M; c += NN) X.ub_n[(size_t)c * P.ncell + cell] = sub[lc][c];
+#pragma unroll
+        for (int c = 0; c < M; ++c)
+            X.dv_n[((size_t)c * P.ncell + cell) * NN + node] = (float)(u[c] - sub[lc][c]);
+    }
+}
+
+// (ubar, dev) -> FP64 nodal values ubar + (dev - dbar).
+template <class C>
+__global__ void __launch_bounds__(C::NT) k_merge_x(Params P, MixBufs X) {
+    constexpr int M = C::M, NN = C::NN;
+    __shared__ SmemX<C> S;
+    const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
+    const int cell = blockIdx.x * C::NCB + lc;
+    const bool active = cell < P.ncell;
+    double ub[M];
+    float dv[M];
+    load_x<C>(P, X, cell, node, active, ub, dv);
+    for (int c = node; c < M; c += NN) S.ubf[lc][c] = (float)ub[c];
+    publish_dev(ub, dv, S, lc, node);
+    if (active)
+#pragma unroll
+        for (int c = 0; c < M; ++c)
+            X.nod_out[((size_t)c * P.ncell + cell) * NN + node] = ub[c] + (double)(dv[c] - S.mean[lc][c]);
+}
+
+// Limiter of (ubar, dev) in place (after set-up).
+template <class C>
+__global__ void __launch_bounds__(C::NT) k_limit_x(Params P, MixBufs X) {
+    constexpr int M = C::M, NN = C::NN;
+    __shared__ SmemX<C> S;
+    const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
+    const int cell = blockIdx.x * C::NCB + lc;
+    const bool active = cell < P.ncell;
+    const Bufs B = scal_of<C>(X);
+    double ub[M];
+    float dv[M], pts[C::PPT][M];
+    load_x<C>(P, X, cell, node, active, ub, dv);
+    for (int c = node; c < M; c += NN) {
+        S.ubd[lc][c] = ub[c];
+        S.ubf[lc][c] = (float)ub[c];
+    }
+    __syncthreads();
+    limit_x(P, B, S, lc, node, active, S.ubd[lc], dv, false, false, pts);
+    if (active)
+#pragma unroll
+        for (int c = 0; c < M; ++c) X.dv_n[((size_t)c * P.ncell + cell) * NN + node] = dv[c];
+}
+
+// Trial-step rate (FP32 S_K values, widened) and bound margins (FP64 evaluation).
+template <class C>
+__global__ void __launch_bounds__(C::NT) k_scan_x(Params P, MixBufs X) {
+    constexpr int DIM = C::D, PHYS = C::PH, M = C::M, NN = C::NN;
+    __shared__ SmemX<C> S;
+    const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
+    const int cell = blockIdx.x * C::NCB + lc;
+    const bool active = cell < P.ncell;
+    double ub[M];
+    float dv[M];
+    load_x<C>(P, X, cell, node, active, ub, dv);
+    for (int c = node; c < M; c += NN) S.ubf[lc][c] = (float)ub[c];
+    publish_dev(ub, dv, S, lc, node);
+    float amax = 0.0f;
+    double m0 = INFINITY, m1 = INFINITY;
+    const float rhx = (float)P.rhx, rhy = (float)P.rhy;
+#pragma unroll
+    for (int j = 0; j < C::PPT; ++j) {
+        int p = node + j * NN;
+        if (p < C::NSK && active) {
+            double v[M];
+            float v32[M];
+            eval64_x(S, lc, p, ub, v, v32);
+            float r = speed_dir_f<PHYS, DIM>(P, v32, 0) * (0.5f * rhx);
+            if constexpr (DIM == 2) r = fmaf(speed_dir_f<PHYS, DIM>(P, v32, 1), 0.5f * rhy, r);
+            amax = fmaxf(amax, r);
+            double a0m, a1m;
+            if constexpr (PHYS == PH_EULER) {
+                a0m = v[0] - P.eps;
+                a1m = rho_e<DIM>(v) - P.eps;
+            } else {
+                a0m = v[0] - P.lo;
+                a1m = P.hi - v[0];
+            }
+            m0 = (a0m == a0m) ? fmin(m0, a0m) : -INFINITY;
+            m1 = (a1m == a1m) ? fmin(m1, a1m) : -INFINITY;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        m0 = fmin(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+        m1 = fmin(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (amax > 0.0f) atomicMax(X.a0, dbits((double)amax * (1.0 + 9.5367431640625e-07)));
+        atomicMin(&X.ord[0], ordbits(m0));
+        atomicMin(&X.ord[1], ordbits(m1));
+    }
+}
+
+// Cell averages: aux[cell][m] = ubar
+template <class C>
+__global__ void k_avg_x(Params P, MixBufs X) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P.ncell * C::M) return;
+    int cell = t / C::M, c = t - cell * C::M;
+    X.aux[t] = X.ub[(size_t)c * P.ncell + cell];
+}
+
+template <int DIM, int N, int PHYS>
+cudaError_t launch_one_x(int kernel, int nblocks, cudaStream_t st, const Params &P, const MixBufs &X) {
+    using C = Cfg<DIM, N, PHYS>;
+    switch (kernel) {
+    case KX_SPLIT: k_split_x<C><<<nblocks, C::NT, 0, st>>>(P, X); break;
+    case KX_MERGE: k_merge_x<C><<<nblocks, C::NT, 0, st>>>(P, X); break;
+    case KX_LIMIT: k_limit_x<C><<<nblocks, C::NT, 0, st>>>(P, X); break;
+    case KX_INNER: k_inner_x<C><<<nblocks, C::NT, 0, st>>>(P, X); break;
+    case KX_FINAL: k_final_x<C><<<nblocks, C::NT, 0, st>>>(P, X); break;
+    case KX_SCAN: k_scan_x<C><<<nblocks, C::NT, 0, st>>>(P, X); break;
+    case KX_AVG: {
+        int tot = P.ncell * C::M;
+        k_avg_x<C><<<(tot + 255) / 256, 256, 0, st>>>(P, X);
+        break;
+    }
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int DIM>
+cudaError_t launch_dim_x(int kernel, int n, int phys, int nblocks, cudaStream_t st, const Params &P,
+                         const MixBufs &X) {
+#define CRKDG_CASE_X(NV, PV) \
+    if (n == NV && phys == PV) return launch_one_x<DIM, NV, PV>(kernel, nblocks, st, P, X);
+    CRKDG_CASE_X(2, PH_ADV) CRKDG_CASE_X(2, PH_BURG) CRKDG_CASE_X(2, PH_EULER)
+    CRKDG_CASE_X(3, PH_ADV) CRKDG_CASE_X(3, PH_BURG) CRKDG_CASE_X(3, PH_EULER)
+    CRKDG_CASE_X(4, PH_ADV) CRKDG_CASE_X(4, PH_BURG) CRKDG_CASE_X(4, PH_EULER)
+#undef CRKDG_CASE_X
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace crkdg

@@ -1,0 +1,271 @@
+// dg_run1d.cuh -- device-resident step loop for 1D meshes (one persistent
+// cooperative launch runs many limited cRKDG steps).
+//
+// Small 1D problems (a few thousand cells) finish a step in a few microseconds
+// of FP64 work, less than a host round trip.  Here one launch keeps the whole
+// Sec. 4.1 loop on the device: every block owns chunks of NCB-2 consecutive
+// cells plus one halo cell on each side, recomputes the (cell-local) inner
+// stages of the halo cells itself, so the final stage's Lax--Friedrichs fluxes
+// need no neighbour data from other blocks (compactness, Sec. 1), and only one
+// grid barrier per attempt decides acceptance, restart (dt halved) and the next
+// trial step from the global admissibility flag and wave-speed rate.
+#pragma once
+
+#include "dg_core.cuh"
+
+namespace crkdg {
+
+template <int N, int PHYS, int NCBV>
+struct RunCfg1D {
+    static constexpr int D = 1;
+    static constexpr int NP = N;
+    static constexpr int PH = PHYS;
+    static constexpr int M = ncomp(PHYS, 1);
+    static constexpr int NN = N;
+    static constexpr int NF = 1;
+    static constexpr int NTR = 2;
+    static constexpr int L = nlob(N);
+    static constexpr int NSK = L;
+    static constexpr int NCB = NCBV;  // cells per chunk including the two halo cells
+    static constexpr int NT = NCB * NN;
+    static constexpr int PPT = (NSK + NN - 1) / NN;
+    static constexpr int FPT = (NTR + NN - 1) / NN;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier with a bounded wait (2 s of %globaltimer).  Returns false
+// when the wait expired; the caller then leaves its step loop.
+__device__ bool grid_barrier(RunCtl *R, unsigned nblocks) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &R->bar_gen;
+        unsigned g = *gen;  // read before arriving: the last arrival cannot pass us
+        __threadfence();
+        unsigned arrived = atomicAdd(&R->bar_count, 1u) + 1u;
+        int ok = 1;
+        if (arrived == nblocks) {
+            atomicExch(&R->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&R->bar_gen, 1u);
+        } else {
+            unsigned long long t0 = global_ns();
+            while (*gen == g) {
+                if (global_ns() - t0 > 2000000000ull) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(40);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int N, int PHYS, int NCBV>
+__global__ void __launch_bounds__(RunCfg1D<N, PHYS, NCBV>::NT) k_run1d(Params P, double *U0, double *U1,
+                                                                        RunCtl *R) {
+    using C = RunCfg1D<N, PHYS, NCBV>;
+    constexpr int M = C::M, NN = C::NN;
+    constexpr int COWN = C::NCB - 2;
+    __shared__ Smem<C> S;
+    __shared__ double sTr[MAXS][C::NCB][2][M];
+    const NodalTables &T = c_tab[N - 2];
+    const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
+    const int a = node;
+    const int nchunks = (P.ncell + COWN - 1) / COWN;
+    const bool periodic = P.bc[0] == BC_PERIODIC;
+
+    double t = R->t;
+    const double t_end = R->t_end, cfl = R->cfl;
+    const int nsteps = R->nsteps, maxh = R->max_halvings;
+    int cur = R->cur, steps = 0, restarts = 0, halv = 0, it = 0, status = RUN_OK;
+    unsigned long long nlim_total = 0;
+    double rate_last = -1.0;
+    double dt_try = fmin(R->dt0, t_end - t);
+
+    while (steps < nsteps && t < t_end) {
+        RunSlot *SL = &R->slot[it % 3];
+        Bufs B;
+        B.flag = &SL->flag;
+        B.nlim = &SL->nlim;
+        B.thmin = &SL->thmin;
+        B.a0 = &SL->rate;
+        const double *un = cur ? U1 : U0;
+        double *unew = cur ? U0 : U1;
+        const double dt = dt_try;
+
+        for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+            const int c0 = chunk * COWN;        // first own cell of the chunk
+            const int graw = c0 - 1 + lc;       // unwrapped global index of this slot
+            const bool exists = periodic || (graw >= 0 && graw < P.ncell);
+            const int gc = periodic ? (graw % P.ncell + P.ncell) % P.ncell : graw;
+            const bool own = lc >= 1 && lc <= COWN && graw < P.ncell;
+            double u0[M], cur_u[M], acc[M], gh[MAXS][M];
+            load_node<1, N, PHYS>(P, un, gc, node, exists, u0);
+#pragma unroll
+            for (int c = 0; c < M; ++c) cur_u[c] = acc[c] = u0[c];
+            // inner stages of every cell of the chunk, halo included
+#pragma unroll
+            for (int i = 0; i < MAXS; ++i) {
+                if (i >= P.s) break;
+                if (i > 0) {
+#pragma unroll
+                    for (int c = 0; c < M; ++c) {
+                        double v = u0[c];
+#pragma unroll
+                        for (int j = 0; j < i; ++j)
+                            if (P.A[i][j] != 0.0) v = fma(dt * P.A[i][j], gh[j][c], v);
+                        cur_u[c] = v;
+                    }
+                    double pts[C::PPT][M];
+                    limit_block(P, B, S, lc, node, own, cur_u, pts, true, true);
+                }
+                double trs[C::FPT][M];
+                eval_G(P, S, lc, node, cur_u, gh[i], trs);
+                if (P.b[i] != 0.0) {
+#pragma unroll
+                    for (int c = 0; c < M; ++c) acc[c] = fma(dt * P.b[i], gh[i][c], acc[c]);
+                }
+                if (P.slot[i] >= 0 && node < 2) {
+#pragma unroll
+                    for (int c = 0; c < M; ++c) sTr[P.slot[i]][lc][node][c] = trs[0][c];
+                }
+            }
+            __syncthreads();
+            // final stage: Lax--Friedrichs correction of the own cells from the chunk's traces
+            double dc[M];
+#pragma unroll
+            for (int c = 0; c < M; ++c) dc[c] = 0.0;
+            if (own && node < 2) {
+                const int face = node;
+                const int nl = face == 0 ? lc - 1 : lc + 1;
+                const int nraw = c0 - 1 + nl;
+                const bool nb_exists = periodic || (nraw >= 0 && nraw < P.ncell);
+                for (int i = 0; i < P.s; ++i) {
+                    const int q = P.slot[i];
+                    if (q < 0) continue;
+                    double ui[M], ue[M], uL[M], uR[M];
+#pragma unroll
+                    for (int c = 0; c < M; ++c) ui[c] = sTr[q][lc][face][c];
+                    if (nb_exists) {
+#pragma unroll
+                        for (int c = 0; c < M; ++c) ue[c] = sTr[q][nl][face ^ 1][c];
+                    } else {
+                        boundary_state<PHYS, 1>(P, face, ui, ue);
+                    }
+#pragma unroll
+                    for (int c = 0; c < M; ++c) {
+                        uL[c] = face ? ui[c] : ue[c];
+                        uR[c] = face ? ue[c] : ui[c];
+                    }
+                    double alpha = fmax(speed_dir<PHYS, 1>(P, uL, 0), speed_dir<PHYS, 1>(P, uR, 0));
+                    double fL[M], fR[M];
+                    flux_dir<PHYS, 1>(P, uL, 0, fL);
+                    flux_dir<PHYS, 1>(P, uR, 0, fR);
+#pragma unroll
+                    for (int c = 0; c < M; ++c) {
+                        double fhat = 0.5 * (fL[c] + fR[c]) - 0.5 * alpha * (uR[c] - uL[c]);
+                        double fint = face ? fL[c] : fR[c];
+                        dc[c] = fma(P.b[i], fhat - fint, dc[c]);
+                    }
+                }
+            }
+            if (node < 2) {
+#pragma unroll
+                for (int c = 0; c < M; ++c) S.tf[lc][node][c] = dc[c];
+            }
+            __syncthreads();
+            double u[M];
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                double corr = -T.liftp[a] * S.tf[lc][1][c] + T.liftm[a] * S.tf[lc][0][c];
+                u[c] = fma(dt, P.rhx * corr, acc[c]);
+            }
+            double pts[C::PPT][M];
+            limit_block(P, B, S, lc, node, own, u, pts, true, true);
+            double amax = 0.0;
+#pragma unroll
+            for (int j = 0; j < C::PPT; ++j) {
+                int p = node + j * NN;
+                if (p < C::NSK && own) amax = fmax(amax, sk_rate<PHYS, 1>(P, pts[j]));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+            if ((threadIdx.x & 31) == 0 && amax > 0.0) atomicMax(B.a0, dbits(amax));
+            if (own) store_node<1, N, PHYS>(P, unew, gc, node, true, u);
+            __syncthreads();
+        }
+        if (!grid_barrier(R, gridDim.x + (unsigned)R->extra_arrivals)) {
+            status = RUN_TIMEOUT;
+            break;
+        }
+        const int fl = *(volatile int *)&SL->flag;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {  // the slot used two attempts ahead
+            RunSlot *Z = &R->slot[(it + 2) % 3];
+            Z->flag = 0;
+            Z->nlim = 0ull;
+            Z->thmin = dbits(1.0);
+            Z->rate = 0ull;
+        }
+        ++it;
+        if (fl == 0) {
+            const double rate = bitsd(*(volatile unsigned long long *)&SL->rate);
+            nlim_total += *(volatile unsigned long long *)&SL->nlim;
+            t += dt;
+            if (t_end - t <= 1e-14 * fabs(t_end)) t = t_end;
+            ++steps;
+            restarts += halv;
+            halv = 0;
+            cur ^= 1;
+            rate_last = rate;
+            // adaptive: the trial step of the new state; fixed (cfl <= 0): dt0 every step
+            dt_try = fmin(cfl > 0.0 ? (rate > 0.0 ? cfl / rate : INFINITY) : R->dt0, t_end - t);
+        } else {
+            if (++halv > maxh) {
+                status = RUN_BOUNDS;
+                break;
+            }
+            dt_try = 0.5 * dt;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        R->t_out = t;
+        R->rate_out = rate_last;
+        R->steps = steps;
+        R->restarts = restarts;
+        R->cur_out = cur;
+        R->status = status;
+        R->nlim_total = nlim_total;
+    }
+}
+
+template <int N, int PHYS>
+cudaError_t run1d_launch(cudaStream_t st, const Params &P, double *u0, double *u1, RunCtl *R, int *nblocks) {
+    constexpr int NCB = 32;
+    using C = RunCfg1D<N, PHYS, NCB>;
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_run1d<N, PHYS, NCB>, C::NT, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int nchunks = (P.ncell + NCB - 3) / (NCB - 2);
+    int grid = nchunks < nsm * per_sm ? nchunks : nsm * per_sm;
+    *nblocks = grid;
+    Params Pc = P;
+    void *args[] = {&Pc, &u0, &u1, &R};
+    return cudaLaunchCooperativeKernel((void *)k_run1d<N, PHYS, NCB>, dim3(grid), dim3(C::NT), args, 0, st);
+}
+
+}  // namespace crkdg

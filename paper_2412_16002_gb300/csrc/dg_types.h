@@ -44,6 +44,9 @@ struct NodalTables {
     double Igl[MAXN][MAXN];     // Igl[alpha][a] = l_a(xl_alpha)   (S_K interpolation)
     double w1[MAXN];            // w_a / 2                          (1D average weights)
     double w2[MAXN * MAXN];     // (w_a/2)(w_b/2) at node b*n+a      (2D average weights)
+    // FP32 copies for the split-precision path
+    float Dhatf[MAXN][MAXN], lmf[MAXN], lpf[MAXN], liftmf[MAXN], liftpf[MAXN], Iglf[MAXN][MAXN];
+    float w1f[MAXN], w2f[MAXN * MAXN];
 };
 
 struct Params {
@@ -60,6 +63,9 @@ struct Params {
     int nslot;
     double dt;
     int mode;
+    int defer_limit;  // final kernel leaves the limiter to the troubled-cell kernel
+    double tvb_M;     // TVB constant of the plain indicator
+    int ind_stage;    // troubled-cell kernel: 0 decide and limit, 1 decide only, 2 limit given flags
 };
 
 struct Bufs {
@@ -73,9 +79,59 @@ struct Bufs {
     unsigned long long *a0;     // bits of the largest spectral radius (non-negative double)
     double *aux;        // per-cell output of the utility kernels
     unsigned long long *ord;    // two order-preserving mins (margins)
+    int *tflags;        // troubled-cell flags (one per cell) or nullptr
+    unsigned long long *ntrb;   // number of troubled cells
+    float *feat;        // MLP features [cell][44]
+    const float *prob;  // MLP probabilities [cell]
 };
 
-enum KernelId { K_INNER = 0, K_FINAL = 1, K_LIMIT = 2, K_A0 = 3, K_MARGINS = 4, K_AVG = 5 };
+enum KernelId { K_INNER = 0, K_FINAL = 1, K_LIMIT = 2, K_A0 = 3, K_MARGINS = 4, K_AVG = 5, K_TROUBLE = 6,
+                K_FEATURES = 7, K_COMBINE = 8 };
+
+// Buffers of the split-precision path: FP64 cell averages plus FP32 nodal
+// deviations (the polynomial is ubar + (dev - mean_w dev)).
+struct MixBufs {
+    const double *ub;   // averages of u^n            [m][cell]
+    const float *dv;    // deviations of u^n          [m][cell][n^d]
+    float *dv_s;        // deviations of u* = u^n + dt sum_i b_i G(u~^(i))
+    double *ub_n;       // averages of u^{n+1}
+    float *dv_n;        // deviations of u^{n+1}
+    float *tr;          // FP32 face traces           [slot][m][cell][face point]
+    const double *nod_in;  // FP64 nodal input (split, operators)
+    double *nod_out;       // FP64 nodal output (merge, operators)
+    int *flag;
+    unsigned long long *nlim, *thmin, *a0, *ord;
+    double *aux;
+};
+
+enum MixKernelId { KX_SPLIT = 0, KX_MERGE = 1, KX_LIMIT = 2, KX_INNER = 3, KX_FINAL = 4, KX_SCAN = 5, KX_AVG = 6 };
+
+// Scalars of one attempt of the device-resident step loop (three rotate).
+struct RunSlot {
+    int flag;
+    int pad;
+    unsigned long long nlim;
+    unsigned long long thmin;
+    unsigned long long rate;  // bits of max over S_K of sum_d lambda_d / h_d
+};
+
+// Control block of the persistent 1D run kernel (device memory).
+struct RunCtl {
+    // inputs
+    double t, t_end, dt0, cfl;
+    int nsteps, max_halvings, cur;
+    int extra_arrivals;  // testing aid: > 0 makes the barrier wait for blocks that never come
+    // outputs
+    double t_out, rate_out;
+    int steps, restarts, cur_out, status;
+    unsigned long long nlim_total;
+    // grid barrier
+    unsigned bar_count, bar_gen;
+    RunSlot slot[3];
+};
+
+// Status values written by the run kernel (match crkdg_status).
+enum RunStatus { RUN_OK = 0, RUN_BOUNDS = 4, RUN_TIMEOUT = 5 };
 
 }  // namespace crkdg
 
@@ -87,4 +143,11 @@ cudaError_t crkdg_launch_1d(int kernel, int n, int phys, int nblocks, cudaStream
                             const crkdg::Params &P, const crkdg::Bufs &B);
 cudaError_t crkdg_launch_2d(int kernel, int n, int phys, int nblocks, cudaStream_t st,
                             const crkdg::Params &P, const crkdg::Bufs &B);
+cudaError_t crkdg_launch_mx_1d(int kernel, int n, int phys, int nblocks, cudaStream_t st,
+                               const crkdg::Params &P, const crkdg::MixBufs &B);
+cudaError_t crkdg_launch_mx_2d(int kernel, int n, int phys, int nblocks, cudaStream_t st,
+                               const crkdg::Params &P, const crkdg::MixBufs &B);
+// Persistent 1D step loop (cooperative launch); *nblocks receives the grid used.
+cudaError_t crkdg_run_1d(int n, int phys, cudaStream_t st, const crkdg::Params &P, double *u0, double *u1,
+                         crkdg::RunCtl *ctl, int *nblocks);
 }

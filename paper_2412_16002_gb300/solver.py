@@ -48,7 +48,7 @@ class Solver:
 
     def __init__(self, dim, nx, ny, k, domain, flux, gamma=1.4, velocity=(1.0, 0.0), bounds=(0.0, 1.0),
                  eps=1e-13, bc=("periodic",) * 4, bc_state=None, stream=None, max_halvings=20,
-                 precision="fp64"):
+                 precision="fp64", indicator="off", tvb_M=10.0):
         self.lib = L.load()
         mesh = L.Mesh()
         mesh.dim, mesh.nx, mesh.ny = dim, nx, ny if dim == 2 else 1
@@ -65,6 +65,8 @@ class Solver:
         self.lib.crkdg_options_default(C.byref(opt))
         opt.max_halvings = max_halvings
         opt.precision = L.PREC[precision]
+        opt.indicator = L.INDICATOR[indicator]
+        opt.tvb_M = tvb_M
         if stream is not None:
             opt.cuda_stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
         self.m = dim + 2 if flux == "euler" else 1
@@ -132,7 +134,7 @@ class Solver:
         info = L.StepInfo()
         self._chk(self.lib.crkdg_step(self.h, dt, C.byref(self._tab(tableau).c), C.byref(info)))
         return {"dt_taken": info.dt_taken, "restarts": info.restarts, "cells_limited": info.cells_limited,
-                "theta_min": info.theta_min}
+                "theta_min": info.theta_min, "troubled": info.troubled}
 
     def advance(self, nsteps, cfl, t_end, tableau="heun3", t=0.0):
         tt = C.c_double(t)
@@ -142,16 +144,25 @@ class Solver:
                                          C.byref(done), C.byref(rs)))
         return tt.value, done.value, rs.value
 
+    def advance_fixed(self, nsteps, dt, t_end, tableau="heun3", t=0.0):
+        tt = C.c_double(t)
+        done = C.c_int()
+        rs = C.c_int()
+        self._chk(self.lib.crkdg_advance_fixed(self.h, nsteps, dt, t_end, C.byref(self._tab(tableau).c),
+                                               C.byref(tt), C.byref(done), C.byref(rs)))
+        return tt.value, done.value, rs.value
+
     # ---- measurement -------------------------------------------------------------
     def set_profiling(self, on=True):
         self._chk(self.lib.crkdg_set_profiling(self.h, 1 if on else 0))
 
     def kernel_times(self):
-        """({'inner': ms, 'final': ms}, {'inner': launches, 'final': launches})"""
-        ms = (C.c_double * 2)()
-        n = (C.c_longlong * 2)()
+        """({'inner','final','run'}: ms, same keys: launches) since profiling was switched on."""
+        ms = (C.c_double * 3)()
+        n = (C.c_longlong * 3)()
         self._chk(self.lib.crkdg_kernel_times(self.h, ms, n))
-        return {"inner": ms[0], "final": ms[1]}, {"inner": n[0], "final": n[1]}
+        keys = ("inner", "final", "run")
+        return dict(zip(keys, ms)), dict(zip(keys, n))
 
     # ---- verification helpers ---------------------------------------------------
     def apply(self, op, x, out):
@@ -159,6 +170,11 @@ class Solver:
         self._chk(self.lib.crkdg_apply_operator(self.h, L.OPS[op], C.c_void_p(x.data_ptr()),
                                                 C.c_void_p(out.data_ptr())))
         return out
+
+    def troubled_flags(self):
+        f = np.empty(self.nx * self.ny, dtype=np.int32)
+        self._chk(self.lib.crkdg_troubled_flags(self.h, C.c_void_p(f.ctypes.data), 0))
+        return f
 
     def averages(self):
         a = np.empty(self.nx * self.ny * self.m)

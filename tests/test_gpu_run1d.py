@@ -1,0 +1,145 @@
+"""Device-resident 1D step loop (crkdg_advance: one persistent cooperative launch) against
+the oracle's host loop, its restart path, and its bounded failure paths."""
+import numpy as np
+import pytest
+
+from gpu_helpers import ORACLE_TABS, pair_from_workload, rel_linf
+from paper_2412_16002_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_16002_gb300 import build
+
+    build()
+
+
+def _oracle_run(o, wl, nsteps, t_end, cfl):
+    t, steps, rs = 0.0, 0, 0
+    while steps < nsteps and t < t_end:
+        dt = min(o.max_dt(cfl), t_end - t)
+        rc, info = o.step(dt, ORACLE_TABS[wl.tableau], t)
+        assert rc == 0
+        t += info["dt_taken"]
+        steps += 1
+        rs += info["restarts"]
+    return t, steps, rs
+
+
+def _wl(name):
+    if name == "burgers200":
+        return inputs.burgers_sine(200, 2)
+    if name == "euler1d_4096":
+        return inputs.euler_blast_tube(4096, 2)
+    # ragged chunking (257 = 8 x 30 + 17) and periodic halo wrap on smooth P3 / RK4 data
+    u = inputs.random_euler(1, 257, 1, 3, seed=5, osc=0.0)
+    return inputs.Workload("euler1d_smooth_257_p3", 1, 257, 1, 3, (0.0, 1.0), "euler", ("periodic",) * 4, u,
+                           eps=1e-13, cfl=0.103, tableau="rk4")
+
+
+def _oracle_fixed(o, wl, nsteps, dt, t_end):
+    t, steps, rs = 0.0, 0, 0
+    while steps < nsteps and t < t_end:
+        rc, info = o.step(min(dt, t_end - t), ORACLE_TABS[wl.tableau], t)
+        assert rc == 0
+        t += info["dt_taken"]
+        if t_end - t <= 1e-14 * abs(t_end):
+            t = t_end
+        steps += 1
+        rs += info["restarts"]
+    return t, steps, rs
+
+
+@pytest.mark.parametrize("name,nsteps,t_end,fac", [("burgers200", 10**6, 0.3, 0.9), ("euler1d_4096", 60, 6.0, 0.3),
+                                                   ("euler1d_257_p3", 60, 6.0, 0.3)])
+def test_advance_fixed_matches_oracle(name, nsteps, t_end, fac):
+    """The device-resident loop with a fixed trial step (Burgers 200 P2 to t = 0.3, the whole
+    smooth phase of workload 1; the 4096-cell blast tube; a ragged 257-cell P3/RK4 mesh):
+    same steps and state as the oracle to 1e-10.  The step stays below the growing wave
+    speed of the blast so that no restart decision sits on the admissibility threshold.
+    (Ragged chunks are exercised on smooth data: the P3 blast tube is as rounding-sensitive
+    near its vacuum front as the 2D blast.)"""
+    wl = _wl(name)
+    g, o = pair_from_workload(wl)
+    g.set_state(wl.state)
+    o.set_state(wl.state)
+    dt = fac * o.max_dt(wl.cfl)
+    tg, sg, rg = g.advance_fixed(nsteps, dt, t_end, wl.tableau)
+    to, so, ro = _oracle_fixed(o, wl, nsteps, dt, t_end)
+    assert sg == so and rg == ro == 0
+    assert abs(tg - to) <= 1e-12 * max(1.0, to)
+    assert rel_linf(g.get_state(), o.get_state(), o.m) < 1e-10
+    assert g.margins().min() >= 0.0
+
+
+def test_advance_adaptive_tracks_oracle():
+    """Adaptive trial steps chosen on the device: the wave-speed maximum sits at S_K points,
+    some of which the positivity limiter has put at the density floor, where the sound speed
+    is ill-conditioned; two implementations therefore pick steps ~1e-8 apart and the shock
+    positions drift apart by that much.  Times agree to 1e-6 and the states in relative L1
+    to 1e-5 after 300 steps, with exact bounds."""
+    wl = _wl("euler1d_4096")
+    g, o = pair_from_workload(wl)
+    g.set_state(wl.state)
+    o.set_state(wl.state)
+    tg, sg, rg = g.advance(300, wl.cfl, 6.0, wl.tableau)
+    to, so, ro = _oracle_run(o, wl, 300, 6.0, wl.cfl)
+    assert sg == so == 300
+    assert abs(tg - to) <= 1e-6 * to
+    a, b = g.get_state(), o.get_state()
+    for c in range(o.m):
+        assert np.abs(a[c] - b[c]).sum() <= 1e-5 * np.abs(b[c]).sum()
+    assert g.margins().min() >= 0.0
+
+
+def test_advance_restarts_on_device():
+    """A fixed trial step far above the bound-preserving limit makes stage averages leave
+    B^eps; the device loop halves dt and redoes the step exactly as the oracle does (Sec. 4.1)."""
+    wl = inputs.euler_blast_tube(512, 2)
+    g, o = pair_from_workload(wl)
+    g.set_state(wl.state)
+    o.set_state(wl.state)
+    dt = 5.0 * o.max_dt(wl.cfl)
+    tg, sg, rg = g.advance_fixed(3, dt, 6.0, "heun3")
+    to, so, ro = _oracle_fixed(o, wl, 3, dt, 6.0)
+    assert ro > 0, "the case must exercise restarts"
+    assert sg == so and rg == ro
+    assert rel_linf(g.get_state(), o.get_state(), o.m) < 1e-10
+    assert g.margins().min() >= 0.0
+
+
+def test_advance_bounds_error_keeps_last_state():
+    from paper_2412_16002_gb300._lib import CrkdgError, E_BOUNDS
+    from paper_2412_16002_gb300.solver import Solver
+
+    wl = inputs.euler_blast_tube(512, 2)
+    g = Solver.from_workload(wl, max_halvings=0)
+    g.set_state(wl.state)
+    before = g.get_state().copy()
+    with pytest.raises(CrkdgError) as e:
+        g.advance(5, 50.0, 6.0, "heun3")
+    assert e.value.status == E_BOUNDS
+    assert np.array_equal(g.get_state(), before)
+
+
+def test_advance_barrier_wait_expires_with_status():
+    """Failure detection without a fault: the barrier waits for a block that never arrives,
+    every wait ends after its bound, and the host reads CRKDG_E_TIMEOUT."""
+    from paper_2412_16002_gb300._lib import CrkdgError, E_TIMEOUT
+    from paper_2412_16002_gb300.solver import Solver
+
+    wl = inputs.euler_blast_tube(256, 2)
+    g = Solver.from_workload(wl)
+    g.set_state(wl.state)
+    g._chk(g.lib.crkdg_set_barrier_test(g.h, 1))
+    with pytest.raises(CrkdgError) as e:
+        g.advance(3, wl.cfl, 6.0, "heun3")
+    assert e.value.status == E_TIMEOUT
+    g._chk(g.lib.crkdg_set_barrier_test(g.h, 0))
+    t, steps, rs = g.advance(3, wl.cfl, 6.0, "heun3")  # the context is still usable
+    assert steps == 3 and g.margins().min() >= 0.0
