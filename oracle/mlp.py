@@ -2,8 +2,8 @@
 
 The network classifies a cell as troubled from 44 features: for each of the 4
 conservative components, the 3x3 neighbourhood of cell averages normalised by the
-stencil's mean and range, and the cell's two first Legendre moments (x and y
-slopes) normalised by the same range.  Architecture 44 -> 64 -> 64 -> 1, ReLU,
+stencil's mean and by the larger of its range and the TVB threshold, and the cell's
+two first Legendre moments (x and y slopes) normalised the same way.  Architecture 44 -> 64 -> 64 -> 1, ReLU,
 sigmoid output, binary cross-entropy loss, Adam updates.  Everything below is
 written out with numpy array operations in FP64; no part of it is shared with
 the CUDA kernels.
@@ -47,18 +47,22 @@ def init_params(seed=0):
     return pack(p)
 
 
-def features(avg3x3, slopes):
+def features(avg3x3, slopes, thr=0.0):
     """avg3x3: [..., 4, 9] cell averages of the 3x3 stencil (row-major, centre = 4);
-    slopes: [..., 4, 2] the centre cell's first Legendre moments (c_x, c_y).
-    Returns [..., 44]: per component (v - mean) / (range + delta), then the slopes
-    over the same (range + delta), with delta = 1e-12 max|v| + 1e-30."""
+    slopes: [..., 4, 2] the centre cell's first Legendre moments (c_x, c_y);
+    thr: the TVB threshold M hx hy of the mesh.
+    Returns [..., 44]: per component (v - mean) / den, then the slopes / den, with
+    den = max(range, thr) + delta and delta = 1e-6 max|v| + 1e-30.  The threshold floor
+    keeps deviations below the TVB threshold below 1 (the plain indicator cannot flag
+    them); delta maps flat stencils to features near 0 instead of rounding noise."""
     avg3x3 = np.asarray(avg3x3, dtype=np.float64)
     slopes = np.asarray(slopes, dtype=np.float64)
     mean = avg3x3.mean(axis=-1, keepdims=True)
     rng_ = avg3x3.max(axis=-1, keepdims=True) - avg3x3.min(axis=-1, keepdims=True)
-    delta = 1e-12 * np.abs(avg3x3).max(axis=-1, keepdims=True) + 1e-30
-    z = (avg3x3 - mean) / (rng_ + delta)
-    s = slopes / (rng_ + delta)
+    delta = 1e-6 * np.abs(avg3x3).max(axis=-1, keepdims=True) + 1e-30
+    den = np.maximum(rng_, thr) + delta
+    z = (avg3x3 - mean) / den
+    s = slopes / den
     lead = avg3x3.shape[:-2]
     return np.concatenate([z.reshape(lead + (36,)), s.reshape(lead + (8,))], axis=-1)
 

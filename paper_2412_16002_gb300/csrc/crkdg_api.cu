@@ -248,7 +248,30 @@ MixBufs base_xbufs(const crkdg_ctx *h) {
     return X;
 }
 
-cudaError_t launch_x(crkdg_ctx *h, int kernel, const Params &P, const MixBufs &X) {
+void fill_f32(Params &P) {
+    ParamsF &F = P.f;
+    F.rhx = (float)P.rhx;
+    F.rhy = (float)P.rhy;
+    F.gamma = (float)P.gamma;
+    F.gm1 = (float)(P.gamma - 1.0);
+    F.velx = (float)P.velx;
+    F.vely = (float)P.vely;
+    F.lo = (float)P.lo;
+    F.hi = (float)P.hi;
+    F.eps = (float)P.eps;
+    for (int s = 0; s < 4; ++s)
+        for (int c = 0; c < MAXM; ++c) F.bcs[s][c] = (float)P.bcs[s][c];
+    for (int i = 0; i < MAXS; ++i) {
+        for (int j = 0; j < MAXS; ++j) F.dtA[i][j] = (float)(P.dt * P.A[i][j]);
+        F.dtb[i] = (float)(P.dt * P.b[i]);
+        F.b[i] = (float)P.b[i];
+    }
+    F.dt = (float)P.dt;
+}
+
+cudaError_t launch_x(crkdg_ctx *h, int kernel, const Params &P0, const MixBufs &X) {
+    Params P = P0;
+    fill_f32(P);
     int ncb = cells_per_block(h->dim, h->n);
     int nblocks = (h->ncell + ncb - 1) / ncb;
     if (h->dim == 1) return crkdg_launch_mx_1d(kernel, h->n, h->phys, nblocks, h->st, P, X);

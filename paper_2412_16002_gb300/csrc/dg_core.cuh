@@ -936,6 +936,8 @@ __global__ void k_features(Params P, Bufs B) {
 #pragma unroll
                 for (int c = 0; c < M; ++c) v[(dy + 1) * 3 + (dx + 1)][c] = val[c];
             }
+        // per component: (v - mean) / den and slopes / den, den = max(range, M hx hy) + 1e-6 max|v|
+        const double thr = P.tvb_M * (2.0 / P.rhx) * (2.0 / P.rhy);
         float *f = B.feat + (size_t)cell * 44;
 #pragma unroll
         for (int c = 0; c < M; ++c) {
@@ -948,7 +950,7 @@ __global__ void k_features(Params P, Bufs B) {
                 amax = fmax(amax, fabs(v[q][c]));
             }
             mean /= 9.0;
-            double scale = 1.0 / ((mx - mn) + (1e-12 * amax + 1e-30));
+            double scale = 1.0 / (fmax(mx - mn, thr) + (1e-6 * amax + 1e-30));
 #pragma unroll
             for (int q = 0; q < 9; ++q) f[c * 9 + q] = (float)((v[q][c] - mean) * scale);
             const double *u = B.unew + ((size_t)c * P.ncell + cell) * NN;

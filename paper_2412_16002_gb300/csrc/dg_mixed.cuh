@@ -28,20 +28,20 @@ namespace crkdg {
 template <int PHYS, int DIM>
 __device__ __forceinline__ void flux_dir_f(const Params &P, const float *u, int dir, float *f) {
     if constexpr (PHYS == PH_ADV) {
-        f[0] = (float)(dir == 0 ? P.velx : P.vely) * u[0];
+        f[0] = (dir == 0 ? P.f.velx : P.f.vely) * u[0];
     } else if constexpr (PHYS == PH_BURG) {
         f[0] = 0.5f * u[0] * u[0];
     } else if constexpr (DIM == 1) {
         float ri = 1.0f / u[0];
         float w = u[1] * ri;
-        float p = (float)(P.gamma - 1.0) * (u[2] - 0.5f * u[1] * w);
+        float p = P.f.gm1 * (u[2] - 0.5f * u[1] * w);
         f[0] = u[1];
         f[1] = u[1] * w + p;
         f[2] = (u[2] + p) * w;
     } else {
         float ri = 1.0f / u[0];
         float wx = u[1] * ri, wy = u[2] * ri;
-        float p = (float)(P.gamma - 1.0) * (u[3] - 0.5f * (u[1] * wx + u[2] * wy));
+        float p = P.f.gm1 * (u[3] - 0.5f * (u[1] * wx + u[2] * wy));
         float wd = dir == 0 ? wx : wy;
         f[0] = u[1 + dir];
         f[1] = u[1] * wd + (dir == 0 ? p : 0.0f);
@@ -53,14 +53,14 @@ __device__ __forceinline__ void flux_dir_f(const Params &P, const float *u, int 
 template <int PHYS>
 __device__ __forceinline__ void flux_xy_f(const Params &P, const float *u, float *fx, float *fy) {
     if constexpr (PHYS == PH_ADV) {
-        fx[0] = (float)P.velx * u[0];
-        fy[0] = (float)P.vely * u[0];
+        fx[0] = P.f.velx * u[0];
+        fy[0] = P.f.vely * u[0];
     } else if constexpr (PHYS == PH_BURG) {
         fx[0] = fy[0] = 0.5f * u[0] * u[0];
     } else {
         float ri = 1.0f / u[0];
         float wx = u[1] * ri, wy = u[2] * ri;
-        float p = (float)(P.gamma - 1.0) * (u[3] - 0.5f * (u[1] * wx + u[2] * wy));
+        float p = P.f.gm1 * (u[3] - 0.5f * (u[1] * wx + u[2] * wy));
         float ep = u[3] + p;
         fx[0] = u[1];
         fx[1] = u[1] * wx + p;
@@ -76,13 +76,13 @@ __device__ __forceinline__ void flux_xy_f(const Params &P, const float *u, float
 template <int PHYS, int DIM>
 __device__ __forceinline__ float speed_dir_f(const Params &P, const float *u, int dir) {
     if constexpr (PHYS == PH_ADV) {
-        return fabsf((float)(dir == 0 ? P.velx : P.vely));
+        return fabsf(dir == 0 ? P.f.velx : P.f.vely);
     } else if constexpr (PHYS == PH_BURG) {
         return fabsf(u[0]);
     } else {
         float ri = 1.0f / u[0];
         float kin = DIM == 1 ? u[1] * u[1] : u[1] * u[1] + u[2] * u[2];
-        float g = (float)P.gamma;
+        float g = P.f.gamma;
         float p = (g - 1.0f) * (u[DIM + 1] - 0.5f * kin * ri);
         float c2 = g * p * ri;
         float c = c2 > 0.0f ? sqrtf(c2) : 0.0f;
@@ -96,7 +96,7 @@ __device__ __forceinline__ void boundary_state_f(const Params &P, int side, cons
     int bc = P.bc[side];
     if (bc == BC_DIRICHLET) {
 #pragma unroll
-        for (int c = 0; c < M; ++c) ue[c] = (float)P.bcs[side][c];
+        for (int c = 0; c < M; ++c) ue[c] = P.f.bcs[side][c];
     } else {
 #pragma unroll
         for (int c = 0; c < M; ++c) ue[c] = ui[c];
@@ -255,7 +255,7 @@ __device__ void eval_G_x(const Params &P, SmemX<C> &S, int lc, int node, const f
         }
     }
     __syncthreads();
-    const float rhx = (float)P.rhx, rhy = (float)P.rhy;
+    const float rhx = P.f.rhx, rhy = P.f.rhy;
     float g32[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) {
@@ -282,6 +282,37 @@ __device__ void eval_G_x(const Params &P, SmemX<C> &S, int lc, int node, const f
 }
 
 // ----------------------------------------------------------------------------- limiter
+
+// FP32 screen of one point: true when the FP32 value v of a point (vb: the FP32
+// copy of the cell average) proves that its FP64 evaluation ubar + (double)(v - vbf)
+// lies in the bounds.  |FP64 evaluation - v| <= 2^-23 (|v| + |vb|) per component
+// (the rounding of ubar to FP32 and of the FP32 sum), doubled here; for Euler it is
+// propagated to rho e = E - |m|^2 / (2 rho) to first order, plus 2^-18 (|E| + |m|^2/(2 rho))
+// for the FP32 rounding of the formula and the FP64 rounding of the reference test.
+template <int PHYS, int DIM>
+__device__ __forceinline__ bool screen_ok(const Params &P, const float *v, const float *vb) {
+    const float tiny_rel = 2.384185791015625e-07f;  // 2^-22
+    const float re_rel = 3.814697265625e-06f;       // 2^-18
+    if constexpr (PHYS == PH_EULER) {
+        const float epsf = P.f.eps * 1.0000002f;  // >= eps although eps was rounded to FP32
+        float dr = tiny_rel * (fabsf(v[0]) + fabsf(vb[0]));
+        if (!(v[0] - dr >= epsf) || !(v[0] > 0.0f)) return false;
+        float kin = 0.0f, dkin = 0.0f;
+#pragma unroll
+        for (int d = 1; d <= DIM; ++d) {
+            kin += v[d] * v[d];
+            dkin += 2.0f * fabsf(v[d]) * tiny_rel * (fabsf(v[d]) + fabsf(vb[d]));
+        }
+        float de = tiny_rel * (fabsf(v[DIM + 1]) + fabsf(vb[DIM + 1]));
+        float hk = 0.5f * kin / v[0];
+        float re = v[DIM + 1] - hk;
+        float dre = de + 0.5f * dkin / (v[0] - dr) + hk * dr / (v[0] - dr) + re_rel * (fabsf(v[DIM + 1]) + hk);
+        return re - dre >= epsf;
+    } else {
+        float mr = tiny_rel * (fabsf(v[0]) + fabsf(vb[0]));
+        return (v[0] - mr >= P.f.lo) && (v[0] + mr <= P.f.hi);
+    }
+}
 
 // The FP64 evaluation of the represented polynomial at S_K point p:
 // ubar + (double)(FP32 interpolation of dev - dbar).  Defines "in the bounds".
@@ -325,8 +356,6 @@ __device__ void limit_x(const Params &P, const Bufs &B, SmemX<C> &S, int lc, int
                         const double *ub, float *dv, bool check_avg, bool stats, float (&pts)[C::PPT][C::M]) {
     constexpr int DIM = C::D, PHYS = C::PH;
     constexpr int M = C::M, NN = C::NN, NSK = C::NSK, PPT = C::PPT;
-    const float tiny_rel = 2.384185791015625e-07f;  // 2^-22: margin of the screen on a component
-    const float re_rel = 3.814697265625e-06f;       // 2^-18: margin of the screen on rho*e
     publish_dev(ub, dv, S, lc, node);
     // 1. FP32 screen of the S_K values with a rounding margin
     int unsafe = 0;
@@ -341,34 +370,7 @@ __device__ void limit_x(const Params &P, const Bufs &B, SmemX<C> &S, int lc, int
                 float d = s[c] - S.mean[lc][c];
                 pts[j][c] = S.ubf[lc][c] + d;
             }
-            if constexpr (PHYS == PH_EULER) {
-                // |FP64 evaluation - FP32 value| <= 2^-23 (|v| + |vbar|) per component (doubled
-                // here); propagate to rho e = E - |m|^2 / (2 rho) to first order plus the
-                // FP32 rounding of the formula itself
-                const float *v = pts[j];
-                const float *vb = S.ubf[lc];
-                const float epsf = (float)P.eps * 1.0000002f;
-                float dr = tiny_rel * (fabsf(v[0]) + fabsf(vb[0]));
-                float kin = 0.0f, dkin = 0.0f;
-#pragma unroll
-                for (int d = 1; d <= DIM; ++d) {
-                    kin += v[d] * v[d];
-                    dkin += 2.0f * fabsf(v[d]) * tiny_rel * (fabsf(v[d]) + fabsf(vb[d]));
-                }
-                float de = tiny_rel * (fabsf(v[DIM + 1]) + fabsf(vb[DIM + 1]));
-                if (!(v[0] - dr >= epsf) || !(v[0] > 0.0f)) {
-                    unsafe = 1;
-                } else {
-                    float hk = 0.5f * kin / v[0];
-                    float re = v[DIM + 1] - hk;
-                    float dre = de + 0.5f * dkin / (v[0] - dr) + hk * dr / (v[0] - dr) +
-                                re_rel * (fabsf(v[DIM + 1]) + hk);
-                    if (!(re - dre >= epsf)) unsafe = 1;
-                }
-            } else {
-                float mr = tiny_rel * (fabsf(pts[j][0]) + fabsf(S.ubf[lc][0]));
-                if (!(pts[j][0] - mr >= (float)P.lo) || !(pts[j][0] + mr <= (float)P.hi)) unsafe = 1;
-            }
+            if (!screen_ok<PHYS, DIM>(P, pts[j], S.ubf[lc])) unsafe = 1;
         }
     }
     S.fl[lc][node] = unsafe;
@@ -376,7 +378,9 @@ __device__ void limit_x(const Params &P, const Bufs &B, SmemX<C> &S, int lc, int
     if (node == 0) {
         int any = 0;
         for (int q = 0; q < NN; ++q) any |= S.fl[lc][q];
-        if (check_avg && active && !admissible<PHYS, DIM>(P, ub)) atomicOr(B.flag, 1);
+        // the averages' admissibility: the FP32 screen clears it, else the FP64 test decides
+        if (check_avg && active && !screen_ok<PHYS, DIM>(P, S.ubf[lc], S.ubf[lc]) && !admissible<PHYS, DIM>(P, ub))
+            atomicOr(B.flag, 1);
         S.unsafe[lc] = any;
         S.bad[lc] = 0;
     }
@@ -582,7 +586,7 @@ __global__ void __launch_bounds__(C::NT) k_inner_x(Params P, MixBufs X) {
                     float inc = 0.0f;
 #pragma unroll
                     for (int j = 0; j < i; ++j)
-                        if (P.A[i][j] != 0.0) inc = fmaf((float)(P.dt * P.A[i][j]), gbh[j][k], inc);
+                        if (P.f.dtA[i][j] != 0.0f) inc = fmaf(P.f.dtA[i][j], gbh[j][k], inc);
                     double v = ub0[k] + (double)inc;
                     S.ubd[lc][c] = v;
                     S.ubf[lc][c] = (float)v;
@@ -593,7 +597,7 @@ __global__ void __launch_bounds__(C::NT) k_inner_x(Params P, MixBufs X) {
                 float w = dv0[c];
 #pragma unroll
                 for (int j = 0; j < i; ++j)
-                    if (P.A[i][j] != 0.0) w = fmaf((float)(P.dt * P.A[i][j]), gd[j][c], w);
+                    if (P.f.dtA[i][j] != 0.0f) w = fmaf(P.f.dtA[i][j], gd[j][c], w);
                 dvc[c] = w;
             }
             __syncthreads();
@@ -612,9 +616,9 @@ __global__ void __launch_bounds__(C::NT) k_inner_x(Params P, MixBufs X) {
 #pragma unroll
                 for (int c = 0; c < M; ++c)
                     X.nod_out[((size_t)c * P.ncell + cell) * NN + node] = (double)S.gbf[lc][c] + (double)gd[i][c];
-        } else if (P.b[i] != 0.0) {
+        } else if (P.f.dtb[i] != 0.0f) {
 #pragma unroll
-            for (int c = 0; c < M; ++c) dacc[c] = fmaf((float)(P.dt * P.b[i]), gd[i][c], dacc[c]);
+            for (int c = 0; c < M; ++c) dacc[c] = fmaf(P.f.dtb[i], gd[i][c], dacc[c]);
         }
         if (P.slot[i] >= 0 && active) {
             float *dst = X.tr + (size_t)P.slot[i] * M * P.ncell * NTR;
@@ -663,7 +667,7 @@ __global__ void __launch_bounds__(C::NT) k_final_x(Params P, MixBufs X) {
     for (int i = 0; i < P.s; ++i) {
         if (P.slot[i] < 0) continue;
         const float *tr = X.tr + (size_t)P.slot[i] * M * P.ncell * NTR;
-        const float bi = (float)P.b[i];
+        const float bi = P.f.b[i];
         float uL[FPT][M], uR[FPT][M];
 #pragma unroll
         for (int j = 0; j < FPT; ++j) {
@@ -729,7 +733,7 @@ __global__ void __launch_bounds__(C::NT) k_final_x(Params P, MixBufs X) {
             }
     }
     __syncthreads();
-    const float rhx = (float)P.rhx, rhy = (float)P.rhy;
+    const float rhx = P.f.rhx, rhy = P.f.rhy;
     float corr[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) {
@@ -773,7 +777,7 @@ __global__ void __launch_bounds__(C::NT) k_final_x(Params P, MixBufs X) {
     }
     __syncthreads();
     float dvn[M];
-    const float fdt = (float)P.dt;
+    const float fdt = P.f.dt;
 #pragma unroll
     for (int c = 0; c < M; ++c) dvn[c] = fmaf(fdt, corr[c] - S.mean[lc][c], dvs[c]);
     float pts[C::PPT][M];
@@ -890,7 +894,7 @@ __global__ void __launch_bounds__(C::NT) k_scan_x(Params P, MixBufs X) {
     publish_dev(ub, dv, S, lc, node);
     float amax = 0.0f;
     double m0 = INFINITY, m1 = INFINITY;
-    const float rhx = (float)P.rhx, rhy = (float)P.rhy;
+    const float rhx = P.f.rhx, rhy = P.f.rhy;
 #pragma unroll
     for (int j = 0; j < C::PPT; ++j) {
         int p = node + j * NN;

@@ -49,6 +49,17 @@ struct NodalTables {
     float w1f[MAXN], w2f[MAXN * MAXN];
 };
 
+// FP32 copies of the parameters for the split-precision kernels, rounded once by
+// the host at launch (the kernels then never convert a double parameter).
+struct ParamsF {
+    float rhx, rhy, gamma, gm1, velx, vely, lo, hi, eps;
+    float bcs[4][MAXM];
+    float dtA[MAXS][MAXS];  // (float)(dt a_ij)
+    float dtb[MAXS];        // (float)(dt b_i)
+    float b[MAXS];
+    float dt;
+};
+
 struct Params {
     int nx, ny, ncell;
     double rhx, rhy;  // 2/hx, 2/hy
@@ -66,6 +77,7 @@ struct Params {
     int defer_limit;  // final kernel leaves the limiter to the troubled-cell kernel
     double tvb_M;     // TVB constant of the plain indicator
     int ind_stage;    // troubled-cell kernel: 0 decide and limit, 1 decide only, 2 limit given flags
+    ParamsF f;        // split-precision kernels only
 };
 
 struct Bufs {

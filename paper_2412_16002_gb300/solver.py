@@ -176,6 +176,25 @@ class Solver:
         self._chk(self.lib.crkdg_troubled_flags(self.h, C.c_void_p(f.ctypes.data), 0))
         return f
 
+    # ---- learned troubled-cell indicator ---------------------------------------------
+    def set_mlp(self, params):
+        """Network of the 'mlp' indicator: a CUDA float32 tensor of CRKDG_MLP_NPARAM values."""
+        assert _is_torch(params) and params.is_cuda and params.element_size() == 4 and params.numel() == 7105
+        self._chk(self.lib.crkdg_set_mlp(self.h, C.c_void_p(params.data_ptr())))
+
+    def set_harvest(self, on=True):
+        """Keep each step's indicator features (training data for the network)."""
+        self._chk(self.lib.crkdg_set_harvest(self.h, 1 if on else 0))
+
+    def last_features(self, out=None):
+        """Features of the last step, [ncell][44] float32 (numpy, or into a CUDA tensor)."""
+        if out is not None and _is_torch(out):
+            self._chk(self.lib.crkdg_last_features(self.h, C.c_void_p(out.data_ptr()), 1))
+            return out
+        f = np.empty((self.nx * self.ny, 44), dtype=np.float32)
+        self._chk(self.lib.crkdg_last_features(self.h, C.c_void_p(f.ctypes.data), 0))
+        return f
+
     def averages(self):
         a = np.empty(self.nx * self.ny * self.m)
         self._chk(self.lib.crkdg_cell_averages(self.h, C.c_void_p(a.ctypes.data), 0))

@@ -58,7 +58,7 @@ def _ghost(o, avg, cx, cy, dx, dy, bc):
     return v
 
 
-def _expected_features(o, modal, bc):
+def _expected_features(o, modal, bc, thr):
     """Features from the oracle's modal state: averages on the 3x3 stencil and the centre cell's
     first Legendre moments c_10 (x) and c_01 (y), through the FP64 reference feature map."""
     avg = o.averages(modal)  # [ny][nx][m]
@@ -69,7 +69,7 @@ def _expected_features(o, modal, bc):
             a3 = np.stack([_ghost(o, avg, cx, cy, dx, dy, bc) for dy in (-1, 0, 1) for dx in (-1, 0, 1)], axis=1)
             cell = cy * o.nx + cx
             sl = np.array([[modal[cell * per + c * n * n + 1], modal[cell * per + c * n * n + n]] for c in range(o.m)])
-            out[cell] = mlp.features(a3, sl)
+            out[cell] = mlp.features(a3, sl, thr)
     return out
 
 
@@ -85,8 +85,7 @@ def test_features_match_oracle_state(lib, k):
     o = Oracle(2, 12, 12, k, wl.domain, "euler", gamma=wl.gamma, eps=wl.eps, bc=wl.bc, indicator=True, tvb_M=1.0)
     g.set_state(wl.state)
     o.set_state(wl.state)
-    g._chk(lib.crkdg_set_harvest(g.h, 1))
-    feat = np.empty((12 * 12, 44), dtype=np.float32)
+    g.set_harvest(True)
     t = 0.0
     for _ in range(3):
         dt = o.max_dt(wl.cfl)
@@ -96,8 +95,8 @@ def test_features_match_oracle_state(lib, k):
         assert rc == 0
         rc, us, _ = o.step_stages(dt, ORACLE_TABS[wl.tableau], t, modal=before)
         t += dt
-        g._chk(lib.crkdg_last_features(g.h, C.c_void_p(feat.ctypes.data), 0))
-        ref = _expected_features(o, us[-1], wl.bc)
+        feat = g.last_features()
+        ref = _expected_features(o, us[-1], wl.bc, 1.0 / 144.0)
         assert np.abs(feat - ref).max() < 1e-5
         assert np.array_equal(g.troubled_flags(), o.troubled(us[-1]))
 
@@ -150,12 +149,10 @@ def _harvest(seeds, n=48, steps=12):
         wl = inputs.riemann_quadrants(seed, n, 2)
         g = Solver.from_workload(wl, indicator="tvb", tvb_M=1.0)
         g.set_state(wl.state)
-        g._chk(g.lib.crkdg_set_harvest(g.h, 1))
-        feat = np.empty((n * n, 44), dtype=np.float32)
+        g.set_harvest(True)
         for _ in range(steps):
             g.step(g.max_dt(wl.cfl), wl.tableau)
-            g._chk(g.lib.crkdg_last_features(g.h, C.c_void_p(feat.ctypes.data), 0))
-            X.append(feat.copy())
+            X.append(g.last_features())
             Y.append(g.troubled_flags().astype(np.float32))
     return np.concatenate(X), np.concatenate(Y)
 
@@ -166,7 +163,8 @@ def test_training_on_harvested_labels_learns_the_plain_indicator(lib):
     all-smooth classifier."""
     Xtr, Ytr = _harvest(range(1000, 1006))
     Xte, Yte = _harvest(range(2000, 2002))
-    assert 0.01 < Ytr.mean() < 0.5
+    print(f"harvest: {len(Ytr)} cells, troubled fraction {Ytr.mean():.4f}")
+    assert Ytr.sum() >= 100 and Ytr.mean() < 0.5
     theta = torch.tensor(mlp.init_params(7), dtype=torch.float32, device="cuda")
     m = torch.zeros_like(theta)
     v = torch.zeros_like(theta)
@@ -192,8 +190,11 @@ def test_training_on_harvested_labels_learns_the_plain_indicator(lib):
             if first is None:
                 torch.cuda.synchronize()
                 first = float(loss.item())
+    grad.zero_()
+    loss.zero_()
+    assert lib.crkdg_mlp_grad(_ptr(theta), _ptr(tx), _ptr(ty), n, _ptr(grad), _ptr(loss), None) == 0
     torch.cuda.synchronize()
-    last = float(loss.item())
+    last = float(loss.item())  # mean loss over the whole training set
     assert last < 0.5 * first
     te = torch.tensor(Xte, device="cuda")
     pr = torch.empty(te.shape[0], device="cuda")
@@ -201,4 +202,5 @@ def test_training_on_harvested_labels_learns_the_plain_indicator(lib):
     torch.cuda.synchronize()
     acc = float(((pr.cpu().numpy() > 0.5) == (Yte > 0.5)).mean())
     base = max(Yte.mean(), 1 - Yte.mean())
+    print(f"held-out accuracy {acc:.4f} (all-smooth classifier {base:.4f}); loss {first:.4f} -> {last:.4f}")
     assert acc > base + 0.5 * (1 - base), (acc, base)

@@ -1,5 +1,5 @@
 """Pins of the FP64 reference MLP (troubled-cell classifier): finite-difference gradients,
-closed forms of the loss, invariances of the features, and learning a separable set."""
+closed forms of the loss, invariances and the threshold floor of the features, and learning a separable set."""
 import numpy as np
 
 from oracle import mlp
@@ -29,17 +29,27 @@ def test_bce_closed_forms():
     assert np.allclose(mlp.sigmoid(np.array([0.0, 800.0, -800.0])), [0.5, 1.0, 0.0])
 
 
-def test_features_are_scale_and_shift_invariant():
+def test_features_scale_shift_and_threshold():
     rng = np.random.default_rng(2)
     a = rng.uniform(0.5, 2.0, size=(3, 4, 9))
     s = rng.normal(size=(3, 4, 2))
     f = mlp.features(a, s)
     assert f.shape == (3, 44)
-    f2 = mlp.features(7.0 * a + 3.0, 7.0 * s)
-    assert np.allclose(f, f2, atol=1e-10)
-    # per-component normalisation: z lies in [-1, 1] with range exactly 1
+    # scaling values, slopes and threshold together leaves the features unchanged
+    assert np.allclose(mlp.features(7.0 * a, 7.0 * s, 7.0 * 0.01), mlp.features(a, s, 0.01), rtol=0, atol=1e-12)
+    # a shift changes only delta = 1e-6 max|v|
+    assert np.allclose(mlp.features(a + 3.0, s), f, rtol=0, atol=1e-5)
+    # without a threshold: z spans exactly [.,.] of range 1 (up to delta)
     z = f[:, :36].reshape(3, 4, 9)
-    assert np.allclose(z.max(-1) - z.min(-1), 1.0)
+    assert np.allclose(z.max(-1) - z.min(-1), 1.0, rtol=0, atol=1e-5)
+    # below the threshold: (v - mean) / (thr + delta), slopes likewise
+    b = 1.0 + 1e-3 * rng.uniform(size=(4, 9))
+    sb = 1e-3 * rng.normal(size=(4, 2))
+    fb = mlp.features(b, sb, thr=0.05)
+    den = 0.05 + 1e-6 * b.max(-1, keepdims=True)
+    assert np.allclose(fb[:36].reshape(4, 9), (b - b.mean(-1, keepdims=True)) / den, rtol=1e-12, atol=0)
+    assert np.allclose(fb[36:].reshape(4, 2), sb / den, rtol=1e-12, atol=0)
+    assert np.abs(fb).max() < 0.05
 
 
 def test_adam_learns_a_separable_set():
