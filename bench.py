@@ -41,6 +41,9 @@ WORKLOADS = {
     "sedov_512_q3_mixed": dict(kind="sedov", nx=512, k=3, precision="mixed"),
     "riemann_1024_q2": dict(kind="riemann", nx=1024, k=2),
     "riemann_1024_q2_mixed": dict(kind="riemann", nx=1024, k=2, precision="mixed"),
+    "riemann_1024_q2_tvb": dict(kind="riemann", nx=1024, k=2, indicator="tvb"),
+    "riemann_1024_q2_mlp": dict(kind="riemann", nx=1024, k=2, indicator="mlp"),
+    "ensemble_64_riemann_mlp": dict(kind="ensemble", count=64, indicator="mlp"),
 }
 DEFAULT = "euler1d_blast_tube_4096_p2"
 
@@ -49,6 +52,8 @@ def make_workload(name, seed=0, nx=None):
     from paper_2412_16002_gb300 import inputs
 
     w = dict(WORKLOADS[name])
+    if w["kind"] == "ensemble":  # sampled as one of its problems (Q^2 Riemann)
+        w = dict(kind="riemann", nx=nx or 256, k=2)
     if nx is not None:
         w["nx"] = nx
     if w["kind"] == "euler1d":
@@ -257,7 +262,13 @@ def run_gb300(args, wl, name):
 
     stream = torch.cuda.current_stream()
     precision = WORKLOADS[name].get("precision", "fp64")
-    g = Solver.from_workload(wl, stream=stream, precision=precision)
+    indicator = WORKLOADS[name].get("indicator", "off")
+    train = None
+    if indicator == "mlp":
+        theta, train = trained_indicator()
+    g = Solver.from_workload(wl, stream=stream, precision=precision, indicator=indicator)
+    if indicator == "mlp":
+        g.set_mlp(theta)
     u0 = torch.from_numpy(wl.state).to(dev)
     g.set_state(u0)
     t = 0.0
@@ -360,7 +371,8 @@ def run_gb300(args, wl, name):
             "vs_baseline": None,
             "dtype": "f64" if precision == "fp64" else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": name, "precision": precision, "cells": wl.cells, "k": wl.k, "m": wl.m, "dofs_per_cell": wl.dofs_per_cell,
+            "config": {"workload": name, "precision": precision, "indicator": indicator, "training": train,
+                       "cells": wl.cells, "k": wl.k, "m": wl.m, "dofs_per_cell": wl.dofs_per_cell,
                        "tableau": wl.tableau, "stages": TAB_S[wl.tableau], "cfl": wl.cfl,
                        "l2": l2_note, "parallelism": f"replicas{world}",
                        "restarts_in_timed_steps": restarts, "t_after": t},
@@ -387,6 +399,151 @@ def run_gb300(args, wl, name):
         dist.destroy_process_group()
 
 
+def trained_indicator(seeds=range(1000, 1004), n=256, steps=800, every=200, epochs=8):
+    """The learned indicator's network, trained on the GPU by the library's kernels on about
+    1e6 cells labelled by the plain indicator in seeded 256^2 Q^2 Riemann runs (4 snapshots
+    per run at t ~ 0.05, 0.1, 0.15, 0.2).  Returns (params, summary)."""
+    from paper_2412_16002_gb300 import indicator as ind
+
+    t0 = time.perf_counter()
+    X, Y = ind.harvest(seeds, n=n, k=2, steps=steps, every=every)
+    theta, hist = ind.train(X, Y, epochs=epochs)
+    conf = ind.confusion(theta, X, Y)
+    summary = {"cells": int(Y.numel()), "troubled_fraction": float(Y.mean().item()), "epochs": epochs,
+               "loss": hist[-1], "train_agreement": conf["accuracy"], "undecided": conf["undecided"],
+               "seconds": time.perf_counter() - t0}
+    del X, Y
+    return theta, summary
+
+
+def run_ensemble(args, name):
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        from paper_2412_16002_gb300 import build
+
+        build()
+    if world > 1:
+        dist.barrier()
+    from paper_2412_16002_gb300 import inputs
+    from paper_2412_16002_gb300.ensemble import Ensemble, riemann_ensemble_specs, riemann_problem
+
+    spec = WORKLOADS[name]
+    specs = riemann_ensemble_specs(spec["count"], seed=0)
+    theta, train = trained_indicator()
+    probs = [riemann_problem(s, n, k) for s, n, k in specs]
+    for p in probs:
+        p["t_end"] = 1e30
+    ens = Ensemble(probs, indicator=spec["indicator"])
+    ens.set_mlp(theta)
+    for i, (s, n, k) in enumerate(specs):
+        x = inputs.riemann_quadrants_device(s, n, k, device=dev)
+        ens.set_state(i, x)
+        del x
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tiles = ens.autotune(reps=1)
+    tune_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        ens.step()
+    cells = sum(n * n for _, n, _ in specs)
+    units_step = sum(n * n * 4 * (k + 1) ** 2 * (4 if k == 3 else 3) for _, n, k in specs)
+    flops_step = 0
+    for _, n, k in specs:
+        wl = inputs.Workload("x", 2, 1, 1, k, (0, 1, 0, 1), "euler", ("outflow",) * 4, None,
+                             tableau="rk4" if k == 3 else "heun3")
+        fi, ff = algorithmic_flops(wl)
+        flops_step += (fi + ff) * n * n
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ens.set_profiling(True)
+    for _ in range(args.steps):
+        ens.step()
+    ms, nst = ens.times()
+    ens.set_profiling(False)
+    clocks = sampler.stop() if sampler else None
+    tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ms_max = float(tt.item())
+    value = units_step * args.steps * world / (ms_max / 1e3)
+    troubled = sum(ens.info(i)["troubled"] for i in range(len(specs)))
+    restarts = sum(ens.info(i)["restarts"] for i in range(len(specs)))
+
+    # end to end through the C ABI with host buffers: every problem's state host -> device,
+    # K steps, every state device -> host (pinned host memory)
+    hosts = [torch.empty(ens.state_size(i), dtype=torch.float64).pin_memory() for i in range(len(specs))]
+    for i in range(len(specs)):
+        ens.get_state(i, hosts[i].numpy())
+    nbytes = sum(h.numel() * 8 for h in hosts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(len(specs)):
+        ens.set_state(i, hosts[i].numpy())
+    for _ in range(args.steps):
+        ens.step()
+    for i in range(len(specs)):
+        ens.get_state(i, hosts[i].numpy())
+    e2e_s = time.perf_counter() - t0
+    e2e_value = units_step * args.steps * world / e2e_s
+    del hosts
+    if rank == 0:
+        achieved = flops_step * args.steps / (ms_max / 1e3) / 1e12
+        line = {
+            "metric": "cell-DOF updates/s per RK stage",
+            "value": value,
+            "unit": "cell-DOF-stage/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": name, "problems": len(specs), "cells": cells,
+                       "dofs": sum(n * n * 4 * (k + 1) ** 2 for _, n, k in specs),
+                       "q3_problems": sum(k == 3 for _, _, k in specs), "sizes": "256^2..1536^2 (seeded)",
+                       "indicator": spec["indicator"], "tiles": tiles, "autotune_s": tune_s,
+                       "training": train, "troubled_cells_last_step": troubled,
+                       "restarts_total": restarts, "graph_steps_timed": nst,
+                       "l2": "inputs larger than L2 (state 26 GB)", "parallelism": f"replicas{world}"},
+            "roofline": {"bound": "alu", "kernel": "k_ens (ensemble step graph)", "achieved": achieved,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "traffic": None,
+                         "peak_source": "FP64 derived from unit count and clock (152 SMs x 4 flop/clk x 2070 MHz)",
+                         "note": "FP64 flops of the method per step (the network's FP32 work not counted)"},
+            "e2e": {"value": e2e_value, "unit": "cell-DOF-stage/s", "h2d_bytes_per_step": nbytes // args.steps,
+                    "d2h_bytes_per_step": nbytes // args.steps},
+            "gpu_launches": int(nst) * 14,
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            v, n, el, swl = oracle_rate(make_workload(name, nx=64), budget_s=args.cpu_seconds)
+            line["cpu_baseline"] = {"value": v, "unit": "cell-DOF-stage/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"{n} time steps of one Q^2 Riemann problem of the ensemble on a "
+                                              f"64x64 mesh ({el:.1f} s, one thread, no indicator)"}
+        print(json.dumps(line))
+    ens.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -401,6 +558,8 @@ def main():
     wl = make_workload(args.workload)
     if args.impl == "reference":
         run_reference(args, wl, args.workload)
+    elif WORKLOADS[args.workload]["kind"] == "ensemble":
+        run_ensemble(args, args.workload)
     else:
         run_gb300(args, wl, args.workload)
 

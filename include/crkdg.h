@@ -194,9 +194,12 @@ crkdg_status crkdg_troubled_flags(crkdg_t h, int *flags, int on_device);
 /* ------------------------------------------------------------------------
  * Learned troubled-cell indicator (CRKDG_IND_MLP; not part of the paper).  A
  * 44 -> 64 -> 64 -> 1 ReLU network with a sigmoid output classifies a cell from
- * its features: per conservative component the 3x3 neighbourhood of cell
- * averages normalised by the stencil mean and range, and the cell's first
- * Legendre moments over the same range (2D Euler).  A cell is troubled when the
+ * its features (2D Euler; layout [cell][44]): per conservative component the
+ * 3x3 neighbourhood of cell averages minus their mean, over den = max(range,
+ * tvb_M hx hy) + 1e-6 max|v| (36 values, [comp][row-major 3x3]), then the cell's
+ * first Legendre moments c_10, c_01 over the same den (8 values, [comp][x,y]).
+ * Stencil positions outside the domain take the nearest interior cell's average
+ * with the crossed sides' boundary states applied.  A cell is troubled when the
  * probability exceeds 0.6, smooth below 0.4, and takes the plain TVB decision in
  * between; the shock limiter and the scaling limiter then act as for the plain
  * indicator.  Parameters are FP32, layout W1[64][44], b1[64], W2[64][64], b2[64],
@@ -254,6 +257,81 @@ size_t crkdg_state_size(crkdg_t h);
 
 /* Human-readable description of the last error on h (static string if h is NULL). */
 const char *crkdg_last_error(crkdg_t h);
+
+/* ------------------------------------------------------------------------
+ * Ensembles of 2D Euler problems of uneven size (not part of the paper).  One
+ * handle advances many independent problems (each its own mesh, degree k = 2 or
+ * 3, tableau, CFL and end time) with the method of crkdg_step: every problem takes
+ * its own trial step (crkdg_max_dt rule, clipped to its end time) and its own
+ * halve-and-restart loop (Sec. 4.1).  The states live in one concatenated device
+ * arena with a per-problem descriptor table; each kernel of a step is one
+ * persistent launch per degree whose blocks pull (problem, tile) work items from
+ * a device counter, and a step is one CUDA graph launch (attempts after a restart
+ * replay a graph that only the restarting problems take part in).  The tile size
+ * of the work items is chosen per (degree, size class) by crkdg_ensemble_autotune.
+ * Results are bit-identical to stepping each problem alone with crkdg_step at the
+ * same trial steps.  FP64 path; indicators as in crkdg_options (the learned
+ * indicator runs one network evaluation over all problems' cells per attempt). */
+typedef struct crkdg_ensemble_ctx *crkdg_ens_t;
+
+typedef struct {
+    crkdg_mesh mesh;              /* dim must be 2 */
+    int k;                        /* 2 or 3 */
+    const crkdg_tableau *tableau; /* copied at creation */
+    double cfl;                   /* trial-step CFL number (> 0) */
+    double t_end;                 /* the problem stops when it reaches t_end */
+} crkdg_ens_problem;
+
+/* Per-problem progress (crkdg_ensemble_info). */
+typedef struct {
+    double t;                 /* current time */
+    long long steps;          /* accepted steps */
+    long long restarts;       /* halvings over all steps */
+    int done;                 /* reached t_end */
+    int status;               /* CRKDG_OK, or CRKDG_E_BOUNDS if it stopped after max_halvings */
+    crkdg_step_info last;     /* the last accepted step */
+} crkdg_ens_info;
+
+/* Create an ensemble of count problems (m = 4, flux kind EULER, shared gamma,
+ * bounds and options; options.precision must be FP64).  Allocates every buffer
+ * at once.  Errors: CRKDG_E_ARG, CRKDG_E_UNSUPPORTED, CRKDG_E_OOM, CRKDG_E_CUDA. */
+crkdg_status crkdg_ensemble_create(int count, const crkdg_ens_problem *problems, int m, const crkdg_flux *flux,
+                                   const crkdg_bounds *bounds, const crkdg_options *opt, crkdg_ens_t *out);
+crkdg_status crkdg_ensemble_destroy(crkdg_ens_t e);
+/* Nodal state of problem i (layout and count as for a single handle of its mesh
+ * and k); set_state applies the scaling limiter and resets the problem's time to 0. */
+crkdg_status crkdg_ensemble_set_state(crkdg_ens_t e, int i, const double *nodal, size_t count, int on_device);
+crkdg_status crkdg_ensemble_get_state(crkdg_ens_t e, int i, double *nodal, size_t count, int on_device);
+size_t crkdg_ensemble_state_size(crkdg_ens_t e, int i);
+/* One step of every problem that has not reached its end time; *active
+ * (nullable) receives how many problems are still running afterwards.  A problem
+ * whose averages stay outside B^eps after max_halvings restarts stops with status
+ * CRKDG_E_BOUNDS (its state stays at its last accepted step); the call itself
+ * then returns CRKDG_E_BOUNDS after the other problems have stepped. */
+crkdg_status crkdg_ensemble_step(crkdg_ens_t e, int *active);
+crkdg_status crkdg_ensemble_info(crkdg_ens_t e, int i, crkdg_ens_info *info);
+/* Network of the learned indicator (device pointer, CRKDG_MLP_NPARAM floats). */
+crkdg_status crkdg_ensemble_set_mlp(crkdg_ens_t e, const float *params);
+/* Time one attempt (inner and final kernels) per candidate tile size for every
+ * (degree, size class) present, reps times each, keep the fastest and rebuild the
+ * step graphs.  Problems' states are not changed.  chosen (nullable, 6 ints)
+ * receives the tiles (blocks of cells per work item) for classes
+ * {k=2, k=3} x {<= 512^2, <= 1024^2, larger cells}; 0 where a class is empty. */
+crkdg_status crkdg_ensemble_autotune(crkdg_ens_t e, int reps, int chosen[6]);
+/* Host-only planning (no GPU needed): the work items of one degree group for
+ * problems of ncells[i] cells split into blocks of cells_per_block cells, tile[i]
+ * blocks per item, largest problems first.  Writes up to cap items as
+ * (problem, first block, blocks) triples into items; returns the item count
+ * (or -1 on bad arguments). */
+int crkdg_ensemble_plan(int count, const long long *ncells, const int *tile, int cells_per_block, int *items,
+                        int cap);
+/* Device timing: while on, each crkdg_ensemble_step brackets its graph launches
+ * (the step and any retry attempts) with CUDA events on the ensemble's stream;
+ * crkdg_ensemble_times returns the milliseconds and the number of steps timed
+ * since profiling was last switched on (switching on resets them). */
+crkdg_status crkdg_ensemble_set_profiling(crkdg_ens_t e, int on);
+crkdg_status crkdg_ensemble_times(crkdg_ens_t e, double *ms, long long *steps);
+const char *crkdg_ensemble_last_error(crkdg_ens_t e);
 
 /* ------------------------------------------------------------------------
  * Allocation-free DG operator.  The paper has no counterpart: this entry point

@@ -47,6 +47,16 @@ class StepInfo(C.Structure):
                 ("theta_min", C.c_double), ("troubled", C.c_longlong), ("mass_drift", C.c_double)]
 
 
+class EnsProblem(C.Structure):
+    _fields_ = [("mesh", Mesh), ("k", C.c_int), ("tableau", C.POINTER(Tableau)), ("cfl", C.c_double),
+                ("t_end", C.c_double)]
+
+
+class EnsInfo(C.Structure):
+    _fields_ = [("t", C.c_double), ("steps", C.c_longlong), ("restarts", C.c_longlong), ("done", C.c_int),
+                ("status", C.c_int), ("last", StepInfo)]
+
+
 class CrkdgError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -89,6 +99,21 @@ SYMBOLS = {
     "crkdg_last_error": (C.c_char_p, [_H]),
     "crkdg_apply_F_noalloc": (C.c_int, [C.POINTER(Mesh), C.c_int, C.c_int, C.POINTER(Flux), C.c_void_p,
                                         C.c_void_p, C.c_void_p]),
+    "crkdg_ensemble_create": (C.c_int, [C.c_int, C.POINTER(EnsProblem), C.c_int, C.POINTER(Flux), C.POINTER(Bounds),
+                                        C.POINTER(Options), C.POINTER(_H)]),
+    "crkdg_ensemble_destroy": (C.c_int, [_H]),
+    "crkdg_ensemble_set_state": (C.c_int, [_H, C.c_int, C.c_void_p, C.c_size_t, C.c_int]),
+    "crkdg_ensemble_get_state": (C.c_int, [_H, C.c_int, C.c_void_p, C.c_size_t, C.c_int]),
+    "crkdg_ensemble_state_size": (C.c_size_t, [_H, C.c_int]),
+    "crkdg_ensemble_step": (C.c_int, [_H, C.POINTER(C.c_int)]),
+    "crkdg_ensemble_info": (C.c_int, [_H, C.c_int, C.POINTER(EnsInfo)]),
+    "crkdg_ensemble_set_mlp": (C.c_int, [_H, C.c_void_p]),
+    "crkdg_ensemble_autotune": (C.c_int, [_H, C.c_int, C.POINTER(C.c_int)]),
+    "crkdg_ensemble_plan": (C.c_int, [C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.c_int,
+                                      C.POINTER(C.c_int), C.c_int]),
+    "crkdg_ensemble_set_profiling": (C.c_int, [_H, C.c_int]),
+    "crkdg_ensemble_times": (C.c_int, [_H, _dp, C.POINTER(C.c_longlong)]),
+    "crkdg_ensemble_last_error": (C.c_char_p, [_H]),
 }
 
 
@@ -111,4 +136,10 @@ def load(path: str = LIB_PATH):
 def check(lib, h, status):
     if status != OK:
         msg = lib.crkdg_last_error(h)
+        raise CrkdgError(status, msg.decode() if msg else "")
+
+
+def check_ens(lib, e, status):
+    if status != OK:
+        msg = lib.crkdg_ensemble_last_error(e)
         raise CrkdgError(status, msg.decode() if msg else "")

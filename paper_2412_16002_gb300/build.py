@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcrkdg.so")
-SOURCES = ["crkdg_api.cu", "dg_1d.cu", "dg_2d.cu", "crkdg_noalloc.cu", "mlp.cu"]
+SOURCES = ["crkdg_api.cu", "dg_1d.cu", "dg_2d.cu", "dg_ens.cu", "crkdg_ensemble.cu", "crkdg_noalloc.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

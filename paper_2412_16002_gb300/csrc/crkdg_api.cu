@@ -127,6 +127,8 @@ void build_tables(NodalTables *tab) {
 
 }  // namespace
 
+void crkdg_build_tables(NodalTables *tab) { build_tables(tab); }
+
 struct crkdg_ctx {
     crkdg_mesh mesh;
     crkdg_flux flux;
@@ -634,12 +636,9 @@ crkdg_status crkdg_step(crkdg_t h, double dt, const crkdg_tableau *tab, crkdg_st
                         P.ind_stage = 1;  // plain decision of the unlimited state
                         CK(h, launch(h, K_TROUBLE, P, B));
                         if (h->feat) CK(h, launch(h, K_FEATURES, P, B));
-                        if (learned) {
-                            if (crkdg_mlp_forward(h->mlp, h->feat, h->ncell, h->prob, h->st) != CRKDG_OK)
-                                return fail(h, CRKDG_E_CUDA, "step: MLP forward failed");
-                            CK(h, launch(h, K_COMBINE, P, B));
-                        }
-                        P.ind_stage = 2;  // limit the flagged cells
+                        if (learned && crkdg_mlp_forward(h->mlp, h->feat, h->ncell, h->prob, h->st) != CRKDG_OK)
+                            return fail(h, CRKDG_E_CUDA, "step: MLP forward failed");
+                        P.ind_stage = learned ? 3 : 2;  // (combine the learned flags and) limit the flagged cells
                     } else {
                         P.ind_stage = 0;
                     }

@@ -521,12 +521,12 @@ __device__ __forceinline__ void store_node(const Params &P, double *dst, int cel
 // and the accumulation u* = u^n + dt sum_i b_i G(u~^(i)); the traces of every
 // u~^(i) with b_i != 0 go to B.tr for the final kernel.
 template <int DIM, int N, int PHYS>
-__global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_inner(Params P, Bufs B) {
+__device__ __forceinline__ void inner_body(const Params &P, const Bufs &B, int blk) {
     using C = Cfg<DIM, N, PHYS>;
     constexpr int M = C::M, NN = C::NN, NTR = C::NTR, FPT = C::FPT;
     __shared__ Smem<C> S;
     const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
-    const int cell = blockIdx.x * C::NCB + lc;
+    const int cell = blk * C::NCB + lc;
     const bool active = cell < P.ncell;
     double un[M], cur[M], acc[M], gh[MAXS][M];
     load_node<DIM, N, PHYS>(P, B.un, cell, node, active, un);
@@ -571,18 +571,23 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_inner(Params P, Bufs 
     store_node<DIM, N, PHYS>(P, B.ustar, cell, node, active, acc);
 }
 
+template <int DIM, int N, int PHYS>
+__global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_inner(Params P, Bufs B) {
+    inner_body<DIM, N, PHYS>(P, B, blockIdx.x);
+}
+
 // Final stage: u^{n+1} = u* + dt lift( sum_i b_i (fhat^(i) - f(u_int^(i))) ), then the
 // limiter, the admissibility test and a0 of the new state.  Each face flux is
 // evaluated from the same ordered pair (lower side, upper side) by both cells
 // sharing the face, so the update is conservative to round-off.
 template <int DIM, int N, int PHYS>
-__global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_final(Params P, Bufs B) {
+__device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int blk) {
     using C = Cfg<DIM, N, PHYS>;
     constexpr int M = C::M, NN = C::NN, NF = C::NF, NTR = C::NTR, FPT = C::FPT;
     __shared__ Smem<C> S;
     const NodalTables &T = c_tab[N - 2];
     const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
-    const int cell = blockIdx.x * C::NCB + lc;
+    const int cell = blk * C::NCB + lc;
     const bool active = cell < P.ncell;
     const int a = node % N, b = DIM == 2 ? node / N : 0;
     double u[M];
@@ -703,6 +708,11 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_final(Params P, Bufs 
     store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
 }
 
+template <int DIM, int N, int PHYS>
+__global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_final(Params P, Bufs B) {
+    final_body<DIM, N, PHYS>(P, B, blockIdx.x);
+}
+
 // Limiter applied to a state (set-up projection, operator checks): un -> unew.
 template <int DIM, int N, int PHYS>
 __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_limit(Params P, Bufs B) {
@@ -738,7 +748,6 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_scan(Params P, Bufs B
         if (p < C::NSK && active) {
             double v[M];
             sk_eval<DIM, N, M, NN>(S.u[lc], p, v);
-#pragma unroll
             amax = fmax(amax, sk_rate<PHYS, DIM>(P, v));
             double a0m, a1m;
             if constexpr (PHYS == PH_EULER) {
@@ -796,7 +805,7 @@ __device__ __forceinline__ double minmod3d(double a, double b, double c) {
 // ubar + minmod(c_x, D+x, D-x) xi + minmod(c_y, D+y, D-y) eta, with c_x, c_y its
 // first Legendre moments.  Reads unew and the averages in aux; writes unew.
 template <int DIM, int N, int PHYS>
-__global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_trouble(Params P, Bufs B) {
+__device__ __forceinline__ void trouble_body(const Params &P, const Bufs &B, int blk) {
     using C = Cfg<DIM, N, PHYS>;
     constexpr int M = C::M, NN = C::NN;
     __shared__ Smem<C> S;
@@ -804,7 +813,7 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_trouble(Params P, Buf
     __shared__ int sTr[C::NCB];
     const NodalTables &T = c_tab[N - 2];
     const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
-    const int cell = blockIdx.x * C::NCB + lc;
+    const int cell = blk * C::NCB + lc;
     const bool active = cell < P.ncell;
     const int a = node % N, b = DIM == 2 ? node / N : 0;
     double u[M];
@@ -860,7 +869,11 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_trouble(Params P, Buf
         if (node == 0 && active) B.tflags[cell] = sTr[lc] != 0 ? 1 : 0;
         return;
     }
-    const bool troubled = active && (P.ind_stage == 2 ? B.tflags[cell] != 0 : sTr[lc] != 0);
+    bool troubled = active && (P.ind_stage >= 2 ? B.tflags[cell] != 0 : sTr[lc] != 0);
+    if (P.ind_stage == 3 && active) {  // learned flags: p > 0.6 troubled, p < 0.4 smooth, else the plain flag
+        const float pr = B.prob[cell];
+        troubled = pr > 0.6f ? true : (pr < 0.4f ? false : troubled);
+    }
     if (troubled) {
 #pragma unroll
         for (int c = 0; c < M; ++c) {
@@ -870,7 +883,7 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_trouble(Params P, Buf
         }
     }
     if (node == 0 && active) {
-        if (B.tflags && P.ind_stage == 0) B.tflags[cell] = troubled ? 1 : 0;
+        if (B.tflags && (P.ind_stage == 0 || P.ind_stage == 3)) B.tflags[cell] = troubled ? 1 : 0;
         if (troubled) atomicAdd(B.ntrb, 1ull);
     }
     double pts[C::PPT][M];
@@ -887,16 +900,21 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_trouble(Params P, Buf
     store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
 }
 
+template <int DIM, int N, int PHYS>
+__global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_trouble(Params P, Bufs B) {
+    trouble_body<DIM, N, PHYS>(P, B, blockIdx.x);
+}
+
 // MLP features of every cell (2D Euler): per component, the 3x3 neighbourhood of
 // cell averages (neighbours across a boundary follow its condition) normalised by the
 // stencil mean and range, and the cell's first Legendre moments over the same range.
 // Layout [cell][44]: 36 normalised averages ([comp][9], row-major, centre 4), then
 // 8 normalised moments ([comp][x, y]).  Reads unew and the averages in aux.
 template <int DIM, int N, int PHYS>
-__global__ void k_features(Params P, Bufs B) {
+__device__ __forceinline__ void features_body(const Params &P, const Bufs &B, int blk) {
     constexpr int M = ncomp(PHYS, DIM);
     constexpr int NN = DIM == 2 ? N * N : N;
-    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cell = blk * blockDim.x + threadIdx.x;
     if constexpr (DIM != 2 || PHYS != PH_EULER) {
         return;
     } else {
@@ -968,14 +986,9 @@ __global__ void k_features(Params P, Bufs B) {
     }
 }
 
-// Learned flags: troubled when the probability is above 0.6, smooth below 0.4, and the
-// plain indicator's decision (already in tflags) in between.
-static __global__ void k_combine(Params P, Bufs B) {
-    int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= P.ncell) return;
-    float p = B.prob[cell];
-    if (p > 0.6f) B.tflags[cell] = 1;
-    else if (p < 0.4f) B.tflags[cell] = 0;
+template <int DIM, int N, int PHYS>
+__global__ void k_features(Params P, Bufs B) {
+    features_body<DIM, N, PHYS>(P, B, blockIdx.x);
 }
 
 template <int DIM, int N, int PHYS>
@@ -987,7 +1000,6 @@ cudaError_t launch_one(int kernel, int nblocks, cudaStream_t st, const Params &P
     case K_LIMIT: k_limit<DIM, N, PHYS><<<nblocks, C::NT, 0, st>>>(P, B); break;
     case K_TROUBLE: k_trouble<DIM, N, PHYS><<<nblocks, C::NT, 0, st>>>(P, B); break;
     case K_FEATURES: k_features<DIM, N, PHYS><<<(P.ncell + 127) / 128, 128, 0, st>>>(P, B); break;
-    case K_COMBINE: k_combine<<<(P.ncell + 255) / 256, 256, 0, st>>>(P, B); break;
     case K_A0:
     case K_MARGINS: k_scan<DIM, N, PHYS><<<nblocks, C::NT, 0, st>>>(P, B); break;
     case K_AVG: {

@@ -76,7 +76,8 @@ struct Params {
     int mode;
     int defer_limit;  // final kernel leaves the limiter to the troubled-cell kernel
     double tvb_M;     // TVB constant of the plain indicator
-    int ind_stage;    // troubled-cell kernel: 0 decide and limit, 1 decide only, 2 limit given flags
+    int ind_stage;    // troubled-cell kernel: 0 decide and limit, 1 decide only, 2 limit given flags,
+                      // 3 combine the given plain flags with the learned probabilities, then limit
     ParamsF f;        // split-precision kernels only
 };
 
@@ -98,7 +99,7 @@ struct Bufs {
 };
 
 enum KernelId { K_INNER = 0, K_FINAL = 1, K_LIMIT = 2, K_A0 = 3, K_MARGINS = 4, K_AVG = 5, K_TROUBLE = 6,
-                K_FEATURES = 7, K_COMBINE = 8 };
+                K_FEATURES = 7 };
 
 // Buffers of the split-precision path: FP64 cell averages plus FP32 nodal
 // deviations (the polynomial is ubar + (dev - mean_w dev)).
@@ -117,6 +118,57 @@ struct MixBufs {
 };
 
 enum MixKernelId { KX_SPLIT = 0, KX_MERGE = 1, KX_LIMIT = 2, KX_INNER = 3, KX_FINAL = 4, KX_SCAN = 5, KX_AVG = 6 };
+
+// ---------------------------------------------------------------- ensembles (2D Euler)
+
+// Scalars of one problem's current attempt.
+struct EnsScal {
+    int flag;                 // a stage average left B^eps
+    int pad;
+    unsigned long long nlim;  // limited cells
+    unsigned long long thmin; // bits of the smallest theta
+    unsigned long long a0;    // bits of the rate of the new state
+    unsigned long long ord[2];
+    unsigned long long ntrb;  // troubled cells
+};
+
+// Descriptor of one problem of an ensemble (device table, one per problem).
+struct EnsProblem {
+    Params P;                // its parameters; P.dt is the step of the current attempt
+    double *u[2];            // u[cur] holds u^n, u[cur ^ 1] receives u^{n+1}
+    double *ustar, *tr, *aux;
+    int *tflags;
+    float *feat;
+    const float *prob;
+    EnsScal *sc;
+    int n;                   // k + 1
+    int cur;
+    int pending;             // takes part in the current attempt
+    int done;                // reached t_end
+    int status;              // 0, or CRKDG_E_BOUNDS after max_halvings
+    int restarts;            // halvings of the current step
+    int klass;               // (n - 3) * 3 + size class, for tuning
+    int pad;
+    double t, t_end, cfl, a0;
+    long long steps, restarts_total;
+    // the last accepted step
+    double last_dt, last_thmin;
+    long long last_nlim, last_ntrb;
+    int last_restarts, pad2;
+};
+
+// Work item: blocks [blk, blk + nblk) of problem prob.
+struct EnsItem {
+    int prob, blk, nblk, pad;
+};
+
+enum { ENS_COUNTERS = 16 };
+enum EnsKernelKind { ENS_INNER = 0, ENS_FINAL = 1, ENS_TROUBLE = 2, ENS_FEATURES = 3 };
+struct EnsCtl {
+    unsigned int counter[ENS_COUNTERS];  // one work counter per persistent launch of an attempt
+    int any_pending;
+    int pad[3];
+};
 
 // Scalars of one attempt of the device-resident step loop (three rotate).
 struct RunSlot {
@@ -159,6 +211,16 @@ cudaError_t crkdg_launch_mx_1d(int kernel, int n, int phys, int nblocks, cudaStr
                                const crkdg::Params &P, const crkdg::MixBufs &B);
 cudaError_t crkdg_launch_mx_2d(int kernel, int n, int phys, int nblocks, cudaStream_t st,
                                const crkdg::Params &P, const crkdg::MixBufs &B);
+// Ensembles of 2D Euler problems (defined in dg_ens.cu).
+cudaError_t crkdg_upload_tables_ens(const crkdg::NodalTables *t);
+cudaError_t crkdg_ens_launch(int kind, int n, int grid, cudaStream_t st, crkdg::EnsProblem *E,
+                             const crkdg::EnsItem *items, int nitems, crkdg::EnsCtl *ctl, int counter, int stage);
+int crkdg_ens_occupancy(int kind, int n);
+int crkdg_ens_cells_per_block(int kind, int n);
+// which: 0 open a step (arg: size class or -1), 1 clear the counters, 2 close an attempt (arg: max_halvings)
+cudaError_t crkdg_ens_control(int which, cudaStream_t st, crkdg::EnsProblem *E, int np, crkdg::EnsCtl *ctl, int arg);
+// Closed-form nodal tables for n = 2, 3, 4 (defined in crkdg_api.cu).
+void crkdg_build_tables(crkdg::NodalTables *tab);
 // Persistent 1D step loop (cooperative launch); *nblocks receives the grid used.
 cudaError_t crkdg_run_1d(int n, int phys, cudaStream_t st, const crkdg::Params &P, double *u0, double *u1,
                          crkdg::RunCtl *ctl, int *nblocks);

@@ -167,7 +167,7 @@ def riemann_states(seed):
     return st
 
 
-def riemann_quadrants(seed, n=1024, k=2, cfl=0.178, t_end=0.2, gamma=GAMMA):
+def riemann_quadrants(seed, n=1024, k=2, cfl=None, t_end=0.2, gamma=GAMMA):
     dom = (0.0, 1.0, 0.0, 1.0)
     X, Y = node_coords(2, n, n, k, dom)
     st = riemann_states(seed)
@@ -177,9 +177,31 @@ def riemann_quadrants(seed, n=1024, k=2, cfl=0.178, t_end=0.2, gamma=GAMMA):
     wy = np.choose(q, [s[2] for s in st])
     p = np.choose(q, [s[3] for s in st])
     U = prim_to_cons(rho, (wx, wy), p, gamma)
+    if cfl is None:  # the paper's CFL numbers for 3- and 4-stage schemes
+        cfl = 0.178 if k != 3 else 0.103
     return Workload(f"riemann2d_seed{seed}", 2, n, n, k, dom, "euler", ("outflow",) * 4,
                     np.ascontiguousarray(U), gamma=gamma, eps=1e-13, cfl=cfl, t_end=t_end,
                     tableau="rk4" if k == 3 else "heun3")
+
+
+def riemann_quadrants_device(seed, n, k, device="cuda", gamma=GAMMA):
+    """The initial state of riemann_quadrants(seed, n, k) built directly on the device (torch,
+    FP64): node coordinates by the same formulas, then each quadrant's conservative state.
+    Equal to the host array element for element."""
+    import torch
+
+    xg, _ = gauss_nodes(k)
+    st = riemann_states(seed)
+    cons = prim_to_cons(np.array([s[0] for s in st]), (np.array([s[1] for s in st]), np.array([s[2] for s in st])),
+                        np.array([s[3] for s in st]), gamma)  # [4 comps][4 quadrants]
+    h = 1.0 / n
+    c = 0.0 + (torch.arange(n, device=device, dtype=torch.float64) + 0.5) * h
+    off = (0.5 * h) * torch.as_tensor(xg, device=device, dtype=torch.float64)
+    X = c[None, :, None, None] + off[None, None, None, :]  # [1, nx, 1, n_x]
+    Y = c[:, None, None, None] + off[None, None, :, None]  # [ny, 1, n_y, 1]
+    q = (X >= 0.5).to(torch.int64) + 2 * (Y >= 0.5).to(torch.int64)  # [ny, nx, n_y, n_x]
+    table = torch.as_tensor(cons, device=device, dtype=torch.float64)  # [4, 4]
+    return table[:, q].contiguous()
 
 
 def _zero_mean(rng, shape_cells, k, dim):
