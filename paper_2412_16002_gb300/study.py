@@ -46,8 +46,16 @@ def _solver(variant, seed, n, tvb_M, mlp):
     return g, wl
 
 
+class RunFailed(RuntimeError):
+    pass
+
+
 def run(variant, seed, n, t_end, tvb_M=10.0, mlp=None):
-    """Advance one variant to t_end; returns (cell averages [n][n][4], device ms, wall s, steps, troubled)."""
+    """Advance one variant to t_end; returns (cell averages [n][n][4], device ms, wall s, steps, troubled).
+    Raises RunFailed (with the step, time, trial step and the bound margins before it) if a step
+    cannot restore the bounds."""
+    from ._lib import CrkdgError
+
     g, wl = _solver(variant, seed, n, tvb_M, mlp)
     g.set_profiling(True)
     t = 0.0
@@ -55,7 +63,13 @@ def run(variant, seed, n, t_end, tvb_M=10.0, mlp=None):
     t0 = time.perf_counter()
     while t < t_end:
         dt = min(g.max_dt(wl.cfl), t_end - t)
-        info = g.step(dt, wl.tableau)
+        if t + dt == t:  # the remaining interval is below the resolution of t
+            break
+        try:
+            info = g.step(dt, wl.tableau)
+        except CrkdgError as err:
+            raise RunFailed(f"{variant} n={n} step {steps} t={t!r} dt={dt!r} margins={g.margins().tolist()} "
+                            f"averages min={g.averages().min(axis=(0, 1)).tolist()}: {err}") from err
         t += info["dt_taken"]
         steps += 1
         troubled += info["troubled"]
@@ -100,16 +114,20 @@ def study(seed=7, sizes=(64, 128, 256), ref_factor=2, t_end=0.1, tvb_M=10.0, var
     for v in variants:
         rows = []
         for n in sizes:
-            avg, ms, wall, steps, troubled = run(v, seed, n, t_end, tvb_M, mlp)
+            try:
+                avg, ms, wall, steps, troubled = run(v, seed, n, t_end, tvb_M, mlp)
+            except RunFailed as err:
+                rows.append({"n": n, "failed": str(err)})
+                continue
             err = l1_error(avg, restrict(ref, ref_n // n))
             rows.append({"n": n, "l1": err, "ms": ms, "wall_s": wall, "steps": steps, "troubled": troubled})
         out["variants"][v] = rows
     base = out["variants"]["fp64"]
     matched = {}
     for v, rows in out["variants"].items():
-        curve = [(r["l1"], r["ms"]) for r in rows]
+        curve = [(r["l1"], r["ms"]) for r in rows if "l1" in r]
         matched[v] = []
-        for b in base:  # at the plain method's errors: time of this variant / time of fp64
+        for b in (r for r in base if "l1" in r):  # at the plain method's errors: time / time of fp64
             t = matched_time(curve, b["l1"])
             matched[v].append({"l1": b["l1"], "ms": t, "speedup_vs_fp64": (b["ms"] / t) if t else None})
     out["matched"] = matched
