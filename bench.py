@@ -31,6 +31,8 @@ sys.path.insert(0, ROOT)
 # FP64 peak of the GB300 derived from the unit count and clock: 152 SMs x 4 FP64
 # flop per clock (two DFMA per clock per SM, the 1.25 TFLOP/s class rate) x 2070 MHz.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+# FP32 (non-tensor) peak from the same unit count: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 WORKLOADS = {
     "euler1d_blast_tube_4096_p2": dict(kind="euler1d", nx=4096, k=2),
@@ -159,6 +161,21 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def job_rate(local_ms, units_per_rank, world, device=None):
+    """Whole-job throughput of N independent replicas: every rank advanced units_per_rank
+    units in local_ms; the job's time is the maximum over ranks (all_reduce MAX when
+    world > 1).  Returns (units/s of the whole job, the maximum ms)."""
+    import torch
+
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return units_per_rank * world / (ms / 1e3), ms
 
 
 def read_traffic(kernel, workload):
@@ -317,12 +334,7 @@ def run_gb300(args, wl, name):
     clocks = sampler.stop() if sampler else None
     kt, kn = g.kernel_times()
     g.set_profiling(False)
-    tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    ms_max = float(tt.item())
-    units = wl.cells * wl.dofs_per_cell * TAB_S[wl.tableau] * args.steps * world
-    value = units / (ms_max / 1e3)
+    value, ms_max = job_rate(ms, wl.cells * wl.dofs_per_cell * TAB_S[wl.tableau] * args.steps, world, dev)
 
     # end to end through the C ABI with host buffers: H2D of the state, one step, D2H
     host_in = torch.from_numpy(g.get_state().reshape(-1).copy()).pin_memory()
@@ -341,23 +353,25 @@ def run_gb300(args, wl, name):
         host_in.copy_(host_out)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = wl.cells * wl.dofs_per_cell * TAB_S[wl.tableau] * e2e_steps * world / float(e2e_t.item())
+    e2e_value, _ = job_rate(1e3 * e2e_s, wl.cells * wl.dofs_per_cell * TAB_S[wl.tableau] * e2e_steps, world, dev)
 
     if rank == 0:
         inner_f, final_f = algorithmic_flops(wl)
         avg_inner = kt["inner"] / max(kn["inner"], 1)
         avg_final = kt["final"] / max(kn["final"], 1)
+        sfx = "_x" if precision == "mixed" else ""
         if kn["run"] > 0:
             avg_run = kt["run"] / kn["run"]
             dom, avg_ms, fl = "k_run1d", avg_run, (inner_f + final_f) * args.steps
         elif avg_inner >= avg_final:
-            dom, avg_ms, fl = "k_inner", avg_inner, inner_f
+            dom, avg_ms, fl = "k_inner" + sfx, avg_inner, inner_f
         else:
-            dom, avg_ms, fl = "k_final", avg_final, final_f
+            dom, avg_ms, fl = "k_final" + sfx, avg_final, final_f
         achieved = fl * wl.cells / (avg_ms / 1e3) / 1e12
+        # the split path runs its operators in FP32: its roofline is the FP32 peak
+        peak = FP32_PEAK_TFLOPS if precision == "mixed" else FP64_PEAK_TFLOPS
+        peak_src = ("FP32 derived from unit count and clock (152 SMs x 128 lanes x 2 x 2070 MHz)" if precision == "mixed"
+                    else "FP64 derived from unit count and clock (152 SMs x 4 flop/clk x 2070 MHz)")
         line = {
             "metric": "cell-DOF updates/s per RK stage",
             "value": value,
@@ -376,10 +390,10 @@ def run_gb300(args, wl, name):
                        "tableau": wl.tableau, "stages": TAB_S[wl.tableau], "cfl": wl.cfl,
                        "l2": l2_note, "parallelism": f"replicas{world}",
                        "restarts_in_timed_steps": restarts, "t_after": t},
-            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": read_traffic(dom, name),
-                         "peak_source": "FP64 derived from unit count and clock (152 SMs x 4 flop/clk x 2070 MHz)",
+                         "peak_source": peak_src,
                          "avg_launch_ms": {"k_inner": avg_inner, "k_final": avg_final,
                                            "k_run1d": kt["run"] / max(kn["run"], 1)},
                          "flops_per_cell": {"k_inner": inner_f, "k_final": final_f}},
@@ -476,11 +490,7 @@ def run_ensemble(args, name):
     ms, nst = ens.times()
     ens.set_profiling(False)
     clocks = sampler.stop() if sampler else None
-    tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    ms_max = float(tt.item())
-    value = units_step * args.steps * world / (ms_max / 1e3)
+    value, ms_max = job_rate(ms, units_step * args.steps, world, dev)
     troubled = sum(ens.info(i)["troubled"] for i in range(len(specs)))
     restarts = sum(ens.info(i)["restarts"] for i in range(len(specs)))
 
@@ -499,7 +509,7 @@ def run_ensemble(args, name):
     for i in range(len(specs)):
         ens.get_state(i, hosts[i].numpy())
     e2e_s = time.perf_counter() - t0
-    e2e_value = units_step * args.steps * world / e2e_s
+    e2e_value, _ = job_rate(1e3 * e2e_s, units_step * args.steps, world, dev)
     del hosts
     if rank == 0:
         achieved = flops_step * args.steps / (ms_max / 1e3) / 1e12
