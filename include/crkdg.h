@@ -65,7 +65,11 @@ enum { CRKDG_IND_OFF = 0, CRKDG_IND_TVB = 1, CRKDG_IND_MLP = 2 };
  * bc[s] for the sides s = 0 left, 1 right, 2 bottom, 3 top; a periodic side
  * must be paired with a periodic opposite side.  bc_state[s] holds the
  * conservative exterior state of a Dirichlet side.  Boundary data enter only
- * the final stage (compactness, Sec. 1 and the Compactness remark of Sec. 3.2). */
+ * the final stage (compactness, Sec. 1 and the Compactness remark of Sec. 3.2):
+ * the exterior trace at a face point is the Dirichlet state, the interior trace
+ * with the normal momentum negated (reflect), or the cell average of the same
+ * stage value (outflow; a constant state is kept exactly and the Lax--Friedrichs
+ * flux keeps its dissipation on outflow faces). */
 typedef struct {
     int dim;
     int nx, ny;
@@ -345,12 +349,13 @@ const char *crkdg_ensemble_last_error(crkdg_ens_t e);
  * CRKDG_OP_F, ...) returns for the same mesh, k and flux.  in_dev and out_dev
  * are caller-owned device arrays in the state layout; they may not alias.
  *
- * Scratch: the interior-trace accumulation and the face traces live in one
- * library-owned static device array of CRKDG_NOALLOC_SCRATCH_DOUBLES doubles
- * (32 MiB), which every GPU that loads the library keeps until the process
- * exits.  A mesh needing more than m * cells * (n^dim + 2*dim*n^(dim-1))
- * doubles beyond that limit is rejected with CRKDG_E_ARG (e.g. 2D Euler Q^3
- * fits up to 32768 cells, 1D Euler P^2 up to 279620 cells).  Every word of the
+ * Scratch: the interior-trace accumulation, the face traces and the cell
+ * averages live in one library-owned static device array of
+ * CRKDG_NOALLOC_SCRATCH_DOUBLES doubles (32 MiB), which every GPU that loads
+ * the library keeps until the process exits.  A mesh needing more than
+ * m * cells * (n^dim + 2*dim*n^(dim-1) + 1) doubles beyond that limit is
+ * rejected with CRKDG_E_ARG (e.g. 2D Euler Q^3 fits up to 31775 cells, 1D
+ * Euler P^2 up to 233016 cells).  Every word of the
  * scratch that a call reads is written earlier in the same call, so nothing
  * needs clearing; the array keeps the last call's contents.  All calls share
  * the one array: calls whose kernels overlap on the GPU (on different streams

@@ -349,8 +349,11 @@ static int neighbour(const orc_problem *P, int cell, int s) {
     }
 }
 
-static void exterior_state(const orc_problem *P, int s, const double *uin, double x, double y,
-                           double t, double *uex) {
+/* Exterior state on boundary side s: uin is the interior trace, avg the cell average of
+ * the same polynomial.  Outflow takes the cell average (the Lax--Friedrichs flux keeps
+ * its dissipation on outflow faces; a constant state is kept exactly). */
+static void exterior_state(const orc_problem *P, int s, const double *uin, const double *avg, double x,
+                           double y, double t, double *uex) {
     int m = P->m;
     switch (P->bc[s]) {
     case ORC_BC_DIRICHLET:
@@ -364,7 +367,7 @@ static void exterior_state(const orc_problem *P, int s, const double *uin, doubl
         if (P->flux == ORC_FLUX_EULER) uex[1 + s / 2] = -uin[1 + s / 2];
         break;
     default: /* outflow */
-        for (int c = 0; c < m; ++c) uex[c] = uin[c];
+        for (int c = 0; c < m; ++c) uex[c] = avg[c];
     }
 }
 
@@ -445,7 +448,9 @@ void orc_apply(const orc_problem *P, int op, const double *in, double *out, doub
                     } else {
                         double x = P->x0 + (cx + 0.5 * (xi + 1.0)) * hx;
                         double y = P->y0 + (cy + 0.5 * (eta + 1.0)) * hy;
-                        exterior_state(P, s, ui, x, y, t, ue);
+                        double av[ORC_MAXM];
+                        for (int c = 0; c < m; ++c) av[c] = cell_coef(P, in, cell, c)[0];
+                        exterior_state(P, s, ui, av, x, y, t, ue);
                     }
                     for (int c = 0; c < m; ++c) {
                         uL[q][c] = (s % 2) ? ui[c] : ue[c];
@@ -716,7 +721,7 @@ static void neighbour_average(const orc_problem *P, const double *c, int cell, i
     }
     double own[ORC_MAXM];
     for (int comp = 0; comp < m; ++comp) own[comp] = cell_coef(P, c, cell, comp)[0];
-    exterior_state(P, s, own, 0.0, 0.0, 0.0, ub);
+    exterior_state(P, s, own, own, 0.0, 0.0, 0.0, ub);
 }
 
 long long orc_troubled_cells(const orc_problem *P, const double *c, int *flags) {

@@ -212,6 +212,7 @@ Bufs base_bufs(const crkdg_ctx *h) {
     B.ustar = h->ustar;
     B.unew = h->unew;
     B.tr = h->tr;
+    B.tavg = h->tr ? h->tr + (size_t)h->tr_slots * h->m * h->ncell * h->ntr : nullptr;
     B.flag = &h->scal->flag;
     B.nlim = &h->scal->nlim;
     B.thmin = &h->scal->thmin;
@@ -241,6 +242,7 @@ MixBufs base_xbufs(const crkdg_ctx *h) {
     X.ub_n = h->xub[1 - h->xcur];
     X.dv_n = h->xdv[1 - h->xcur];
     X.tr = h->xtr;
+    X.tavg = h->xtr ? h->xtr + (size_t)h->xtr_slots * h->m * h->ncell * h->ntr : nullptr;
     X.flag = &h->scal->flag;
     X.nlim = &h->scal->nlim;
     X.thmin = &h->scal->thmin;
@@ -296,7 +298,8 @@ crkdg_status ensure_traces(crkdg_ctx *h, int slots) {
     if (h->tr) cudaFree(h->tr);
     h->tr = nullptr;
     h->tr_slots = 0;
-    size_t bytes = (size_t)slots * h->m * h->ncell * h->ntr * sizeof(double);
+    // traces [slot][m][cell][face point], then the traced stages' cell averages [slot][m][cell]
+    size_t bytes = (size_t)slots * h->m * h->ncell * (h->ntr + 1) * sizeof(double);
     CK(h, cudaMalloc(&h->tr, bytes));
     h->tr_slots = slots;
     return CRKDG_OK;
@@ -307,7 +310,7 @@ crkdg_status ensure_traces_x(crkdg_ctx *h, int slots) {
     if (h->xtr) cudaFree(h->xtr);
     h->xtr = nullptr;
     h->xtr_slots = 0;
-    CK(h, cudaMalloc(&h->xtr, (size_t)slots * h->m * h->ncell * h->ntr * sizeof(float)));
+    CK(h, cudaMalloc(&h->xtr, (size_t)slots * h->m * h->ncell * (h->ntr + 1) * sizeof(float)));
     h->xtr_slots = slots;
     return CRKDG_OK;
 }

@@ -48,7 +48,7 @@ struct crkdg_ensemble_ctx {
     int *hpend = nullptr;  // pinned
     // arenas
     double *arena_u[2] = {nullptr, nullptr};
-    double *arena_ustar = nullptr, *arena_tr = nullptr, *arena_aux = nullptr;
+    double *arena_ustar = nullptr, *arena_tr = nullptr, *arena_tavg = nullptr, *arena_aux = nullptr;
     int *arena_flags = nullptr;
     float *arena_feat = nullptr, *arena_prob = nullptr, *mlp = nullptr;
     long long total_cells = 0;
@@ -215,6 +215,7 @@ Bufs single_bufs(const EnsProblem &p) {
     B.unew = p.u[p.cur ^ 1];
     B.ustar = p.ustar;
     B.tr = p.tr;
+    B.tavg = p.tavg;
     B.flag = &p.sc->flag;
     B.nlim = &p.sc->nlim;
     B.thmin = &p.sc->thmin;
@@ -273,7 +274,7 @@ void release(crkdg_ens_t e) {
     for (int g = 0; g < 2; ++g)
         for (int k = 0; k < 2; ++k)
             if (e->ditems[g][k]) cudaFree(e->ditems[g][k]);
-    for (double *p : {e->arena_u[0], e->arena_u[1], e->arena_ustar, e->arena_tr, e->arena_aux})
+    for (double *p : {e->arena_u[0], e->arena_u[1], e->arena_ustar, e->arena_tr, e->arena_tavg, e->arena_aux})
         if (p) cudaFree(p);
     if (e->arena_flags) cudaFree(e->arena_flags);
     if (e->arena_feat) cudaFree(e->arena_feat);
@@ -363,9 +364,9 @@ crkdg_status crkdg_ensemble_create(int count, const crkdg_ens_problem *problems,
 
     // sizes and arena offsets (slices aligned to 32 doubles)
     const bool ind = e->opt.indicator != CRKDG_IND_OFF;
-    std::vector<size_t> off_u(count), off_tr(count), off_aux(count);
+    std::vector<size_t> off_u(count), off_tr(count), off_tavg(count), off_aux(count);
     std::vector<long long> off_cell(count);
-    size_t tot_u = 0, tot_tr = 0, tot_aux = 0;
+    size_t tot_u = 0, tot_tr = 0, tot_tavg = 0, tot_aux = 0;
     long long tot_cells = 0;
     for (int i = 0; i < count; ++i) {
         const int n = problems[i].k + 1;
@@ -376,6 +377,8 @@ crkdg_status crkdg_ensemble_create(int count, const crkdg_ens_problem *problems,
         tot_u += align_up((size_t)4 * nc * n * n, 32);
         off_tr[i] = tot_tr;
         tot_tr += align_up((size_t)std::max(ns, 1) * 4 * nc * 4 * n, 32);
+        off_tavg[i] = tot_tavg;
+        tot_tavg += align_up((size_t)std::max(ns, 1) * 4 * nc, 32);
         off_aux[i] = tot_aux;
         tot_aux += align_up((size_t)4 * nc, 32);
         off_cell[i] = tot_cells;
@@ -385,6 +388,7 @@ crkdg_status crkdg_ensemble_create(int count, const crkdg_ens_problem *problems,
     auto alloc = [&](void **p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 256)) == cudaSuccess; };
     bool ok = alloc((void **)&e->arena_u[0], tot_u * 8) && alloc((void **)&e->arena_u[1], tot_u * 8) &&
               alloc((void **)&e->arena_ustar, tot_u * 8) && alloc((void **)&e->arena_tr, tot_tr * 8) &&
+              alloc((void **)&e->arena_tavg, tot_tavg * 8) &&
               alloc((void **)&e->arena_aux, tot_aux * 8) && alloc((void **)&e->dsc, sizeof(EnsScal) * count) &&
               alloc((void **)&e->dctl, sizeof(EnsCtl)) && alloc((void **)&e->dprob, sizeof(EnsProblem) * count);
     if (ok && ind) ok = alloc((void **)&e->arena_flags, sizeof(int) * (size_t)tot_cells);
@@ -442,6 +446,7 @@ crkdg_status crkdg_ensemble_create(int count, const crkdg_ens_problem *problems,
         p.u[1] = e->arena_u[1] + off_u[i];
         p.ustar = e->arena_ustar + off_u[i];
         p.tr = e->arena_tr + off_tr[i];
+        p.tavg = e->arena_tavg + off_tavg[i];
         p.aux = e->arena_aux + off_aux[i];
         p.tflags = ind ? e->arena_flags + off_cell[i] : nullptr;
         p.feat = ind ? e->arena_feat + (size_t)off_cell[i] * CRKDG_MLP_NIN : nullptr;

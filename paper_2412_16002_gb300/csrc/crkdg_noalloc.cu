@@ -147,8 +147,8 @@ extern "C" crkdg_status crkdg_apply_F_noalloc(const crkdg_mesh *mesh, int k, int
     int nn = mesh->dim == 2 ? n * n : n;
     int ntr = mesh->dim == 2 ? 4 * n : 2;
     double cells = (double)mesh->nx * ny;
-    // scratch: the accumulated G (state size) followed by one slot of face traces
-    double need = cells * nn * m + cells * ntr * m;
+    // scratch: the accumulated G (state size), one slot of face traces, the cell averages
+    double need = cells * nn * m + cells * ntr * m + cells * m;
     if (need > (double)CRKDG_NOALLOC_SCRATCH_DOUBLES) return CRKDG_E_ARG;  // beyond the fixed scratch size
     int ncell = mesh->nx * ny;
 
@@ -184,6 +184,7 @@ extern "C" crkdg_status crkdg_apply_F_noalloc(const crkdg_mesh *mesh, int k, int
     B.un = in_dev;
     B.ustar = scratch;                              // G(in), fully written by the inner kernel
     B.tr = scratch + (size_t)ncell * nn * m;        // traces of in, fully written before they are read
+    B.tavg = B.tr + (size_t)ncell * ntr * m;        // cell averages of in, likewise
     B.unew = out_dev;
 
     cudaStream_t st = (cudaStream_t)cuda_stream;

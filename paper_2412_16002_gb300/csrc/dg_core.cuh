@@ -158,6 +158,22 @@ __device__ __forceinline__ void boundary_state(const Params &P, int side, const 
     }
 }
 
+// Exterior trace of a boundary face point in the final stage: Dirichlet the side's
+// state, reflect the interior trace with the normal momentum negated, outflow the
+// cell average of the same stage value (avg; a constant state is kept exactly, and
+// the Lax--Friedrichs flux keeps its dissipation on outflow faces).
+template <int PHYS, int DIM>
+__device__ __forceinline__ void exterior_state(const Params &P, int side, const double *ui, const double *avg,
+                                               double *ue) {
+    constexpr int M = ncomp(PHYS, DIM);
+    if (P.bc[side] == BC_OUTFLOW) {
+#pragma unroll
+        for (int c = 0; c < M; ++c) ue[c] = avg[c];
+    } else {
+        boundary_state<PHYS, DIM>(P, side, ui, ue);
+    }
+}
+
 // neighbour across side (0 L, 1 R, 2 B, 3 T), or -1 on a non-periodic boundary
 __device__ __forceinline__ int neighbour(const Params &P, int cell, int side) {
     int cx = cell % P.nx, cy = cell / P.nx;
@@ -549,6 +565,16 @@ __device__ __forceinline__ void inner_body(const Params &P, const Bufs &B, int b
         }
         double trs[FPT][M];
         eval_G(P, S, lc, node, cur, gh[i], trs);
+        if (P.slot[i] >= 0) {  // cell average of the traced stage value (outflow exterior state)
+            const NodalTables &T = c_tab[N - 2];
+            for (int c = node; c < M; c += NN) {
+                double s = 0.0;
+#pragma unroll
+                for (int q = 0; q < NN; ++q) s = fma(DIM == 2 ? T.w2[q] : T.w1[q], S.u[lc][c][q], s);
+                if (active) B.tavg[((size_t)P.slot[i] * M + c) * P.ncell + cell] = s;
+            }
+            __syncthreads();
+        }
         if (P.mode == MODE_OP_G) {
 #pragma unroll
             for (int c = 0; c < M; ++c) acc[c] = gh[i][c];
@@ -617,7 +643,10 @@ __device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int b
 #pragma unroll
                     for (int c = 0; c < M; ++c) ue[c] = tr[((size_t)c * P.ncell + nb) * NTR + ofp];
                 } else {
-                    boundary_state<PHYS, DIM>(P, face, ui, ue);
+                    double av[M];
+#pragma unroll
+                    for (int c = 0; c < M; ++c) av[c] = B.tavg[((size_t)P.slot[i] * M + c) * P.ncell + cell];
+                    exterior_state<PHYS, DIM>(P, face, ui, av, ue);
                 }
                 bool upper = face & 1;  // R or T: the cell is on the lower side of the face
 #pragma unroll

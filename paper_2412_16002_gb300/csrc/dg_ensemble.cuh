@@ -22,6 +22,7 @@ __device__ __forceinline__ void ens_bufs(const EnsProblem &E, Bufs &B) {
     B.unew = E.u[E.cur ^ 1];
     B.ustar = E.ustar;
     B.tr = E.tr;
+    B.tavg = E.tavg;
     B.flag = &E.sc->flag;
     B.nlim = &E.sc->nlim;
     B.thmin = &E.sc->thmin;

@@ -106,6 +106,20 @@ __device__ __forceinline__ void boundary_state_f(const Params &P, int side, cons
     }
 }
 
+// Exterior trace of a boundary face point (FP32): outflow takes the cell average of
+// the same stage value, the other conditions as boundary_state_f.
+template <int PHYS, int DIM>
+__device__ __forceinline__ void exterior_state_f(const Params &P, int side, const float *ui, const float *avg,
+                                                 float *ue) {
+    constexpr int M = ncomp(PHYS, DIM);
+    if (P.bc[side] == BC_OUTFLOW) {
+#pragma unroll
+        for (int c = 0; c < M; ++c) ue[c] = avg[c];
+    } else {
+        boundary_state_f<PHYS, DIM>(P, side, ui, ue);
+    }
+}
+
 // ----------------------------------------------------------------------------- block storage
 
 template <class C>
@@ -515,6 +529,7 @@ __device__ void limit_x(const Params &P, const Bufs &B, SmemX<C> &S, int lc, int
 template <class C>
 __device__ __forceinline__ Bufs scal_of(const MixBufs &X) {
     Bufs B;
+    memset(&B, 0, sizeof(B));
     B.un = nullptr;
     B.ustar = nullptr;
     B.unew = nullptr;
@@ -621,6 +636,7 @@ __global__ void __launch_bounds__(C::NT) k_inner_x(Params P, MixBufs X) {
             for (int c = 0; c < M; ++c) dacc[c] = fmaf(P.f.dtb[i], gd[i][c], dacc[c]);
         }
         if (P.slot[i] >= 0 && active) {
+            for (int c = node; c < M; c += NN) X.tavg[((size_t)P.slot[i] * M + c) * P.ncell + cell] = S.ubf[lc][c];
             float *dst = X.tr + (size_t)P.slot[i] * M * P.ncell * NTR;
 #pragma unroll
             for (int j = 0; j < FPT; ++j) {
@@ -683,7 +699,10 @@ __global__ void __launch_bounds__(C::NT) k_final_x(Params P, MixBufs X) {
 #pragma unroll
                     for (int c = 0; c < M; ++c) ue[c] = tr[((size_t)c * P.ncell + nb) * NTR + ofp];
                 } else {
-                    boundary_state_f<PHYS, DIM>(P, face, ui, ue);
+                    float av[M];
+#pragma unroll
+                    for (int c = 0; c < M; ++c) av[c] = X.tavg[((size_t)P.slot[i] * M + c) * P.ncell + cell];
+                    exterior_state_f<PHYS, DIM>(P, face, ui, av, ue);
                 }
                 bool upper = face & 1;
 #pragma unroll

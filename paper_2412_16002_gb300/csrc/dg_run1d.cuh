@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(RunCfg1D<N, PHYS, NCBV>::NT) k_run1d(Params P,
     constexpr int COWN = C::NCB - 2;
     __shared__ Smem<C> S;
     __shared__ double sTr[MAXS][C::NCB][2][M];
+    __shared__ double sAv[MAXS][C::NCB][M];  // cell averages of the traced stage values
     const NodalTables &T = c_tab[N - 2];
     const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
     const int a = node;
@@ -139,6 +140,15 @@ __global__ void __launch_bounds__(RunCfg1D<N, PHYS, NCBV>::NT) k_run1d(Params P,
 #pragma unroll
                     for (int c = 0; c < M; ++c) sTr[P.slot[i]][lc][node][c] = trs[0][c];
                 }
+                if (P.slot[i] >= 0) {  // S.u holds the stage values until the next stage's limiter
+                    for (int c = node; c < M; c += NN) {
+                        double s = 0.0;
+#pragma unroll
+                        for (int q = 0; q < NN; ++q) s = fma(T.w1[q], S.u[lc][c][q], s);
+                        sAv[P.slot[i]][lc][c] = s;
+                    }
+                    __syncthreads();
+                }
             }
             __syncthreads();
             // final stage: Lax--Friedrichs correction of the own cells from the chunk's traces
@@ -160,7 +170,7 @@ __global__ void __launch_bounds__(RunCfg1D<N, PHYS, NCBV>::NT) k_run1d(Params P,
 #pragma unroll
                         for (int c = 0; c < M; ++c) ue[c] = sTr[q][nl][face ^ 1][c];
                     } else {
-                        boundary_state<PHYS, 1>(P, face, ui, ue);
+                        exterior_state<PHYS, 1>(P, face, ui, sAv[q][lc], ue);
                     }
 #pragma unroll
                     for (int c = 0; c < M; ++c) {

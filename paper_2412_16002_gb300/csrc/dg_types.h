@@ -86,6 +86,7 @@ struct Bufs {
     double *ustar;      // u^n + dt sum_i b_i G(u~^(i))   (or G(u) in MODE_OP_G)
     double *unew;       // u^{n+1}
     double *tr;         // face traces of u~^(i): [slot][m][cell][face point]
+    double *tavg;       // cell averages of the same u~^(i): [slot][m][cell] (outflow exterior state)
     int *flag;          // set when a stage average leaves B
     unsigned long long *nlim;   // limited cells
     unsigned long long *thmin;  // bits of the smallest theta (non-negative double)
@@ -110,6 +111,7 @@ struct MixBufs {
     double *ub_n;       // averages of u^{n+1}
     float *dv_n;        // deviations of u^{n+1}
     float *tr;          // FP32 face traces           [slot][m][cell][face point]
+    float *tavg;        // FP32 cell averages of the traced stages [slot][m][cell]
     const double *nod_in;  // FP64 nodal input (split, operators)
     double *nod_out;       // FP64 nodal output (merge, operators)
     int *flag;
@@ -136,7 +138,7 @@ struct EnsScal {
 struct EnsProblem {
     Params P;                // its parameters; P.dt is the step of the current attempt
     double *u[2];            // u[cur] holds u^n, u[cur ^ 1] receives u^{n+1}
-    double *ustar, *tr, *aux;
+    double *ustar, *tr, *tavg, *aux;
     int *tflags;
     float *feat;
     const float *prob;
