@@ -226,7 +226,16 @@ Bufs base_bufs(const crkdg_ctx *h) {
     return B;
 }
 
+// Stages with a trace slot write their traces and cell averages (inner kernel) and the
+// final kernel reads them: refuse a launch whose buffers are missing.
+bool slots_ok(const Params &P, const void *tr, const void *tavg) {
+    for (int i = 0; i < P.s && i < MAXS; ++i)
+        if (P.slot[i] >= 0 && (!tr || !tavg)) return false;
+    return true;
+}
+
 cudaError_t launch(crkdg_ctx *h, int kernel, const Params &P, const Bufs &B) {
+    if ((kernel == K_INNER || kernel == K_FINAL) && !slots_ok(P, B.tr, B.tavg)) return cudaErrorInvalidValue;
     int ncb = cells_per_block(h->dim, h->n);
     int nblocks = (h->ncell + ncb - 1) / ncb;
     if (h->dim == 1) return crkdg_launch_1d(kernel, h->n, h->phys, nblocks, h->st, P, B);
@@ -274,6 +283,7 @@ void fill_f32(Params &P) {
 }
 
 cudaError_t launch_x(crkdg_ctx *h, int kernel, const Params &P0, const MixBufs &X) {
+    if ((kernel == KX_INNER || kernel == KX_FINAL) && !slots_ok(P0, X.tr, X.tavg)) return cudaErrorInvalidValue;
     Params P = P0;
     fill_f32(P);
     int ncb = cells_per_block(h->dim, h->n);
@@ -860,7 +870,7 @@ crkdg_status crkdg_apply_operator(crkdg_t h, int op, const double *in_dev, doubl
         } else if (op == CRKDG_OP_F) {
             crkdg_status s = ensure_traces(h, 1);
             if (s) return s;
-            B.tr = h->tr;
+            B = base_bufs(h);  // the trace buffer (and its stage averages) may be new
             P.slot[0] = 0;
             P.nslot = 1;
             P.mode = MODE_OP_G;

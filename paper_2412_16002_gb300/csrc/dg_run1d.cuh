@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(RunCfg1D<N, PHYS, NCBV>::NT) k_run1d(Params P,
     __shared__ Smem<C> S;
     __shared__ double sTr[MAXS][C::NCB][2][M];
     __shared__ double sAv[MAXS][C::NCB][M];  // cell averages of the traced stage values
+    __shared__ double sFc[MAXS][C::NCB][2][M];  // per face: fhat - f(u_L), fhat - f(u_R)
     const NodalTables &T = c_tab[N - 2];
     const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
     const int a = node;
@@ -151,31 +152,36 @@ __global__ void __launch_bounds__(RunCfg1D<N, PHYS, NCBV>::NT) k_run1d(Params P,
                 }
             }
             __syncthreads();
-            // final stage: Lax--Friedrichs correction of the own cells from the chunk's traces
-            double dc[M];
+            // final stage: Lax--Friedrichs flux of every face of the chunk and every traced
+            // stage, once per face (face j lies between slots j and j+1); a cell then sums its
+            // two faces' corrections over the stages in stage order
+            {
+                const int nfaces = C::NCB - 1;
+                const int nitems = nfaces * P.nslot;
+                for (int k = threadIdx.x; k < nitems; k += blockDim.x) {
+                    const int j = k % nfaces, q = k / nfaces;
+                    const int rl = c0 - 1 + j, rr = rl + 1;  // unwrapped indices of the two cells
+                    const bool el = periodic || (rl >= 0 && rl < P.ncell);
+                    const bool er = periodic || (rr >= 0 && rr < P.ncell);
+                    double uL[M], uR[M];
+                    if (el && er) {
 #pragma unroll
-            for (int c = 0; c < M; ++c) dc[c] = 0.0;
-            if (own && node < 2) {
-                const int face = node;
-                const int nl = face == 0 ? lc - 1 : lc + 1;
-                const int nraw = c0 - 1 + nl;
-                const bool nb_exists = periodic || (nraw >= 0 && nraw < P.ncell);
-                for (int i = 0; i < P.s; ++i) {
-                    const int q = P.slot[i];
-                    if (q < 0) continue;
-                    double ui[M], ue[M], uL[M], uR[M];
+                        for (int c = 0; c < M; ++c) {
+                            uL[c] = sTr[q][j][1][c];
+                            uR[c] = sTr[q][j + 1][0][c];
+                        }
+                    } else if (er) {  // the left side of the mesh: exterior state of side 0
+                        double ui[M];
 #pragma unroll
-                    for (int c = 0; c < M; ++c) ui[c] = sTr[q][lc][face][c];
-                    if (nb_exists) {
+                        for (int c = 0; c < M; ++c) ui[c] = uR[c] = sTr[q][j + 1][0][c];
+                        exterior_state<PHYS, 1>(P, 0, ui, sAv[q][j + 1], uL);
+                    } else if (el) {  // the right side: exterior state of side 1
+                        double ui[M];
 #pragma unroll
-                        for (int c = 0; c < M; ++c) ue[c] = sTr[q][nl][face ^ 1][c];
+                        for (int c = 0; c < M; ++c) ui[c] = uL[c] = sTr[q][j][1][c];
+                        exterior_state<PHYS, 1>(P, 1, ui, sAv[q][j], uR);
                     } else {
-                        exterior_state<PHYS, 1>(P, face, ui, sAv[q][lc], ue);
-                    }
-#pragma unroll
-                    for (int c = 0; c < M; ++c) {
-                        uL[c] = face ? ui[c] : ue[c];
-                        uR[c] = face ? ue[c] : ui[c];
+                        continue;  // a face beyond the mesh: no own cell uses it
                     }
                     double alpha = fmax(speed_dir<PHYS, 1>(P, uL, 0), speed_dir<PHYS, 1>(P, uR, 0));
                     double fL[M], fR[M];
@@ -184,21 +190,34 @@ __global__ void __launch_bounds__(RunCfg1D<N, PHYS, NCBV>::NT) k_run1d(Params P,
 #pragma unroll
                     for (int c = 0; c < M; ++c) {
                         double fhat = 0.5 * (fL[c] + fR[c]) - 0.5 * alpha * (uR[c] - uL[c]);
-                        double fint = face ? fL[c] : fR[c];
-                        dc[c] = fma(P.b[i], fhat - fint, dc[c]);
+                        sFc[q][j][0][c] = fhat - fL[c];  // the left cell's right face
+                        sFc[q][j][1][c] = fhat - fR[c];  // the right cell's left face
                     }
                 }
             }
-            if (node < 2) {
-#pragma unroll
-                for (int c = 0; c < M; ++c) S.tf[lc][node][c] = dc[c];
-            }
             __syncthreads();
             double u[M];
+            if (own) {
+                double dl[M], dr[M];
 #pragma unroll
-            for (int c = 0; c < M; ++c) {
-                double corr = -T.liftp[a] * S.tf[lc][1][c] + T.liftm[a] * S.tf[lc][0][c];
-                u[c] = fma(dt, P.rhx * corr, acc[c]);
+                for (int c = 0; c < M; ++c) dl[c] = dr[c] = 0.0;
+                for (int i = 0; i < P.s; ++i) {
+                    const int q = P.slot[i];
+                    if (q < 0) continue;
+#pragma unroll
+                    for (int c = 0; c < M; ++c) {
+                        dl[c] = fma(P.b[i], sFc[q][lc - 1][1][c], dl[c]);
+                        dr[c] = fma(P.b[i], sFc[q][lc][0][c], dr[c]);
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < M; ++c) {
+                    double corr = -T.liftp[a] * dr[c] + T.liftm[a] * dl[c];
+                    u[c] = fma(dt, P.rhx * corr, acc[c]);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < M; ++c) u[c] = acc[c];
             }
             double pts[C::PPT][M];
             limit_block(P, B, S, lc, node, own, u, pts, true, true);

@@ -12,7 +12,10 @@ The reference is the fp64 variant on a grid `ref_factor` times finer than the fi
 the sweep; its cell averages are restricted (averaged) onto each coarse grid.  The L1 error
 is the sum over components of the mean absolute difference of the averages, divided by the
 same sum for the reference's averages (a relative error over the domain).  Time is the
-device time of the step kernels (inner, final, indicator) over the whole run.
+device time of the step kernels (inner, final, indicator) over the whole run.  Oscillation
+measures (what an anti-oscillation indicator is for): the total variation of the density
+averages relative to the restricted reference's, and the overshoot of the density averages
+beyond the reference's range.
 
 `matched_time(curve, target)`: the time a variant needs to reach the L1 error `target`,
 interpolated log-linearly between the sweep's grids (None outside its range).
@@ -90,6 +93,17 @@ def l1_error(avg, ref):
     return float(np.abs(avg - ref).mean(axis=(0, 1)).sum() / np.abs(ref).mean(axis=(0, 1)).sum())
 
 
+def total_variation(rho):
+    """Mean absolute jump of the density averages between neighbouring cells (x and y)."""
+    return float((np.abs(np.diff(rho, axis=0)).sum() + np.abs(np.diff(rho, axis=1)).sum()) / rho.size)
+
+
+def overshoot(rho, ref):
+    """How far the density averages leave the range of the (restricted) reference, relative to it."""
+    lo, hi = ref.min(), ref.max()
+    return float(max(0.0, rho.max() - hi, lo - rho.min()) / (hi - lo))
+
+
 def matched_time(curve, target):
     """curve: list of (l1, ms) for increasing grids.  Log-linear interpolation of ms at l1 = target."""
     pts = sorted(curve, key=lambda p: -p[0])  # decreasing error
@@ -119,8 +133,11 @@ def study(seed=7, sizes=(64, 128, 256), ref_factor=2, t_end=0.1, tvb_M=10.0, var
             except RunFailed as err:
                 rows.append({"n": n, "failed": str(err)})
                 continue
-            err = l1_error(avg, restrict(ref, ref_n // n))
-            rows.append({"n": n, "l1": err, "ms": ms, "wall_s": wall, "steps": steps, "troubled": troubled})
+            rr = restrict(ref, ref_n // n)
+            err = l1_error(avg, rr)
+            rows.append({"n": n, "l1": err, "ms": ms, "wall_s": wall, "steps": steps, "troubled": troubled,
+                         "tv_ratio": total_variation(avg[..., 0]) / total_variation(rr[..., 0]),
+                         "overshoot": overshoot(avg[..., 0], rr[..., 0])})
         out["variants"][v] = rows
     base = out["variants"]["fp64"]
     matched = {}
