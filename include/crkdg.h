@@ -256,6 +256,12 @@ crkdg_status crkdg_kernel_times(crkdg_t h, double ms[3], long long launches[3]);
  * hangs).  0 (the default) restores normal operation. */
 crkdg_status crkdg_set_barrier_test(crkdg_t h, int extra);
 
+/* Tuning of the 1D device-resident loop: the own cells of one block's chunk (1..30;
+ * each chunk also recomputes one halo cell per side).  0 (the default) takes 30, the
+ * fastest measured size.  Results do not depend on it (every cell's arithmetic is the
+ * same); only the time does. */
+crkdg_status crkdg_set_run1d_chunk(crkdg_t h, int cells);
+
 /* Number of doubles of the state. */
 size_t crkdg_state_size(crkdg_t h);
 

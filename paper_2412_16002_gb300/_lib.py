@@ -94,6 +94,7 @@ SYMBOLS = {
     "crkdg_total_mass": (C.c_int, [_H, C.c_int, _dp]),
     "crkdg_set_profiling": (C.c_int, [_H, C.c_int]),
     "crkdg_set_barrier_test": (C.c_int, [_H, C.c_int]),
+    "crkdg_set_run1d_chunk": (C.c_int, [_H, C.c_int]),
     "crkdg_kernel_times": (C.c_int, [_H, _dp, C.POINTER(C.c_longlong)]),
     "crkdg_state_size": (C.c_size_t, [_H]),
     "crkdg_last_error": (C.c_char_p, [_H]),

@@ -163,6 +163,7 @@ struct crkdg_ctx {
     float *mlp = nullptr;    // MLP parameters of the learned indicator
     bool harvest = false;
     int barrier_extra = 0;   // testing aid (crkdg_set_barrier_test)
+    int run1d_chunk = 0;     // own cells per block chunk of the 1D step loop (0: automatic)
     RunCtl *ctl = nullptr;   // device control block of the 1D step loop
     RunCtl *hctl = nullptr;  // pinned host copy
     std::string err;
@@ -527,6 +528,12 @@ crkdg_status crkdg_set_profiling(crkdg_t h, int on) {
     return CRKDG_OK;
 }
 
+crkdg_status crkdg_set_run1d_chunk(crkdg_t h, int cells) {
+    if (!h || cells < 0 || cells > 30) return CRKDG_E_ARG;
+    h->run1d_chunk = cells;
+    return CRKDG_OK;
+}
+
 crkdg_status crkdg_set_barrier_test(crkdg_t h, int extra) {
     if (!h || extra < 0) return CRKDG_E_ARG;
     h->barrier_extra = extra;
@@ -732,7 +739,7 @@ static crkdg_status advance_1d(crkdg_t h, int nsteps, double cfl, double dt_fixe
     CK(h, cudaMemcpyAsync(h->ctl, c, sizeof(RunCtl), cudaMemcpyHostToDevice, h->st));
     int nb = 0;
     if (h->prof) CK(h, cudaEventRecord(h->ev[0], h->st));
-    CK(h, crkdg_run_1d(h->n, h->phys, h->st, P, h->u, h->unew, h->ctl, &nb));
+    CK(h, crkdg_run_1d(h->n, h->phys, h->st, P, h->u, h->unew, h->ctl, h->run1d_chunk, &nb));
     if (h->prof) CK(h, cudaEventRecord(h->ev[1], h->st));
     CK(h, cudaMemcpyAsync(c, h->ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, h->st));
     CK(h, cudaStreamSynchronize(h->st));

@@ -15,9 +15,9 @@ cudaError_t crkdg_launch_1d(int kernel, int n, int phys, int nblocks, cudaStream
 }
 
 cudaError_t crkdg_run_1d(int n, int phys, cudaStream_t st, const Params &P, double *u0, double *u1, RunCtl *ctl,
-                         int *nblocks) {
+                         int chunk, int *nblocks) {
 #define CRKDG_RUN(NV, PV) \
-    if (n == NV && phys == PV) return run1d_launch<NV, PV>(st, P, u0, u1, ctl, nblocks);
+    if (n == NV && phys == PV) return run1d_launch<NV, PV>(st, P, u0, u1, ctl, chunk, nblocks);
     CRKDG_RUN(2, PH_ADV) CRKDG_RUN(2, PH_BURG) CRKDG_RUN(2, PH_EULER)
     CRKDG_RUN(3, PH_ADV) CRKDG_RUN(3, PH_BURG) CRKDG_RUN(3, PH_EULER)
     CRKDG_RUN(4, PH_ADV) CRKDG_RUN(4, PH_BURG) CRKDG_RUN(4, PH_EULER)

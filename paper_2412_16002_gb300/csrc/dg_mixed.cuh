@@ -124,11 +124,12 @@ __device__ __forceinline__ void exterior_state_f(const Params &P, int side, cons
 
 template <class C>
 struct SmemX {
-    float u[C::NCB][C::M][C::NN];     // node values (or deviations in the limiter)
-    float f[C::D][C::NCB][C::M][C::NN];
-    float tf[C::NCB][C::NTR][C::M];   // trace fluxes / face corrections
-    float fh[C::NCB][C::NTR][C::M];   // sum_i b_i fhat^(i) at the face points
-    float w[C::NCB][C::M][C::NN];     // weighted values for the per-cell FP32 means
+    // component-major ([m][cell][...]): a warp's threads (consecutive nodes or face points of
+    // consecutive cells) touch consecutive words of one component
+    float u[C::M][C::NCB][C::NN];     // node values (or deviations in the limiter)
+    float f[C::D][C::M][C::NCB][C::NN];
+    float tf[C::M][C::NCB][C::NTR];   // trace fluxes / face corrections
+    float w[C::M][C::NCB][C::NN];     // weighted values for the per-cell FP32 means
     float ubf[C::NCB][C::M];          // FP32 copy of the averages
     float mean[C::NCB][C::M];
     double gb[C::NCB][C::M];          // FP64 face sums
@@ -139,7 +140,7 @@ struct SmemX {
     union {  // never live at the same time
         double redd[C::NCB][C::NN][2];
         float al[C::NCB][C::NTR];
-        double term[C::NCB][C::NTR][C::M];
+        double term[C::M][C::NCB][C::NTR];
     };
     double th[C::NCB][2];
     int fl[C::NCB][C::NN];
@@ -167,8 +168,9 @@ __device__ __forceinline__ void init_kappa(const Params &P, SmemX<C> &S) {
 }
 
 // FP32 interpolation of node data q[c][node] of one cell to S_K point p
+// q: the cell's node data of component 0; component c starts at q + c * cs
 template <int DIM, int N, int M, int NN>
-__device__ __forceinline__ void sk_eval_f(const float (&q)[M][NN], int p, float *v) {
+__device__ __forceinline__ void sk_eval_f(const float *q, int cs, int p, float *v) {
     const NodalTables &T = c_tab[N - 2];
     constexpr int L = nlob(N);
     if constexpr (DIM == 1) {
@@ -176,7 +178,7 @@ __device__ __forceinline__ void sk_eval_f(const float (&q)[M][NN], int p, float 
         for (int c = 0; c < M; ++c) {
             float s = 0.0f;
 #pragma unroll
-            for (int a = 0; a < N; ++a) s = fmaf(T.Iglf[p][a], q[c][a], s);
+            for (int a = 0; a < N; ++a) s = fmaf(T.Iglf[p][a], q[c * cs + a], s);
             v[c] = s;
         }
     } else if (p < N * L) {
@@ -185,7 +187,7 @@ __device__ __forceinline__ void sk_eval_f(const float (&q)[M][NN], int p, float 
         for (int c = 0; c < M; ++c) {
             float s = 0.0f;
 #pragma unroll
-            for (int a = 0; a < N; ++a) s = fmaf(T.Iglf[al][a], q[c][beta * N + a], s);
+            for (int a = 0; a < N; ++a) s = fmaf(T.Iglf[al][a], q[c * cs + beta * N + a], s);
             v[c] = s;
         }
     } else {
@@ -195,7 +197,7 @@ __device__ __forceinline__ void sk_eval_f(const float (&q)[M][NN], int p, float 
         for (int c = 0; c < M; ++c) {
             float s = 0.0f;
 #pragma unroll
-            for (int b = 0; b < N; ++b) s = fmaf(T.Iglf[al][b], q[c][b * N + beta], s);
+            for (int b = 0; b < N; ++b) s = fmaf(T.Iglf[al][b], q[c * cs + b * N + beta], s);
             v[c] = s;
         }
     }
@@ -224,9 +226,9 @@ __device__ void eval_G_x(const Params &P, SmemX<C> &S, int lc, int node, const f
         }
 #pragma unroll
         for (int c = 0; c < M; ++c) {
-            S.u[lc][c][node] = u[c];
-            S.f[0][lc][c][node] = fx[c];
-            if constexpr (DIM == 2) S.f[1][lc][c][node] = fy[c];
+            S.u[c][lc][node] = u[c];
+            S.f[0][c][lc][node] = fx[c];
+            if constexpr (DIM == 2) S.f[1][c][lc][node] = fy[c];
         }
     }
     __syncthreads();
@@ -235,12 +237,12 @@ __device__ void eval_G_x(const Params &P, SmemX<C> &S, int lc, int node, const f
     for (int c = 0; c < M; ++c) {
         float s = 0.0f;
 #pragma unroll
-        for (int q = 0; q < N; ++q) s = fmaf(T.Dhatf[a][q], S.f[0][lc][c][b * N + q], s);
+        for (int q = 0; q < N; ++q) s = fmaf(T.Dhatf[a][q], S.f[0][c][lc][b * N + q], s);
         vx[c] = s;
         if constexpr (DIM == 2) {
             float t = 0.0f;
 #pragma unroll
-            for (int r = 0; r < N; ++r) t = fmaf(T.Dhatf[b][r], S.f[1][lc][c][r * N + a], t);
+            for (int r = 0; r < N; ++r) t = fmaf(T.Dhatf[b][r], S.f[1][c][lc][r * N + a], t);
             vy[c] = t;
         }
     }
@@ -255,17 +257,17 @@ __device__ void eval_G_x(const Params &P, SmemX<C> &S, int lc, int node, const f
                 float s = 0.0f;
                 if (DIM == 1 || face < 2) {
 #pragma unroll
-                    for (int q = 0; q < N; ++q) s = fmaf(l[q], S.u[lc][c][pos * N + q], s);
+                    for (int q = 0; q < N; ++q) s = fmaf(l[q], S.u[c][lc][pos * N + q], s);
                 } else {
 #pragma unroll
-                    for (int q = 0; q < N; ++q) s = fmaf(l[q], S.u[lc][c][q * N + pos], s);
+                    for (int q = 0; q < N; ++q) s = fmaf(l[q], S.u[c][lc][q * N + pos], s);
                 }
                 trs[j][c] = s;
             }
             float f[M];
             flux_dir_f<PHYS, DIM>(P, trs[j], face >> 1, f);
 #pragma unroll
-            for (int c = 0; c < M; ++c) S.tf[lc][fp][c] = f[c];
+            for (int c = 0; c < M; ++c) S.tf[c][lc][fp] = f[c];
         }
     }
     __syncthreads();
@@ -273,20 +275,20 @@ __device__ void eval_G_x(const Params &P, SmemX<C> &S, int lc, int node, const f
     float g32[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) {
-        float gx = vx[c] - T.liftpf[a] * S.tf[lc][NF + b][c] + T.liftmf[a] * S.tf[lc][b][c];
+        float gx = vx[c] - T.liftpf[a] * S.tf[c][lc][NF + b] + T.liftmf[a] * S.tf[c][lc][b];
         float gv = rhx * gx;
         if constexpr (DIM == 2) {
-            float gy = vy[c] - T.liftpf[b] * S.tf[lc][3 * NF + a][c] + T.liftmf[b] * S.tf[lc][2 * NF + a][c];
+            float gy = vy[c] - T.liftpf[b] * S.tf[c][lc][3 * NF + a] + T.liftmf[b] * S.tf[c][lc][2 * NF + a];
             gv = fmaf(rhy, gy, gv);
         }
         g32[c] = gv;
-        S.w[lc][c][node] = wnode_f<DIM, N>(node) * gv;
+        S.w[c][lc][node] = wnode_f<DIM, N>(node) * gv;
     }
     __syncthreads();
     for (int c = node; c < M; c += NN) {
         float m = 0.0f, g = 0.0f;
-        for (int q = 0; q < NN; ++q) m += S.w[lc][c][q];
-        for (int fp = 0; fp < NTR; ++fp) g = fmaf(S.kapf[fp], S.tf[lc][fp][c], g);
+        for (int q = 0; q < NN; ++q) m += S.w[c][lc][q];
+        for (int fp = 0; fp < NTR; ++fp) g = fmaf(S.kapf[fp], S.tf[c][lc][fp], g);
         S.mean[lc][c] = m;
         S.gbf[lc][c] = g;
     }
@@ -334,7 +336,7 @@ template <class C>
 __device__ __forceinline__ void eval64_x(SmemX<C> &S, int lc, int p, const double *ub, double *v, float *v32) {
     constexpr int M = C::M;
     float s[M];
-    sk_eval_f<C::D, C::NP, M, C::NN>(S.u[lc], p, s);
+    sk_eval_f<C::D, C::NP, M, C::NN>(&S.u[0][lc][0], C::NCB * C::NN, p, s);
 #pragma unroll
     for (int c = 0; c < M; ++c) {
         float d = s[c] - S.mean[lc][c];
@@ -350,13 +352,13 @@ __device__ __forceinline__ void publish_dev(const double *ub, const float *dv, S
     (void)ub;  // S.ubf already holds the FP32 copy of the averages
 #pragma unroll
     for (int c = 0; c < M; ++c) {
-        S.u[lc][c][node] = dv[c];
-        S.w[lc][c][node] = wnode_f<C::D, C::NP>(node) * dv[c];
+        S.u[c][lc][node] = dv[c];
+        S.w[c][lc][node] = wnode_f<C::D, C::NP>(node) * dv[c];
     }
     __syncthreads();
     for (int c = node; c < M; c += NN) {
         float m = 0.0f;
-        for (int q = 0; q < NN; ++q) m += S.w[lc][c][q];
+        for (int q = 0; q < NN; ++q) m += S.w[c][lc][q];
         S.mean[lc][c] = m;
     }
     __syncthreads();
@@ -378,7 +380,7 @@ __device__ void limit_x(const Params &P, const Bufs &B, SmemX<C> &S, int lc, int
         int p = node + j * NN;
         if (p < NSK) {
             float s[M];
-            sk_eval_f<DIM, C::NP, M, NN>(S.u[lc], p, s);
+            sk_eval_f<DIM, C::NP, M, NN>(&S.u[0][lc][0], C::NCB * C::NN, p, s);
 #pragma unroll
             for (int c = 0; c < M; ++c) {
                 float d = s[c] - S.mean[lc][c];
@@ -561,7 +563,7 @@ __device__ __forceinline__ void load_x(const Params &P, const MixBufs &X, int ce
 
 // Inner stages of the split representation (cell-local).
 template <class C>
-__global__ void __launch_bounds__(C::NT) k_inner_x(Params P, MixBufs X) {
+__global__ void __launch_bounds__(C::NT, (C::NT > 128 ? 2 : 4)) k_inner_x(Params P, MixBufs X) {
     constexpr int M = C::M, NN = C::NN, NTR = C::NTR, FPT = C::FPT;
     __shared__ SmemX<C> S;
     const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
@@ -656,7 +658,7 @@ __global__ void __launch_bounds__(C::NT) k_inner_x(Params P, MixBufs X) {
 // sum_i b_i fhat^(i) over the face points, deviations from the FP32 lift of
 // sum_i b_i (fhat^(i) - f(u_int^(i))); then the limiter and the trial-step rate.
 template <class C>
-__global__ void __launch_bounds__(C::NT) k_final_x(Params P, MixBufs X) {
+__global__ void __launch_bounds__(C::NT, (C::NT > 128 ? 2 : 4)) k_final_x(Params P, MixBufs X) {
     constexpr int DIM = C::D, N = C::NP, PHYS = C::PH;
     constexpr int M = C::M, NN = C::NN, NF = C::NF, NTR = C::NTR, FPT = C::FPT;
     __shared__ SmemX<C> S;
@@ -747,8 +749,7 @@ __global__ void __launch_bounds__(C::NT) k_final_x(Params P, MixBufs X) {
         if (fp < NTR)
 #pragma unroll
             for (int c = 0; c < M; ++c) {
-                S.tf[lc][fp][c] = dcf[j][c];
-                S.fh[lc][fp][c] = fhs[j][c];
+                S.tf[c][lc][fp] = dcf[j][c];
             }
     }
     __syncthreads();
@@ -756,14 +757,14 @@ __global__ void __launch_bounds__(C::NT) k_final_x(Params P, MixBufs X) {
     float corr[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) {
-        float cx = -T.liftpf[a] * S.tf[lc][NF + b][c] + T.liftmf[a] * S.tf[lc][b][c];
+        float cx = -T.liftpf[a] * S.tf[c][lc][NF + b] + T.liftmf[a] * S.tf[c][lc][b];
         float cv = rhx * cx;
         if constexpr (DIM == 2) {
-            float cy = -T.liftpf[b] * S.tf[lc][3 * NF + a][c] + T.liftmf[b] * S.tf[lc][2 * NF + a][c];
+            float cy = -T.liftpf[b] * S.tf[c][lc][3 * NF + a] + T.liftmf[b] * S.tf[c][lc][2 * NF + a];
             cv = fmaf(rhy, cy, cv);
         }
         corr[c] = cv;
-        S.w[lc][c][node] = wnode_f<DIM, N>(node) * cv;
+        S.w[c][lc][node] = wnode_f<DIM, N>(node) * cv;
     }
     if (P.mode == MODE_OP_F) {  // F = G + lift(fhat - f_int): nodal FP64 output, no limiter
         if (active)
@@ -781,15 +782,15 @@ __global__ void __launch_bounds__(C::NT) k_final_x(Params P, MixBufs X) {
         int fp = node + j * NN;
         if (fp < NTR)
 #pragma unroll
-            for (int c = 0; c < M; ++c) S.term[lc][fp][c] = S.kap[fp] * (double)fhs[j][c];
+            for (int c = 0; c < M; ++c) S.term[c][lc][fp] = S.kap[fp] * (double)fhs[j][c];
     }
     __syncthreads();
     for (int c = node; c < M; c += NN) {
         float m = 0.0f;
-        for (int q = 0; q < NN; ++q) m += S.w[lc][c][q];
+        for (int q = 0; q < NN; ++q) m += S.w[c][lc][q];
         S.mean[lc][c] = m;
         double g = 0.0;
-        for (int fp = 0; fp < NTR; ++fp) g += S.term[lc][fp][c];
+        for (int fp = 0; fp < NTR; ++fp) g += S.term[c][lc][fp];
         double v = fma(P.dt, g, ub0[c]);
         S.ubd[lc][c] = v;
         S.ubf[lc][c] = (float)v;

@@ -223,7 +223,8 @@ int crkdg_ens_cells_per_block(int kind, int n);
 cudaError_t crkdg_ens_control(int which, cudaStream_t st, crkdg::EnsProblem *E, int np, crkdg::EnsCtl *ctl, int arg);
 // Closed-form nodal tables for n = 2, 3, 4 (defined in crkdg_api.cu).
 void crkdg_build_tables(crkdg::NodalTables *tab);
-// Persistent 1D step loop (cooperative launch); *nblocks receives the grid used.
+// Persistent 1D step loop (cooperative launch); chunk: own cells per block chunk (0: fill
+// every block slot of the GPU); *nblocks receives the grid used.
 cudaError_t crkdg_run_1d(int n, int phys, cudaStream_t st, const crkdg::Params &P, double *u0, double *u1,
-                         crkdg::RunCtl *ctl, int *nblocks);
+                         crkdg::RunCtl *ctl, int chunk, int *nblocks);
 }

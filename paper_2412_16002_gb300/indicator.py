@@ -140,3 +140,38 @@ def confusion(theta, X, Y, lo=0.4, hi=0.6):
         "positives": int(y.sum().item()),
         "cells": int(Y.numel()),
     }
+
+
+def main():
+    """Harvest labelled cells from seeded Riemann runs, train the network, save its parameters."""
+    import argparse
+    import time
+
+    import torch
+
+    from . import build
+
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--seeds", default="1000,1001,1002,1003")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--steps", type=int, default=800)
+    ap.add_argument("--every", type=int, default=200)
+    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--tvb-M", type=float, default=10.0)
+    ap.add_argument("--out", default=None, help="write the FP32 parameters here (numpy .npy)")
+    args = ap.parse_args()
+    build()
+    t0 = time.perf_counter()
+    X, Y = harvest([int(s) for s in args.seeds.split(",")], n=args.n, steps=args.steps, every=args.every,
+                   tvb_M=args.tvb_M)
+    theta, hist = train(X, Y, epochs=args.epochs)
+    conf = confusion(theta, X, Y)
+    torch.cuda.synchronize()
+    print({"cells": int(Y.numel()), "troubled_fraction": float(Y.mean().item()), "loss": hist,
+           "agreement": conf["accuracy"], "seconds": time.perf_counter() - t0})
+    if args.out:
+        np.save(args.out, theta.cpu().numpy())
+
+
+if __name__ == "__main__":
+    main()

@@ -152,6 +152,10 @@ class Solver:
                                                C.byref(tt), C.byref(done), C.byref(rs)))
         return tt.value, done.value, rs.value
 
+    def set_run1d_chunk(self, cells=0):
+        """Own cells per block chunk of the 1D device-resident loop (0: automatic)."""
+        self._chk(self.lib.crkdg_set_run1d_chunk(self.h, cells))
+
     # ---- measurement -------------------------------------------------------------
     def set_profiling(self, on=True):
         self._chk(self.lib.crkdg_set_profiling(self.h, 1 if on else 0))

@@ -143,3 +143,24 @@ def test_advance_barrier_wait_expires_with_status():
     g._chk(g.lib.crkdg_set_barrier_test(g.h, 0))
     t, steps, rs = g.advance(3, wl.cfl, 6.0, "heun3")  # the context is still usable
     assert steps == 3 and g.margins().min() >= 0.0
+
+
+@pytest.mark.parametrize("cfl_scale", [1.0, 5.0])
+def test_chunk_size_does_not_change_results(cfl_scale):
+    """Every cell's arithmetic in the device-resident loop is the same whatever the chunk
+    size (halo cells recompute the same inner stages), so states, times and restart counts
+    are bit-identical for chunks of 30, 13, 7 and 1 own cells and the automatic choice."""
+    from paper_2412_16002_gb300.solver import Solver
+
+    wl = inputs.euler_blast_tube(1000, 2)
+    out = []
+    for chunk in (30, 13, 7, 1, 0):
+        g = Solver.from_workload(wl)
+        g.set_state(wl.state)
+        g.set_run1d_chunk(chunk)
+        t, done, rs = g.advance(40, wl.cfl * cfl_scale, 1e30, wl.tableau)
+        out.append((g.get_state().copy(), t, done, rs))
+    for st, t, done, rs in out[1:]:
+        assert np.array_equal(st, out[0][0]) and t == out[0][1] and done == out[0][2] and rs == out[0][3]
+    if cfl_scale > 1:
+        assert out[0][3] > 0
