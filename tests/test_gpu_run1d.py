@@ -164,3 +164,68 @@ def test_chunk_size_does_not_change_results(cfl_scale):
         assert np.array_equal(st, out[0][0]) and t == out[0][1] and done == out[0][2] and rs == out[0][3]
     if cfl_scale > 1:
         assert out[0][3] > 0
+
+
+@pytest.mark.parametrize("case", ["burgers200_p2", "tube1000_p2", "smooth257_p3"])
+@pytest.mark.parametrize("adaptive", [False, True])
+def test_loop_is_bitwise_the_step_path(case, adaptive):
+    """The device-resident loop (one thread per node and component) forms every value with
+    the operations of the per-step kernels in the same order: 40 steps of crkdg_advance
+    (adaptive) or crkdg_advance_fixed agree with 40 crkdg_step calls at the same trial
+    steps to rounding (relative 1e-12: the compiler may contract a multiply-add
+    differently in the two kernels), with the same restarts."""
+    from paper_2412_16002_gb300.solver import Solver
+
+    if case == "burgers200_p2":
+        wl, scale = inputs.burgers_sine(200, 2), 1.0
+    elif case == "tube1000_p2":
+        wl, scale = inputs.euler_blast_tube(1000, 2), 1.0
+    else:
+        wl = inputs.Workload("smooth", 1, 257, 1, 3, (0.0, 1.0), "euler", ("periodic",) * 4,
+                             inputs.random_euler(1, 257, 1, 3, seed=3, osc=0.05), cfl=0.1, tableau="rk4")
+        scale = 1.0
+    cfl = wl.cfl * scale
+    a = Solver.from_workload(wl)
+    a.set_state(wl.state)
+    b = Solver.from_workload(wl)
+    b.set_state(wl.state)
+    dt0 = 0.3 * a.max_dt(cfl)  # fixed steps well inside the limit as the flow speeds up
+    if adaptive:
+        t, done, rs = a.advance(40, cfl, 1e30, wl.tableau)
+    else:
+        t, done, rs = a.advance_fixed(40, dt0, 1e30, wl.tableau)
+    tb, rsb = 0.0, 0
+    for _ in range(40):
+        info = b.step(b.max_dt(cfl) if adaptive else dt0, wl.tableau)
+        tb += info["dt_taken"]
+        rsb += info["restarts"]
+    assert done == 40 and rs == rsb
+    err = rel_linf(a.get_state(), b.get_state(), wl.m)
+    print(f"{case} adaptive={adaptive}: loop vs step path relative L-inf {err:.3e}")
+    assert err < 1e-12
+    assert abs(t - tb) <= 1e-12 * abs(tb)
+
+
+def test_loop_and_step_path_restart_alike():
+    """The blast tube at 5x its CFL number restarts in both paths at the same steps; the
+    states are then compared through the invariants only (under restarts at that step size
+    the limiter near the density floor amplifies the paths' rounding differences)."""
+    from paper_2412_16002_gb300.solver import Solver
+
+    wl = inputs.euler_blast_tube(1000, 2)
+    cfl = 5.0 * wl.cfl
+    a = Solver.from_workload(wl)
+    a.set_state(wl.state)
+    b = Solver.from_workload(wl)
+    b.set_state(wl.state)
+    t, done, rs = a.advance(20, cfl, 1e30, wl.tableau)
+    tb, rsb = 0.0, 0
+    for _ in range(20):
+        info = b.step(b.max_dt(cfl), wl.tableau)
+        tb += info["dt_taken"]
+        rsb += info["restarts"]
+    assert done == 20 and rs == rsb and rs > 0
+    assert abs(t - tb) <= 1e-6 * tb
+    assert a.margins().min() >= 0.0 and b.margins().min() >= 0.0
+    for c in (0, 1, 2):
+        assert abs(a.mass(c) - b.mass(c)) <= 1e-6 * max(1.0, abs(b.mass(c)))
