@@ -653,9 +653,8 @@ crkdg_status crkdg_step(crkdg_t h, double dt, const crkdg_tableau *tab, crkdg_st
                 if (ind) {
                     const bool learned = h->opt.indicator == CRKDG_IND_MLP;
                     if (learned || h->harvest) {
-                        P.ind_stage = 1;  // plain decision of the unlimited state
-                        CK(h, launch(h, K_TROUBLE, P, B));
-                        if (h->feat) CK(h, launch(h, K_FEATURES, P, B));
+                        // features and the plain decision of the unlimited state in one pass
+                        CK(h, launch(h, K_FEATURES, P, B));
                         if (learned && crkdg_mlp_forward(h->mlp, h->feat, h->ncell, h->prob, h->st) != CRKDG_OK)
                             return fail(h, CRKDG_E_CUDA, "step: MLP forward failed");
                         P.ind_stage = learned ? 3 : 2;  // (combine the learned flags and) limit the flagged cells

@@ -148,8 +148,7 @@ crkdg_status enqueue_attempt(crkdg_ens_t e) {
     if (ind != CRKDG_IND_OFF) {
         const bool learned = ind == CRKDG_IND_MLP;
         if (learned || e->harvest) {
-            ECK(e, run(ENS_TROUBLE, 1));
-            ECK(e, run(ENS_FEATURES, 0));
+            ECK(e, run(ENS_FEATURES, 0));  // features and the plain decision in one pass
             if (learned && crkdg_mlp_forward(e->mlp, e->arena_feat, (int)e->total_cells, e->arena_prob, e->st) !=
                                CRKDG_OK)
                 return efail(e, CRKDG_E_CUDA, "ensemble: MLP forward failed");

@@ -894,10 +894,6 @@ __device__ __forceinline__ void trouble_body(const Params &P, const Bufs &B, int
         if (trouble) atomicOr(&sTr[lc], 1);
     }
     __syncthreads();
-    if (P.ind_stage == 1) {  // decision only: the flags go to memory
-        if (node == 0 && active) B.tflags[cell] = sTr[lc] != 0 ? 1 : 0;
-        return;
-    }
     bool troubled = active && (P.ind_stage >= 2 ? B.tflags[cell] != 0 : sTr[lc] != 0);
     if (P.ind_stage == 3 && active) {  // learned flags: p > 0.6 troubled, p < 0.4 smooth, else the plain flag
         const float pr = B.prob[cell];
@@ -934,11 +930,12 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_trouble(Params P, Buf
     trouble_body<DIM, N, PHYS>(P, B, blockIdx.x);
 }
 
-// MLP features of every cell (2D Euler): per component, the 3x3 neighbourhood of
-// cell averages (neighbours across a boundary follow its condition) normalised by the
-// stencil mean and range, and the cell's first Legendre moments over the same range.
-// Layout [cell][44]: 36 normalised averages ([comp][9], row-major, centre 4), then
-// 8 normalised moments ([comp][x, y]).  Reads unew and the averages in aux.
+// MLP features of every cell (2D Euler) and the plain indicator's decision (tflags).
+// Features, per component: the 3x3 neighbourhood of cell averages (neighbours across a
+// boundary follow its condition) minus their mean over den = max(range, M hx hy) +
+// 1e-6 max|v|, and the cell's first Legendre moments over the same den.  Layout
+// [cell][44]: 36 normalised averages ([comp][9], row-major, centre 4), then 8
+// normalised moments ([comp][x, y]).  Reads unew and the averages in aux.
 template <int DIM, int N, int PHYS>
 __device__ __forceinline__ void features_body(const Params &P, const Bufs &B, int blk) {
     constexpr int M = ncomp(PHYS, DIM);
@@ -1012,6 +1009,34 @@ __device__ __forceinline__ void features_body(const Params &P, const Bufs &B, in
             f[36 + 2 * c] = (float)(cx * scale);
             f[37 + 2 * c] = (float)(cy * scale);
         }
+        // the plain indicator's decision for this cell, with the troubled-cell kernel's
+        // arithmetic: the label of harvested features and the fallback of the learned flags
+        int trouble = 0;
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+            const double h = 2.0 / (d == 0 ? P.rhx : P.rhy);
+            const double thr = P.tvb_M * h * h;
+            const double *lo = v[d == 0 ? 3 : 1], *hi = v[d == 0 ? 5 : 7], *own = v[4];
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                const double *uc = B.unew + ((size_t)c * P.ncell + cell) * NN;
+                double fr = 0.0, fl = 0.0;
+                for (int q = 0; q < NN; ++q) {
+                    int qa = q % N, qb = q / N;
+                    int along = d == 0 ? qa : qb, across = d == 0 ? qb : qa;
+                    double wa = T.w1[across];
+                    double val = uc[q];
+                    fr = fma(wa * T.lp[along], val, fr);
+                    fl = fma(wa * T.lm[along], val, fl);
+                }
+                double utR = fr - own[c], utL = own[c] - fl;
+                double dp = hi[c] - own[c], dm = own[c] - lo[c];
+                double mR = fabs(utR) <= thr ? utR : minmod3d(utR, dp, dm);
+                double mL = fabs(utL) <= thr ? utL : minmod3d(utL, dp, dm);
+                if (mR != utR || mL != utL) trouble = 1;
+            }
+        }
+        if (B.tflags) B.tflags[cell] = trouble;
     }
 }
 

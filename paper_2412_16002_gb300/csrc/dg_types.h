@@ -76,8 +76,9 @@ struct Params {
     int mode;
     int defer_limit;  // final kernel leaves the limiter to the troubled-cell kernel
     double tvb_M;     // TVB constant of the plain indicator
-    int ind_stage;    // troubled-cell kernel: 0 decide and limit, 1 decide only, 2 limit given flags,
-                      // 3 combine the given plain flags with the learned probabilities, then limit
+    int ind_stage;    // troubled-cell kernel: 0 decide and limit, 2 limit the given flags (the feature
+                      // kernel decided), 3 combine the given plain flags with the learned
+                      // probabilities, then limit
     ParamsF f;        // split-precision kernels only
 };
 
