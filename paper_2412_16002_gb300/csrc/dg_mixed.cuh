@@ -122,12 +122,20 @@ __device__ __forceinline__ void exterior_state_f(const Params &P, int side, cons
 
 // ----------------------------------------------------------------------------- block storage
 
+// Q^3 in 2D (n = 4): node rows are 16-byte aligned float4s, so the line operators read a
+// whole row with one shared-memory load; column access goes through transposed copies.
 template <class C>
-struct SmemX {
+constexpr bool vec4() {
+    return C::D == 2 && C::NP == 4;
+}
+
+template <class C>
+struct alignas(16) SmemX {
     // component-major ([m][cell][...]): a warp's threads (consecutive nodes or face points of
     // consecutive cells) touch consecutive words of one component
     float u[C::M][C::NCB][C::NN];     // node values (or deviations in the limiter)
-    float f[C::D][C::M][C::NCB][C::NN];
+    float uT[C::M][C::NCB][vec4<C>() ? C::NN : 1];  // the same, transposed (node a*n + b)
+    float f[C::D][C::M][C::NCB][C::NN];  // fluxes; with vec4 the y-fluxes are transposed
     float tf[C::M][C::NCB][C::NTR];   // trace fluxes / face corrections
     float w[C::M][C::NCB][C::NN];     // weighted values for the per-cell FP32 means
     float ubf[C::NCB][C::M];          // FP32 copy of the averages
@@ -168,9 +176,10 @@ __device__ __forceinline__ void init_kappa(const Params &P, SmemX<C> &S) {
 }
 
 // FP32 interpolation of node data q[c][node] of one cell to S_K point p
-// q: the cell's node data of component 0; component c starts at q + c * cs
+// q: the cell's node data of component 0; component c starts at q + c * cs.  qT (may be
+// null unless n = 4 in 2D): the transposed copy, read as float4 columns.
 template <int DIM, int N, int M, int NN>
-__device__ __forceinline__ void sk_eval_f(const float *q, int cs, int p, float *v) {
+__device__ __forceinline__ void sk_eval_f(const float *q, const float *qT, int cs, int p, float *v) {
     const NodalTables &T = c_tab[N - 2];
     constexpr int L = nlob(N);
     if constexpr (DIM == 1) {
@@ -179,6 +188,31 @@ __device__ __forceinline__ void sk_eval_f(const float *q, int cs, int p, float *
             float s = 0.0f;
 #pragma unroll
             for (int a = 0; a < N; ++a) s = fmaf(T.Iglf[p][a], q[c * cs + a], s);
+            v[c] = s;
+        }
+    } else if (DIM == 2 && N == 4 && p < N * L) {  // row beta as one float4 per component
+        int beta = p / L, al = p - beta * L;
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            const float4 r = *reinterpret_cast<const float4 *>(q + c * cs + beta * N);
+            float s = 0.0f;
+            s = fmaf(T.Iglf[al][0], r.x, s);
+            s = fmaf(T.Iglf[al][1], r.y, s);
+            s = fmaf(T.Iglf[al][2], r.z, s);
+            s = fmaf(T.Iglf[al][3], r.w, s);
+            v[c] = s;
+        }
+    } else if (DIM == 2 && N == 4) {  // column beta from the transposed copy
+        int rr = p - N * L;
+        int beta = rr / L, al = rr - beta * L;
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            const float4 r = *reinterpret_cast<const float4 *>(qT + c * cs + beta * N);
+            float s = 0.0f;
+            s = fmaf(T.Iglf[al][0], r.x, s);
+            s = fmaf(T.Iglf[al][1], r.y, s);
+            s = fmaf(T.Iglf[al][2], r.z, s);
+            s = fmaf(T.Iglf[al][3], r.w, s);
             v[c] = s;
         }
     } else if (p < N * L) {
@@ -228,22 +262,43 @@ __device__ void eval_G_x(const Params &P, SmemX<C> &S, int lc, int node, const f
         for (int c = 0; c < M; ++c) {
             S.u[c][lc][node] = u[c];
             S.f[0][c][lc][node] = fx[c];
-            if constexpr (DIM == 2) S.f[1][c][lc][node] = fy[c];
+            if constexpr (vec4<C>()) {
+                S.uT[c][lc][a * N + b] = u[c];
+                S.f[1][c][lc][a * N + b] = fy[c];  // transposed: column a is contiguous
+            } else if constexpr (DIM == 2) {
+                S.f[1][c][lc][node] = fy[c];
+            }
         }
     }
     __syncthreads();
     float vx[M], vy[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) {
-        float s = 0.0f;
-#pragma unroll
-        for (int q = 0; q < N; ++q) s = fmaf(T.Dhatf[a][q], S.f[0][c][lc][b * N + q], s);
-        vx[c] = s;
-        if constexpr (DIM == 2) {
-            float t = 0.0f;
-#pragma unroll
-            for (int r = 0; r < N; ++r) t = fmaf(T.Dhatf[b][r], S.f[1][c][lc][r * N + a], t);
+        if constexpr (vec4<C>()) {
+            const float4 fr = *reinterpret_cast<const float4 *>(&S.f[0][c][lc][b * N]);
+            const float4 fc = *reinterpret_cast<const float4 *>(&S.f[1][c][lc][a * N]);
+            float s = 0.0f, t = 0.0f;
+            s = fmaf(T.Dhatf[a][0], fr.x, s);
+            s = fmaf(T.Dhatf[a][1], fr.y, s);
+            s = fmaf(T.Dhatf[a][2], fr.z, s);
+            s = fmaf(T.Dhatf[a][3], fr.w, s);
+            t = fmaf(T.Dhatf[b][0], fc.x, t);
+            t = fmaf(T.Dhatf[b][1], fc.y, t);
+            t = fmaf(T.Dhatf[b][2], fc.z, t);
+            t = fmaf(T.Dhatf[b][3], fc.w, t);
+            vx[c] = s;
             vy[c] = t;
+        } else {
+            float s = 0.0f;
+#pragma unroll
+            for (int q = 0; q < N; ++q) s = fmaf(T.Dhatf[a][q], S.f[0][c][lc][b * N + q], s);
+            vx[c] = s;
+            if constexpr (DIM == 2) {
+                float t = 0.0f;
+#pragma unroll
+                for (int r = 0; r < N; ++r) t = fmaf(T.Dhatf[b][r], S.f[1][c][lc][r * N + a], t);
+                vy[c] = t;
+            }
         }
     }
 #pragma unroll
@@ -255,7 +310,14 @@ __device__ void eval_G_x(const Params &P, SmemX<C> &S, int lc, int node, const f
 #pragma unroll
             for (int c = 0; c < M; ++c) {
                 float s = 0.0f;
-                if (DIM == 1 || face < 2) {
+                if constexpr (vec4<C>()) {  // row pos (x faces) or column pos (y faces) as a float4
+                    const float4 r = *reinterpret_cast<const float4 *>(face < 2 ? &S.u[c][lc][pos * N]
+                                                                                : &S.uT[c][lc][pos * N]);
+                    s = fmaf(l[0], r.x, s);
+                    s = fmaf(l[1], r.y, s);
+                    s = fmaf(l[2], r.z, s);
+                    s = fmaf(l[3], r.w, s);
+                } else if (DIM == 1 || face < 2) {
 #pragma unroll
                     for (int q = 0; q < N; ++q) s = fmaf(l[q], S.u[c][lc][pos * N + q], s);
                 } else {
@@ -336,7 +398,7 @@ template <class C>
 __device__ __forceinline__ void eval64_x(SmemX<C> &S, int lc, int p, const double *ub, double *v, float *v32) {
     constexpr int M = C::M;
     float s[M];
-    sk_eval_f<C::D, C::NP, M, C::NN>(&S.u[0][lc][0], C::NCB * C::NN, p, s);
+    sk_eval_f<C::D, C::NP, M, C::NN>(&S.u[0][lc][0], vec4<C>() ? &S.uT[0][lc][0] : nullptr, C::NCB * C::NN, p, s);
 #pragma unroll
     for (int c = 0; c < M; ++c) {
         float d = s[c] - S.mean[lc][c];
@@ -353,6 +415,7 @@ __device__ __forceinline__ void publish_dev(const double *ub, const float *dv, S
 #pragma unroll
     for (int c = 0; c < M; ++c) {
         S.u[c][lc][node] = dv[c];
+        if constexpr (vec4<C>()) S.uT[c][lc][(node % 4) * 4 + node / 4] = dv[c];
         S.w[c][lc][node] = wnode_f<C::D, C::NP>(node) * dv[c];
     }
     __syncthreads();
@@ -380,7 +443,7 @@ __device__ void limit_x(const Params &P, const Bufs &B, SmemX<C> &S, int lc, int
         int p = node + j * NN;
         if (p < NSK) {
             float s[M];
-            sk_eval_f<DIM, C::NP, M, NN>(&S.u[0][lc][0], C::NCB * C::NN, p, s);
+            sk_eval_f<DIM, C::NP, M, NN>(&S.u[0][lc][0], vec4<C>() ? &S.uT[0][lc][0] : nullptr, C::NCB * C::NN, p, s);
 #pragma unroll
             for (int c = 0; c < M; ++c) {
                 float d = s[c] - S.mean[lc][c];
