@@ -45,6 +45,8 @@ WORKLOADS = {
     "riemann_1024_q2_mixed": dict(kind="riemann", nx=1024, k=2, precision="mixed"),
     "riemann_1024_q2_tvb": dict(kind="riemann", nx=1024, k=2, indicator="tvb"),
     "riemann_1024_q2_mlp": dict(kind="riemann", nx=1024, k=2, indicator="mlp"),
+    "riemann_1024_q2_mixed_tvb": dict(kind="riemann", nx=1024, k=2, precision="mixed", indicator="tvb"),
+    "riemann_1024_q2_mixed_mlp": dict(kind="riemann", nx=1024, k=2, precision="mixed", indicator="mlp"),
     "ensemble_64_riemann_mlp": dict(kind="ensemble", count=64, indicator="mlp"),
 }
 DEFAULT = "euler1d_blast_tube_4096_p2"

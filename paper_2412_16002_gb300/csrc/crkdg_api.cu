@@ -259,6 +259,9 @@ MixBufs base_xbufs(const crkdg_ctx *h) {
     X.a0 = &h->scal->a0;
     X.ord = h->scal->ord;
     X.aux = h->aux;
+    X.tflags = h->tflags;
+    X.prob = h->prob;
+    X.ntrb = &h->scal->ntrb;
     return X;
 }
 
@@ -409,7 +412,9 @@ crkdg_status crkdg_create(const crkdg_mesh *mesh, int k, int m, const crkdg_flux
     if (o.max_halvings < 0 || o.max_halvings > 60) return CRKDG_E_ARG;
     if (o.precision != CRKDG_PREC_FP64 && o.precision != CRKDG_PREC_MIXED) return CRKDG_E_ARG;
     if (o.indicator < CRKDG_IND_OFF || o.indicator > CRKDG_IND_MLP || !(o.tvb_M >= 0.0)) return CRKDG_E_ARG;
-    if (o.indicator != CRKDG_IND_OFF && (o.precision != CRKDG_PREC_FP64 || flux->kind != CRKDG_FLUX_EULER))
+    if (o.indicator != CRKDG_IND_OFF && flux->kind != CRKDG_FLUX_EULER) return CRKDG_E_UNSUPPORTED;
+    // with split precision the indicators run on 2D meshes (their decisions use the FP64 feature kernel)
+    if (o.indicator != CRKDG_IND_OFF && o.precision == CRKDG_PREC_MIXED && mesh->dim != 2)
         return CRKDG_E_UNSUPPORTED;
     if (o.indicator == CRKDG_IND_MLP && mesh->dim != 2) return CRKDG_E_UNSUPPORTED;
 
@@ -648,6 +653,25 @@ crkdg_status crkdg_step(crkdg_t h, double dt, const crkdg_tableau *tab, crkdg_st
             if (h->prof) CK(h, cudaEventRecord(h->ev[1], h->st));
             if (h->mixed) {
                 CK(h, launch_x(h, KX_FINAL, P, base_xbufs(h)));
+                if (ind) {
+                    // the unlimited u^{n+1} as FP64 nodal values and averages, the plain decision
+                    // and features by the FP64 feature kernel, then the split troubled-cell pass
+                    const bool learned = h->opt.indicator == CRKDG_IND_MLP;
+                    MixBufs Xn = base_xbufs(h);
+                    Xn.ub = h->xub[1 - h->xcur];
+                    Xn.dv = h->xdv[1 - h->xcur];
+                    Xn.nod_out = h->unew;
+                    CK(h, launch_x(h, KX_MERGE, P, Xn));
+                    CK(h, launch_x(h, KX_AVG, P, Xn));
+                    Bufs Bf = base_bufs(h);
+                    Bf.unew = h->unew;
+                    CK(h, launch(h, K_FEATURES, P, Bf));
+                    if (learned && crkdg_mlp_forward(h->mlp, h->feat, h->ncell, h->prob, h->st) != CRKDG_OK)
+                        return fail(h, CRKDG_E_CUDA, "step: MLP forward failed");
+                    P.ind_stage = learned ? 3 : 2;
+                    CK(h, launch_x(h, KX_TROUBLE, P, base_xbufs(h)));
+                    P.ind_stage = 0;
+                }
             } else {
                 CK(h, launch(h, K_FINAL, P, B));
                 if (ind) {

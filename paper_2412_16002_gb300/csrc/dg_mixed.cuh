@@ -863,6 +863,16 @@ __global__ void __launch_bounds__(C::NT, (C::NT > 128 ? 2 : 4)) k_final_x(Params
     const float fdt = P.f.dt;
 #pragma unroll
     for (int c = 0; c < M; ++c) dvn[c] = fmaf(fdt, corr[c] - S.mean[lc][c], dvs[c]);
+    if (P.defer_limit) {  // the troubled-cell kernel limits; the averages' admissibility is tested here
+        if (node == 0 && active && !screen_ok<PHYS, DIM>(P, S.ubf[lc], S.ubf[lc]) && !admissible<PHYS, DIM>(P, S.ubd[lc]))
+            atomicOr(B.flag, 1);
+        if (active) {
+            for (int c = node; c < M; c += NN) X.ub_n[(size_t)c * P.ncell + cell] = S.ubd[lc][c];
+#pragma unroll
+            for (int c = 0; c < M; ++c) X.dv_n[((size_t)c * P.ncell + cell) * NN + node] = dvn[c];
+        }
+        return;
+    }
     float pts[C::PPT][M];
     limit_x(P, B, S, lc, node, active, S.ubd[lc], dvn, true, true, pts);
     double ubn[M];
@@ -887,6 +897,109 @@ __global__ void __launch_bounds__(C::NT, (C::NT > 128 ? 2 : 4)) k_final_x(Params
 #pragma unroll
         for (int c = 0; c < M; ++c) X.dv_n[((size_t)c * P.ncell + cell) * NN + node] = dvn[c];
     }
+}
+
+// Shock limiter of the flagged cells and the scaling limiter, on the split state of
+// u^{n+1} (X.ub, X.dv, rewritten in place): the plain indicator's flags are in tflags
+// (ind_stage 2) or are combined with the learned probabilities (ind_stage 3: p > 0.6
+// troubled, p < 0.4 smooth).  A troubled cell keeps its FP64 average and becomes
+// ubar + minmod(c_x, D+x, D-x) xi + minmod(c_y, D+y, D-y) eta, the moments c_x, c_y taken
+// in FP64 from ubar + (dev - dbar) and the neighbour averages from aux (as the FP64
+// troubled-cell kernel); the deviations are then the FP32 values of that linear part.
+// Then the scaling limiter and the trial-step rate.
+template <class C>
+__global__ void __launch_bounds__(C::NT) k_trouble_x(Params P, MixBufs X) {
+    constexpr int DIM = C::D, N = C::NP, PHYS = C::PH, M = C::M, NN = C::NN;
+    __shared__ SmemX<C> S;
+    __shared__ double sP1[C::NCB][2][M];
+    const NodalTables &T = c_tab[N - 2];
+    const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
+    const int cell = blockIdx.x * C::NCB + lc;
+    const bool active = cell < P.ncell;
+    const int a = node % N, b = DIM == 2 ? node / N : 0;
+    Bufs B = scal_of<C>(X);
+    double ub[M];
+    float dv[M];
+    {
+        MixBufs Y = X;
+        Y.ub = X.ub_n;
+        Y.dv = X.dv_n;
+        load_x<C>(P, Y, cell, node, active, ub, dv);
+    }
+    for (int c = node; c < M; c += NN) {
+        S.ubd[lc][c] = ub[c];
+        S.ubf[lc][c] = (float)ub[c];
+    }
+    __syncthreads();
+    publish_dev(ub, dv, S, lc, node);
+    bool troubled = active && X.tflags[cell] != 0;
+    if (P.ind_stage == 3 && active) {
+        const float pr = X.prob[cell];
+        troubled = pr > 0.6f ? true : (pr < 0.4f ? false : troubled);
+    }
+    if (node == 0 && active) {
+        if (P.ind_stage == 3) X.tflags[cell] = troubled ? 1 : 0;
+        if (troubled) atomicAdd(X.ntrb, 1ull);
+    }
+    if (node < DIM && active) {  // thread d: limited first moments in direction d
+        const int d = node;
+        double own[M], lo[M], hi[M];
+#pragma unroll
+        for (int c = 0; c < M; ++c) own[c] = X.aux[(size_t)cell * M + c];
+        int nl = neighbour(P, cell, 2 * d), nh = neighbour(P, cell, 2 * d + 1);
+        if (nl >= 0) {
+#pragma unroll
+            for (int c = 0; c < M; ++c) lo[c] = X.aux[(size_t)nl * M + c];
+        } else {
+            boundary_state<PHYS, DIM>(P, 2 * d, own, lo);
+        }
+        if (nh >= 0) {
+#pragma unroll
+            for (int c = 0; c < M; ++c) hi[c] = X.aux[(size_t)nh * M + c];
+        } else {
+            boundary_state<PHYS, DIM>(P, 2 * d + 1, own, hi);
+        }
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            double p1 = 0.0;
+            for (int q = 0; q < NN; ++q) {
+                int qa = q % N, qb = DIM == 2 ? q / N : 0;
+                int along = d == 0 ? qa : qb;
+                double v = ub[c] + (double)(S.u[c][lc][q] - S.mean[lc][c]);
+                p1 = fma(3.0 * T.w1[qa] * (DIM == 2 ? T.w1[qb] : 1.0) * T.xg[along], v, p1);
+            }
+            double dp = hi[c] - own[c], dm = own[c] - lo[c];
+            sP1[lc][d][c] = minmod3d(p1, dp, dm);
+        }
+    }
+    __syncthreads();
+    if (troubled) {
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            double v = sP1[lc][0][c] * T.xg[a];
+            if constexpr (DIM == 2) v = fma(sP1[lc][1][c], T.xg[b], v);
+            dv[c] = (float)v;
+        }
+    }
+    float pts[C::PPT][M];
+    limit_x(P, B, S, lc, node, active, S.ubd[lc], dv, false, true, pts);
+    const float rhx = P.f.rhx, rhy = P.f.rhy;
+    float amax = 0.0f;
+#pragma unroll
+    for (int j = 0; j < C::PPT; ++j) {
+        int p = node + j * NN;
+        if (p < C::NSK && active) {
+            float r = speed_dir_f<PHYS, DIM>(P, pts[j], 0) * (0.5f * rhx);
+            if constexpr (DIM == 2) r = fmaf(speed_dir_f<PHYS, DIM>(P, pts[j], 1), 0.5f * rhy, r);
+            amax = fmaxf(amax, r);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if ((threadIdx.x & 31) == 0 && amax > 0.0f) atomicMax(X.a0, dbits((double)amax * (1.0 + 9.5367431640625e-07)));
+    if (active)
+#pragma unroll
+        for (int c = 0; c < M; ++c) X.dv_n[((size_t)c * P.ncell + cell) * NN + node] = dv[c];
 }
 
 // FP64 nodal -> (ubar, dev), then (optionally) the limiter.
@@ -1032,6 +1145,7 @@ cudaError_t launch_one_x(int kernel, int nblocks, cudaStream_t st, const Params 
     case KX_INNER: k_inner_x<C><<<nblocks, C::NT, 0, st>>>(P, X); break;
     case KX_FINAL: k_final_x<C><<<nblocks, C::NT, 0, st>>>(P, X); break;
     case KX_SCAN: k_scan_x<C><<<nblocks, C::NT, 0, st>>>(P, X); break;
+    case KX_TROUBLE: k_trouble_x<C><<<nblocks, C::NT, 0, st>>>(P, X); break;
     case KX_AVG: {
         int tot = P.ncell * C::M;
         k_avg_x<C><<<(tot + 255) / 256, 256, 0, st>>>(P, X);

@@ -118,9 +118,13 @@ struct MixBufs {
     int *flag;
     unsigned long long *nlim, *thmin, *a0, *ord;
     double *aux;
+    int *tflags;              // troubled-cell flags (indicator on)
+    const float *prob;        // learned probabilities (ind_stage 3)
+    unsigned long long *ntrb; // troubled cells
 };
 
-enum MixKernelId { KX_SPLIT = 0, KX_MERGE = 1, KX_LIMIT = 2, KX_INNER = 3, KX_FINAL = 4, KX_SCAN = 5, KX_AVG = 6 };
+enum MixKernelId { KX_SPLIT = 0, KX_MERGE = 1, KX_LIMIT = 2, KX_INNER = 3, KX_FINAL = 4, KX_SCAN = 5, KX_AVG = 6,
+                   KX_TROUBLE = 7 };
 
 // ---------------------------------------------------------------- ensembles (2D Euler)
 

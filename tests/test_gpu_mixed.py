@@ -130,3 +130,107 @@ def test_mixed_shock_workloads(name, cmp_step):
     if name.startswith("sedov"):
         for c in (0, 3):
             assert abs(g.mass(c) - m0[c]) <= 1e-13 * abs(m0[c])
+
+
+def _riemann_pair(precision, indicator, seed=2, n=48, **kw):
+    from paper_2412_16002_gb300.solver import Solver
+
+    wl = inputs.riemann_quadrants(seed, n, 2)
+    g = Solver.from_workload(wl, precision=precision, indicator=indicator, **kw)
+    g.set_state(wl.state)
+    return g, wl
+
+
+def test_mixed_tvb_indicator_invariants_and_fp64_agreement():
+    """Split precision with the plain indicator (four-quadrant Riemann 48^2, Q^2, 20 steps at
+    the FP64 run's trial steps): bounds exact every step, the flags agree with the FP64 path's
+    in at least 99% of the cell-steps (the decisions are FP64 on states that differ by FP32
+    rounding), and the relative L1 gap to the FP64 path stays below 1e-3."""
+    gm, wl = _riemann_pair("mixed", "tvb", tvb_M=10.0)
+    gf, _ = _riemann_pair("fp64", "tvb", tvb_M=10.0)
+    agree = total = flagged = 0
+    for _ in range(20):
+        dt = gf.max_dt(wl.cfl)
+        im = gm.step(dt, wl.tableau)
+        gf.step(dt, wl.tableau)
+        fm, ff = gm.troubled_flags(), gf.troubled_flags()
+        agree += int((fm == ff).sum())
+        total += fm.size
+        flagged += int(ff.sum())
+        assert im["troubled"] == int(fm.sum())
+        assert gm.margins().min() >= 0.0
+    assert flagged > 0 and agree >= 0.99 * total, (agree, total)
+    gap = _rel_l1(gm.get_state(), gf.get_state(), 4)
+    print(f"split + TVB against FP64 + TVB after 20 steps: L1 gap {gap:.3e}, flag agreement {agree / total:.5f}")
+    assert gap < 1e-3
+
+
+def test_mixed_learned_with_undecided_network_is_the_plain_indicator():
+    """A network with zero parameters outputs p = 0.5 for every cell, which the learned rule
+    leaves to the plain decision: the split-precision learned path then reproduces the
+    split-precision TVB path bit for bit, flags included."""
+    ga, wl = _riemann_pair("mixed", "tvb", tvb_M=10.0)
+    gb, _ = _riemann_pair("mixed", "mlp", tvb_M=10.0)
+    gb.set_mlp(torch.zeros(7105, dtype=torch.float32, device="cuda"))
+    for _ in range(10):
+        dt = ga.max_dt(wl.cfl)
+        ia = ga.step(dt, wl.tableau)
+        ib = gb.step(dt, wl.tableau)
+        assert ia["troubled"] == ib["troubled"] and ia["restarts"] == ib["restarts"]
+        assert np.array_equal(ga.troubled_flags(), gb.troubled_flags())
+    assert np.array_equal(ga.get_state(), gb.get_state())
+
+
+def test_mixed_tvb_conserves_the_blast():
+    """Sedov-type blast (reflecting and outflow sides, not reached), Q^3, split precision with
+    the plain indicator: the shock limiter keeps the FP64 averages, so mass and energy are
+    conserved to FP64 round-off; bounds hold every step."""
+    from paper_2412_16002_gb300.solver import Solver
+
+    wl = inputs.sedov(32, 3)
+    g = Solver.from_workload(wl, precision="mixed", indicator="tvb", tvb_M=10.0)
+    g.set_state(wl.state)
+    m0 = [g.mass(c) for c in (0, 3)]
+    troubled = 0
+    for _ in range(20):
+        info = g.step(g.max_dt(wl.cfl), wl.tableau)
+        troubled += info["troubled"]
+        assert g.margins().min() >= 0.0
+    assert troubled > 0
+    for c, m in zip((0, 3), m0):
+        assert abs(g.mass(c) - m) <= 1e-13 * abs(m)
+
+
+@pytest.mark.parametrize("seed,n,k,M", [(4, 32, 2, 1.0), (5, 24, 3, 10.0)])
+def test_mixed_tvb_indicator_against_oracle(seed, n, k, M):
+    """Split precision with the plain indicator against the FP64 oracle with the same
+    indicator, five steps at the oracle's trial steps: the flags are FP64 decisions on states
+    that differ by FP32 rounding, so at most 0.5% of them may differ; the states agree to 1e-5
+    relative L1 and the bounds hold exactly."""
+    from paper_2412_16002_gb300.solver import Solver
+
+    wl = inputs.riemann_quadrants(seed, n, k)
+    g = Solver.from_workload(wl, precision="mixed", indicator="tvb", tvb_M=M)
+    o = Oracle(wl.dim, wl.nx, wl.ny, wl.k, wl.domain, wl.flux, gamma=wl.gamma, eps=wl.eps, bc=wl.bc,
+               bc_state=wl.bc_state, indicator=True, tvb_M=M)
+    g.set_state(wl.state)
+    o.set_state(wl.state)
+    t = 0.0
+    flagged = differ = 0
+    for step in range(5):
+        dt = o.max_dt(wl.cfl)
+        ig = g.step(dt, wl.tableau)
+        before = o.c.copy()
+        rc, io = o.step(dt, ORACLE_TABS[wl.tableau], t)
+        assert rc == 0 and ig["restarts"] == io["restarts"] == 0
+        rc2, us, _ = o.step_stages(dt, ORACLE_TABS[wl.tableau], t, modal=before)
+        fo, fg = o.troubled(us[-1]), g.troubled_flags()
+        flagged += int(fo.sum())
+        differ += int((fo != fg).sum())
+        assert ig["troubled"] == int(fg.sum())
+        assert g.margins().min() >= 0.0
+        t += dt
+    gap = _rel_l1(g.get_state(), o.get_state(), o.m)
+    print(f"riemann{n}_q{k} split + TVB: {flagged} oracle flags, {differ} differ; L1 gap {gap:.3e}")
+    assert flagged > 0 and differ <= 0.005 * 5 * n * n
+    assert gap < 1e-5
