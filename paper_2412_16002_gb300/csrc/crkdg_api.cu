@@ -413,9 +413,6 @@ crkdg_status crkdg_create(const crkdg_mesh *mesh, int k, int m, const crkdg_flux
     if (o.precision != CRKDG_PREC_FP64 && o.precision != CRKDG_PREC_MIXED) return CRKDG_E_ARG;
     if (o.indicator < CRKDG_IND_OFF || o.indicator > CRKDG_IND_MLP || !(o.tvb_M >= 0.0)) return CRKDG_E_ARG;
     if (o.indicator != CRKDG_IND_OFF && flux->kind != CRKDG_FLUX_EULER) return CRKDG_E_UNSUPPORTED;
-    // with split precision the indicators run on 2D meshes (their decisions use the FP64 feature kernel)
-    if (o.indicator != CRKDG_IND_OFF && o.precision == CRKDG_PREC_MIXED && mesh->dim != 2)
-        return CRKDG_E_UNSUPPORTED;
     if (o.indicator == CRKDG_IND_MLP && mesh->dim != 2) return CRKDG_E_UNSUPPORTED;
 
     crkdg_ctx *h = new (std::nothrow) crkdg_ctx();
@@ -654,21 +651,25 @@ crkdg_status crkdg_step(crkdg_t h, double dt, const crkdg_tableau *tab, crkdg_st
             if (h->mixed) {
                 CK(h, launch_x(h, KX_FINAL, P, base_xbufs(h)));
                 if (ind) {
-                    // the unlimited u^{n+1} as FP64 nodal values and averages, the plain decision
-                    // and features by the FP64 feature kernel, then the split troubled-cell pass
+                    // the final stage left the unlimited u^{n+1} and its averages (aux); the plain
+                    // decision is taken in the troubled-cell pass, unless features are wanted:
+                    // then the FP64 feature kernel takes it on the merged nodal values
                     const bool learned = h->opt.indicator == CRKDG_IND_MLP;
-                    MixBufs Xn = base_xbufs(h);
-                    Xn.ub = h->xub[1 - h->xcur];
-                    Xn.dv = h->xdv[1 - h->xcur];
-                    Xn.nod_out = h->unew;
-                    CK(h, launch_x(h, KX_MERGE, P, Xn));
-                    CK(h, launch_x(h, KX_AVG, P, Xn));
-                    Bufs Bf = base_bufs(h);
-                    Bf.unew = h->unew;
-                    CK(h, launch(h, K_FEATURES, P, Bf));
-                    if (learned && crkdg_mlp_forward(h->mlp, h->feat, h->ncell, h->prob, h->st) != CRKDG_OK)
-                        return fail(h, CRKDG_E_CUDA, "step: MLP forward failed");
-                    P.ind_stage = learned ? 3 : 2;
+                    if (learned || h->harvest) {
+                        MixBufs Xn = base_xbufs(h);
+                        Xn.ub = h->xub[1 - h->xcur];
+                        Xn.dv = h->xdv[1 - h->xcur];
+                        Xn.nod_out = h->unew;
+                        CK(h, launch_x(h, KX_MERGE, P, Xn));
+                        Bufs Bf = base_bufs(h);
+                        Bf.unew = h->unew;
+                        CK(h, launch(h, K_FEATURES, P, Bf));
+                        if (learned && crkdg_mlp_forward(h->mlp, h->feat, h->ncell, h->prob, h->st) != CRKDG_OK)
+                            return fail(h, CRKDG_E_CUDA, "step: MLP forward failed");
+                        P.ind_stage = learned ? 3 : 2;
+                    } else {
+                        P.ind_stage = 0;
+                    }
                     CK(h, launch_x(h, KX_TROUBLE, P, base_xbufs(h)));
                     P.ind_stage = 0;
                 }

@@ -824,6 +824,21 @@ __device__ __forceinline__ double minmod3d(double a, double b, double c) {
     return 0.0;
 }
 
+// Average of component c of the neighbour of `cell` across `side` (the averages are in
+// aux, [cell][m]); across a domain boundary, the boundary condition applied to the
+// cell's own average.
+template <int PHYS, int DIM>
+__device__ __forceinline__ double nb_average(const Params &P, const double *aux, int cell, int side, int c) {
+    constexpr int M = ncomp(PHYS, DIM);
+    const int nb = neighbour(P, cell, side);
+    if (nb >= 0) return aux[(size_t)nb * M + c];
+    double own[M], ext[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) own[i] = aux[(size_t)cell * M + i];
+    boundary_state<PHYS, DIM>(P, side, own, ext);
+    return ext[c];
+}
+
 // Plain troubled-cell indicator and shock limiter, then the scaling limiter (an
 // optional anti-oscillation stage outside the paper's method, run once per step
 // after the final stage so the inner stages stay compact).  Per component and
@@ -851,47 +866,31 @@ __device__ __forceinline__ void trouble_body(const Params &P, const Bufs &B, int
     for (int c = 0; c < M; ++c) S.u[lc][c][node] = u[c];
     if (node == 0) sTr[lc] = 0;
     __syncthreads();
-    if (node < DIM && active) {  // thread d handles direction d for every component (decision and limited slopes)
-        const int d = node;
+    // the (direction, component) pairs are spread over the cell's threads: each takes the
+    // decision and the limited first moment of its pairs
+    for (int j = node; j < DIM * M && active; j += NN) {
+        const int d = j / M, c = j - d * M;
         const double h = 2.0 / (d == 0 ? P.rhx : P.rhy);
         const double thr = P.tvb_M * h * h;
-        double own[M], lo[M], hi[M];
-#pragma unroll
-        for (int c = 0; c < M; ++c) own[c] = B.aux[(size_t)cell * M + c];
-        int nl = neighbour(P, cell, 2 * d), nh = neighbour(P, cell, 2 * d + 1);
-        if (nl >= 0) {
-#pragma unroll
-            for (int c = 0; c < M; ++c) lo[c] = B.aux[(size_t)nl * M + c];
-        } else {
-            boundary_state<PHYS, DIM>(P, 2 * d, own, lo);
+        const double own = B.aux[(size_t)cell * M + c];
+        const double lo = nb_average<PHYS, DIM>(P, B.aux, cell, 2 * d, c);
+        const double hi = nb_average<PHYS, DIM>(P, B.aux, cell, 2 * d + 1, c);
+        double fr = 0.0, fl = 0.0, p1 = 0.0;
+        for (int q = 0; q < NN; ++q) {
+            int qa = q % N, qb = DIM == 2 ? q / N : 0;
+            int along = d == 0 ? qa : qb, across = d == 0 ? qb : qa;
+            double wa = DIM == 2 ? T.w1[across] : 1.0;
+            double v = S.u[lc][c][q];
+            fr = fma(wa * T.lp[along], v, fr);
+            fl = fma(wa * T.lm[along], v, fl);
+            p1 = fma(3.0 * T.w1[qa] * (DIM == 2 ? T.w1[qb] : 1.0) * T.xg[along], v, p1);
         }
-        if (nh >= 0) {
-#pragma unroll
-            for (int c = 0; c < M; ++c) hi[c] = B.aux[(size_t)nh * M + c];
-        } else {
-            boundary_state<PHYS, DIM>(P, 2 * d + 1, own, hi);
-        }
-        int trouble = 0;
-#pragma unroll
-        for (int c = 0; c < M; ++c) {
-            double fr = 0.0, fl = 0.0, p1 = 0.0;
-            for (int q = 0; q < NN; ++q) {
-                int qa = q % N, qb = DIM == 2 ? q / N : 0;
-                int along = d == 0 ? qa : qb, across = d == 0 ? qb : qa;
-                double wa = DIM == 2 ? T.w1[across] : 1.0;
-                double v = S.u[lc][c][q];
-                fr = fma(wa * T.lp[along], v, fr);
-                fl = fma(wa * T.lm[along], v, fl);
-                p1 = fma(3.0 * T.w1[qa] * (DIM == 2 ? T.w1[qb] : 1.0) * T.xg[along], v, p1);
-            }
-            double utR = fr - own[c], utL = own[c] - fl;
-            double dp = hi[c] - own[c], dm = own[c] - lo[c];
-            double mR = fabs(utR) <= thr ? utR : minmod3d(utR, dp, dm);
-            double mL = fabs(utL) <= thr ? utL : minmod3d(utL, dp, dm);
-            if (mR != utR || mL != utL) trouble = 1;
-            sP1[lc][d][c] = minmod3d(p1, dp, dm);
-        }
-        if (trouble) atomicOr(&sTr[lc], 1);
+        double utR = fr - own, utL = own - fl;
+        double dp = hi - own, dm = own - lo;
+        double mR = fabs(utR) <= thr ? utR : minmod3d(utR, dp, dm);
+        double mL = fabs(utL) <= thr ? utL : minmod3d(utL, dp, dm);
+        if (mR != utR || mL != utL) atomicOr(&sTr[lc], 1);
+        sP1[lc][d][c] = minmod3d(p1, dp, dm);
     }
     __syncthreads();
     bool troubled = active && (P.ind_stage >= 2 ? B.tflags[cell] != 0 : sTr[lc] != 0);

@@ -863,11 +863,15 @@ __global__ void __launch_bounds__(C::NT, (C::NT > 128 ? 2 : 4)) k_final_x(Params
     const float fdt = P.f.dt;
 #pragma unroll
     for (int c = 0; c < M; ++c) dvn[c] = fmaf(fdt, corr[c] - S.mean[lc][c], dvs[c]);
-    if (P.defer_limit) {  // the troubled-cell kernel limits; the averages' admissibility is tested here
+    if (P.defer_limit) {  // the troubled-cell kernel limits; the averages' admissibility is tested here,
+                          // the new averages also go to aux for the indicator
         if (node == 0 && active && !screen_ok<PHYS, DIM>(P, S.ubf[lc], S.ubf[lc]) && !admissible<PHYS, DIM>(P, S.ubd[lc]))
             atomicOr(B.flag, 1);
         if (active) {
-            for (int c = node; c < M; c += NN) X.ub_n[(size_t)c * P.ncell + cell] = S.ubd[lc][c];
+            for (int c = node; c < M; c += NN) {
+                X.ub_n[(size_t)c * P.ncell + cell] = S.ubd[lc][c];
+                X.aux[(size_t)cell * M + c] = S.ubd[lc][c];
+            }
 #pragma unroll
             for (int c = 0; c < M; ++c) X.dv_n[((size_t)c * P.ncell + cell) * NN + node] = dvn[c];
         }
@@ -899,19 +903,49 @@ __global__ void __launch_bounds__(C::NT, (C::NT > 128 ? 2 : 4)) k_final_x(Params
     }
 }
 
-// Shock limiter of the flagged cells and the scaling limiter, on the split state of
-// u^{n+1} (X.ub, X.dv, rewritten in place): the plain indicator's flags are in tflags
-// (ind_stage 2) or are combined with the learned probabilities (ind_stage 3: p > 0.6
-// troubled, p < 0.4 smooth).  A troubled cell keeps its FP64 average and becomes
-// ubar + minmod(c_x, D+x, D-x) xi + minmod(c_y, D+y, D-y) eta, the moments c_x, c_y taken
-// in FP64 from ubar + (dev - dbar) and the neighbour averages from aux (as the FP64
-// troubled-cell kernel); the deviations are then the FP32 values of that linear part.
-// Then the scaling limiter and the trial-step rate.
+// FP32 screen of the plain indicator's decision for one face-averaged trace deviation
+// t, given an FP32 estimate s with |s - t| <= E, the threshold thr and the differences
+// of the averages dp, dm (FP32 roundings of FP64 values; sdp, sdm their exact signs).
+// The cell keeps t (not troubled) iff |t| <= thr, or t, dp, dm share one sign and
+// |t| <= min(|dp|, |dm|).  Every comparison is taken only when it clears the margin
+// E + 2^-20 (|x| + |y|), which covers the roundings of thr, dp, dm and of the FP32
+// comparisons themselves.  Returns 0 (kept), 1 (troubled) or 2 (undecided).
+__device__ __forceinline__ int tvb_screen(float s, float E, float thr, float dp, float dm, int sdp, int sdm) {
+    const float as = fabsf(s);
+    const float m1 = E + 9.5367431640625e-07f * (as + thr) + 1e-37f;
+    if (thr - as > m1) return 0;
+    if (!(as - thr > m1)) return 2;
+    // |t| > thr >= 0, so t != 0 and has the sign of s
+    const int ss = s > 0.0f ? 1 : -1;
+    if (sdp != ss || sdm != ss) return 1;
+    const float adp = fabsf(dp), adm = fabsf(dm);
+    const float m2 = E + 9.5367431640625e-07f * (as + fmaxf(adp, adm)) + 1e-37f;
+    if (as - adp > m2 || as - adm > m2) return 1;
+    if (adp - as > m2 && adm - as > m2) return 0;
+    return 2;
+}
+
+// Troubled-cell pass of the split representation, on the unlimited u^{n+1} (X.ub_n,
+// X.dv_n, rewritten in place) with its averages in aux.  The decision is the plain
+// indicator's (ind_stage 0: taken here; 2: read from tflags; 3: combined with the
+// learned probabilities, p > 0.6 troubled, p < 0.4 smooth).  Taken here, it is the FP64
+// decision on the merged nodal values ubar + (double)(dev - dbar): the face-averaged
+// trace deviations are estimated in FP32 from the deviations alone (the average
+// cancels in them), with the bound
+//   |s - t| <= (n_nodes + 6) 2^-24 sum_q |W_q| |dev_q| + 2^-43 (1 + sum_q |W_q|) (|ubar| + max_q |dev_q|),
+// the first term the FP32 weights and dot product, the second the FP64 evaluation
+// (merge rounding, dot product, sum of the weights vs 1); a pair the screen cannot
+// decide is evaluated in FP64 exactly as on the merged values.  A troubled cell keeps
+// its FP64 average and becomes ubar + minmod(c_x, D+x, D-x) xi + minmod(c_y, D+y, D-y) eta,
+// its moments c_x, c_y in FP64 from the merged values; the deviations become the FP32
+// values of that linear part.  Then the scaling limiter and the trial-step rate.
 template <class C>
 __global__ void __launch_bounds__(C::NT) k_trouble_x(Params P, MixBufs X) {
     constexpr int DIM = C::D, N = C::NP, PHYS = C::PH, M = C::M, NN = C::NN;
     __shared__ SmemX<C> S;
-    __shared__ double sP1[C::NCB][2][M];
+    __shared__ double sP1[C::NCB][DIM][M];
+    __shared__ double sD[C::NCB][DIM][M][2];
+    __shared__ int sTr[C::NCB];
     const NodalTables &T = c_tab[N - 2];
     const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
     const int cell = blockIdx.x * C::NCB + lc;
@@ -930,46 +964,86 @@ __global__ void __launch_bounds__(C::NT) k_trouble_x(Params P, MixBufs X) {
         S.ubd[lc][c] = ub[c];
         S.ubf[lc][c] = (float)ub[c];
     }
-    __syncthreads();
+    if (node == 0) sTr[lc] = 0;
     publish_dev(ub, dv, S, lc, node);
-    bool troubled = active && X.tflags[cell] != 0;
+    // (direction, component) pairs spread over the cell's threads
+    for (int j = node; j < DIM * M && active; j += NN) {
+        const int d = j / M, c = j - d * M;
+        const double own = S.ubd[lc][c];
+        const double lo = nb_average<PHYS, DIM>(P, X.aux, cell, 2 * d, c);
+        const double hi = nb_average<PHYS, DIM>(P, X.aux, cell, 2 * d + 1, c);
+        const double dp = hi - own, dm = own - lo;
+        sD[lc][d][c][0] = dp;
+        sD[lc][d][c][1] = dm;
+        if (P.ind_stage != 0) continue;
+        const float mean = S.mean[lc][c];
+        float sR = 0.0f, sL = 0.0f, bR = 0.0f, bL = 0.0f, aR = 0.0f, aL = 0.0f, dmax = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NN; ++q) {
+            const int qa = q % N, qb = DIM == 2 ? q / N : 0;
+            const int along = d == 0 ? qa : qb, across = d == 0 ? qb : qa;
+            const float wa = DIM == 2 ? T.w1f[across] : 1.0f;
+            const float wr = wa * T.lpf[along], wl = wa * T.lmf[along];
+            const float e = S.u[c][lc][q] - mean;
+            sR = fmaf(wr, e, sR);
+            sL = fmaf(wl, e, sL);
+            bR = fmaf(fabsf(wr), fabsf(e), bR);
+            bL = fmaf(fabsf(wl), fabsf(e), bL);
+            aR += fabsf(wr);
+            aL += fabsf(wl);
+            dmax = fmaxf(dmax, fabsf(e));
+        }
+        const float base = fabsf(S.ubf[lc][c]) + dmax;
+        const float ER = 1.01f * (NN + 6) * 5.9604644775390625e-08f * bR + 1.1368683772161603e-13f * (1.01f + aR) * base;
+        const float EL = 1.01f * (NN + 6) * 5.9604644775390625e-08f * bL + 1.1368683772161603e-13f * (1.01f + aL) * base;
+        const double h = 2.0 / (d == 0 ? P.rhx : P.rhy);
+        const double thr = P.tvb_M * h * h;
+        const float thrf = (float)thr, dpf = (float)dp, dmf = (float)dm;
+        const int sdp = dp > 0.0 ? 1 : (dp < 0.0 ? -1 : 0), sdm = dm > 0.0 ? 1 : (dm < 0.0 ? -1 : 0);
+        // the left deviation is ubar - avg_face(u_L) = -(face-averaged dev)
+        const int rR = tvb_screen(sR, ER, thrf, dpf, dmf, sdp, sdm);
+        const int rL = tvb_screen(-sL, EL, thrf, dpf, dmf, sdp, sdm);
+        int trouble = (rR == 1 || rL == 1) ? 1 : 0;
+        if (!trouble && (rR == 2 || rL == 2)) {  // FP64 on the merged values
+            double fr = 0.0, fl = 0.0;
+            for (int q = 0; q < NN; ++q) {
+                const int qa = q % N, qb = DIM == 2 ? q / N : 0;
+                const int along = d == 0 ? qa : qb, across = d == 0 ? qb : qa;
+                const double wa = DIM == 2 ? T.w1[across] : 1.0;
+                const double v = own + (double)(S.u[c][lc][q] - mean);
+                fr = fma(wa * T.lp[along], v, fr);
+                fl = fma(wa * T.lm[along], v, fl);
+            }
+            const double utR = fr - own, utL = own - fl;
+            const double mR = fabs(utR) <= thr ? utR : minmod3d(utR, dp, dm);
+            const double mL = fabs(utL) <= thr ? utL : minmod3d(utL, dp, dm);
+            trouble = (mR != utR || mL != utL) ? 1 : 0;
+        }
+        if (trouble) atomicOr(&sTr[lc], 1);
+    }
+    __syncthreads();
+    bool troubled = active && (P.ind_stage == 0 ? sTr[lc] != 0 : X.tflags[cell] != 0);
     if (P.ind_stage == 3 && active) {
         const float pr = X.prob[cell];
         troubled = pr > 0.6f ? true : (pr < 0.4f ? false : troubled);
     }
     if (node == 0 && active) {
-        if (P.ind_stage == 3) X.tflags[cell] = troubled ? 1 : 0;
+        if (P.ind_stage != 2) X.tflags[cell] = troubled ? 1 : 0;
         if (troubled) atomicAdd(X.ntrb, 1ull);
     }
-    if (node < DIM && active) {  // thread d: limited first moments in direction d
-        const int d = node;
-        double own[M], lo[M], hi[M];
-#pragma unroll
-        for (int c = 0; c < M; ++c) own[c] = X.aux[(size_t)cell * M + c];
-        int nl = neighbour(P, cell, 2 * d), nh = neighbour(P, cell, 2 * d + 1);
-        if (nl >= 0) {
-#pragma unroll
-            for (int c = 0; c < M; ++c) lo[c] = X.aux[(size_t)nl * M + c];
-        } else {
-            boundary_state<PHYS, DIM>(P, 2 * d, own, lo);
-        }
-        if (nh >= 0) {
-#pragma unroll
-            for (int c = 0; c < M; ++c) hi[c] = X.aux[(size_t)nh * M + c];
-        } else {
-            boundary_state<PHYS, DIM>(P, 2 * d + 1, own, hi);
-        }
-#pragma unroll
-        for (int c = 0; c < M; ++c) {
+    if (troubled) {  // the same value for all threads of the cell
+        for (int j = node; j < DIM * M; j += NN) {
+            const int d = j / M, c = j - d * M;
+            const double own = S.ubd[lc][c];
+            const float mean = S.mean[lc][c];
             double p1 = 0.0;
             for (int q = 0; q < NN; ++q) {
-                int qa = q % N, qb = DIM == 2 ? q / N : 0;
-                int along = d == 0 ? qa : qb;
-                double v = ub[c] + (double)(S.u[c][lc][q] - S.mean[lc][c]);
+                const int qa = q % N, qb = DIM == 2 ? q / N : 0;
+                const int along = d == 0 ? qa : qb;
+                const double v = own + (double)(S.u[c][lc][q] - mean);
                 p1 = fma(3.0 * T.w1[qa] * (DIM == 2 ? T.w1[qb] : 1.0) * T.xg[along], v, p1);
             }
-            double dp = hi[c] - own[c], dm = own[c] - lo[c];
-            sP1[lc][d][c] = minmod3d(p1, dp, dm);
+            sP1[lc][d][c] = minmod3d(p1, sD[lc][d][c][0], sD[lc][d][c][1]);
         }
     }
     __syncthreads();

@@ -167,8 +167,9 @@ def test_mixed_tvb_indicator_invariants_and_fp64_agreement():
 
 def test_mixed_learned_with_undecided_network_is_the_plain_indicator():
     """A network with zero parameters outputs p = 0.5 for every cell, which the learned rule
-    leaves to the plain decision: the split-precision learned path then reproduces the
-    split-precision TVB path bit for bit, flags included."""
+    leaves to the plain decision: the split-precision learned path (decision by the FP64
+    feature kernel on the merged nodal values) then reproduces the split-precision TVB path
+    (decision by the FP32 screen of the troubled-cell pass) bit for bit, flags included."""
     ga, wl = _riemann_pair("mixed", "tvb", tvb_M=10.0)
     gb, _ = _riemann_pair("mixed", "mlp", tvb_M=10.0)
     gb.set_mlp(torch.zeros(7105, dtype=torch.float32, device="cuda"))
@@ -233,4 +234,59 @@ def test_mixed_tvb_indicator_against_oracle(seed, n, k, M):
     gap = _rel_l1(g.get_state(), o.get_state(), o.m)
     print(f"riemann{n}_q{k} split + TVB: {flagged} oracle flags, {differ} differ; L1 gap {gap:.3e}")
     assert flagged > 0 and differ <= 0.005 * 5 * n * n
+    assert gap < 1e-5
+
+
+@pytest.mark.parametrize("seed,n,k,M", [(3, 40, 2, 0.0), (3, 40, 2, 10.0), (6, 32, 3, 1.0)])
+def test_mixed_screened_decision_is_the_fp64_decision(seed, n, k, M):
+    """The split troubled-cell pass takes the plain decision from an FP32 screen of the
+    deviations with an FP64 fallback; with harvesting on, the FP64 feature kernel takes it on
+    the merged nodal values instead.  Both must give the same flags and the same states bit
+    for bit.  M = 0 leaves most decisions of the smooth and constant regions to the fallback
+    (trace deviations at rounding level against a zero threshold)."""
+    ga, wl = _riemann_pair("mixed", "tvb", seed=seed, n=n, tvb_M=M)
+    gb, _ = _riemann_pair("mixed", "tvb", seed=seed, n=n, tvb_M=M)
+    gb.set_harvest(True)
+    flagged = 0
+    for _ in range(12):
+        dt = ga.max_dt(wl.cfl)
+        ia = ga.step(dt, wl.tableau)
+        ib = gb.step(dt, wl.tableau)
+        fa, fb = ga.troubled_flags(), gb.troubled_flags()
+        assert np.array_equal(fa, fb), np.nonzero(fa != fb)
+        assert ia["troubled"] == ib["troubled"] == int(fa.sum())
+        flagged += int(fa.sum())
+    assert flagged > 0
+    assert np.array_equal(ga.get_state(), gb.get_state())
+
+
+def test_mixed_tvb_1d_against_oracle():
+    """Split precision with the plain indicator on a 1D mesh (blast tube, 256 P^2 cells):
+    flags within 0.5% of the oracle's, states to 1e-5 relative L1, bounds exact."""
+    from paper_2412_16002_gb300.solver import Solver
+
+    wl = inputs.euler_blast_tube(256, 2)
+    M = 1.0
+    g = Solver.from_workload(wl, precision="mixed", indicator="tvb", tvb_M=M)
+    o = Oracle(wl.dim, wl.nx, wl.ny, wl.k, wl.domain, wl.flux, gamma=wl.gamma, eps=wl.eps, bc=wl.bc,
+               bc_state=wl.bc_state, indicator=True, tvb_M=M)
+    g.set_state(wl.state)
+    o.set_state(wl.state)
+    t = 0.0
+    flagged = differ = 0
+    for step in range(5):
+        dt = o.max_dt(wl.cfl)
+        ig = g.step(dt, wl.tableau)
+        before = o.c.copy()
+        rc, io = o.step(dt, ORACLE_TABS[wl.tableau], t)
+        assert rc == 0 and ig["restarts"] == io["restarts"]
+        rc2, us, _ = o.step_stages(dt, ORACLE_TABS[wl.tableau], t, modal=before)
+        fo, fg = o.troubled(us[-1]), g.troubled_flags()
+        flagged += int(fo.sum())
+        differ += int((fo != fg).sum())
+        assert g.margins().min() >= 0.0
+        t += dt
+    gap = _rel_l1(g.get_state(), o.get_state(), o.m)
+    print(f"blast1d_256_p2 split + TVB: {flagged} oracle flags, {differ} differ; L1 gap {gap:.3e}")
+    assert flagged > 0 and differ <= 0.005 * 5 * 256
     assert gap < 1e-5
