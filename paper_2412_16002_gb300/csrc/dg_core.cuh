@@ -38,6 +38,28 @@ __device__ __forceinline__ unsigned long long ordbits(double x) {
     return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
+// Comparisons and min/max that need no FP64 arithmetic run on the integer units: the
+// FP64 pipe of this part takes one warp instruction per 64 cycles whatever the number
+// of active lanes, while a 64-bit integer compare-and-select costs a few ALU issues.
+// Keys of +inf and -inf under ordbits.
+constexpr unsigned long long kKeyPosInf = 0xfff0000000000000ull;
+constexpr unsigned long long kKeyNegInf = 0x000fffffffffffffull;
+// inverse of ordbits
+__device__ __forceinline__ double ordbits_inv(unsigned long long k) {
+    return bitsd((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k);
+}
+__device__ __forceinline__ bool isnan_bits(double x) {
+    return (dbits(x) & 0x7fffffffffffffffull) > 0x7ff0000000000000ull;
+}
+__device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) { return a < b ? a : b; }
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
+// fmax of two non-negative doubles (a NaN operand is ignored, as by fmax)
+__device__ __forceinline__ double fmax_nonneg(double a, double b) {
+    if (isnan_bits(a)) return b;
+    if (isnan_bits(b)) return a;
+    return bitsd(umax64(dbits(a), dbits(b)));
+}
+
 // theta = num/den clamped to [0, 1]; a non-positive denominator gives 0
 __device__ __forceinline__ double ratio01(double num, double den) {
     if (!(den > 0.0)) return 0.0;
@@ -115,13 +137,74 @@ __device__ __forceinline__ double speed_dir(const Params &P, const double *u, in
     }
 }
 
+// flux_dir and speed_dir given the reciprocal ri = 1/rho of the state (Euler; other
+// fluxes ignore it): the same values as flux_dir and speed_dir, one division fewer
+// when a state needs both.
+template <int PHYS, int DIM>
+__device__ __forceinline__ void flux_dir_ri(const Params &P, const double *u, int dir, double ri, double *f) {
+    if constexpr (PHYS != PH_EULER) {
+        flux_dir<PHYS, DIM>(P, u, dir, f);
+    } else if constexpr (DIM == 1) {
+        double w = u[1] * ri;
+        double p = (P.gamma - 1.0) * (u[2] - 0.5 * u[1] * w);
+        f[0] = u[1];
+        f[1] = u[1] * w + p;
+        f[2] = (u[2] + p) * w;
+    } else {
+        double wx = u[1] * ri, wy = u[2] * ri;
+        double p = (P.gamma - 1.0) * (u[3] - 0.5 * (u[1] * wx + u[2] * wy));
+        double wd = dir == 0 ? wx : wy;
+        f[0] = u[1 + dir];
+        f[1] = u[1] * wd + (dir == 0 ? p : 0.0);
+        f[2] = u[2] * wd + (dir == 1 ? p : 0.0);
+        f[3] = (u[3] + p) * wd;
+    }
+}
+template <int PHYS, int DIM>
+__device__ __forceinline__ double speed_dir_ri(const Params &P, const double *u, int dir, double ri) {
+    if constexpr (PHYS != PH_EULER) {
+        return speed_dir<PHYS, DIM>(P, u, dir);
+    } else {
+        double kin = DIM == 1 ? u[1] * u[1] : u[1] * u[1] + u[2] * u[2];
+        double p = (P.gamma - 1.0) * (u[DIM + 1] - 0.5 * kin * ri);
+        double c2 = P.gamma * p * ri;
+        double c = c2 > 0.0 ? sqrt(c2) : 0.0;
+        return fabs(u[1 + dir] * ri) + c;
+    }
+}
+template <int PHYS>
+__device__ __forceinline__ double recip_rho(const double *u) {
+    if constexpr (PHYS == PH_EULER) return 1.0 / u[0];
+    return 0.0;
+}
+// both for one state; returns the spectral radius
+template <int PHYS, int DIM>
+__device__ __forceinline__ double flux_speed_dir(const Params &P, const double *u, int dir, double *f) {
+    double ri = recip_rho<PHYS>(u);
+    flux_dir_ri<PHYS, DIM>(P, u, dir, ri, f);
+    return speed_dir_ri<PHYS, DIM>(P, u, dir, ri);
+}
+
 // Trial-step rate at one point: sum over directions of lambda_d / h_d, so that
 // dt = CFL / max rate (eq. numerical_experiment:CFL, directional radii summed in 2D).
+// The Euler form shares the reciprocal and the sound speed between the directions
+// (the same values as speed_dir per direction).
 template <int PHYS, int DIM>
 __device__ __forceinline__ double sk_rate(const Params &P, const double *u) {
-    double r = speed_dir<PHYS, DIM>(P, u, 0) * (0.5 * P.rhx);
-    if constexpr (DIM == 2) r = fma(speed_dir<PHYS, DIM>(P, u, 1), 0.5 * P.rhy, r);
-    return r;
+    if constexpr (PHYS == PH_EULER) {
+        double ri = 1.0 / u[0];
+        double kin = DIM == 1 ? u[1] * u[1] : u[1] * u[1] + u[2] * u[2];
+        double p = (P.gamma - 1.0) * (u[DIM + 1] - 0.5 * kin * ri);
+        double c2 = P.gamma * p * ri;
+        double c = c2 > 0.0 ? sqrt(c2) : 0.0;
+        double r = (fabs(u[1] * ri) + c) * (0.5 * P.rhx);
+        if constexpr (DIM == 2) r = fma(fabs(u[2] * ri) + c, 0.5 * P.rhy, r);
+        return r;
+    } else {
+        double r = speed_dir<PHYS, DIM>(P, u, 0) * (0.5 * P.rhx);
+        if constexpr (DIM == 2) r = fma(speed_dir<PHYS, DIM>(P, u, 1), 0.5 * P.rhy, r);
+        return r;
+    }
 }
 
 // rho e = E - |m|^2 / (2 rho)   (eq. Euler-limiter2)
@@ -211,7 +294,7 @@ struct Smem {
     double tf[C::NCB][C::NTR][C::M];
     double avg[C::NCB][C::M];
     union {  // the limiter's reductions and the final kernel's edge speeds never overlap
-        double red[C::NCB][C::NN][2];
+        unsigned long long red[C::NCB][C::NN][2];  // ordbits keys
         double al[C::NCB][C::NTR];
     };
     double th[C::NCB][2];
@@ -304,32 +387,43 @@ __device__ void limit_block(const Params &P, const Bufs &B, Smem<C> &S, int lc, 
         S.avg[lc][c] = s;
     }
     __syncthreads();
-    // 3. values at S_K and this thread's extremes
-    double pmin = INFINITY, pmax = -INFINITY;
+    // 3. values at S_K and this thread's extremes (order-preserving integer keys)
+    unsigned long long kmin = kKeyPosInf, kmax = kKeyNegInf;
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
         int p = node + j * NN;
         if (p < NSK) {
             sk_eval<DIM, N, M, NN>(S.u[lc], p, pts[j]);
-            pmin = fmin(pmin, pts[j][0]);
-            pmax = fmax(pmax, pts[j][0]);
-            if (!(pts[j][0] == pts[j][0])) pmin = -INFINITY;  // NaN counts as a violation
+            if (isnan_bits(pts[j][0])) {
+                kmin = kKeyNegInf;  // NaN counts as a violation
+            } else {
+                unsigned long long k = ordbits(pts[j][0]);
+                kmin = umin64(kmin, k);
+                kmax = umax64(kmax, k);
+            }
         }
     }
-    S.red[lc][node][0] = pmin;
-    S.red[lc][node][1] = pmax;
+    S.red[lc][node][0] = kmin;
+    S.red[lc][node][1] = kmax;
     double ub[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) ub[c] = S.avg[lc][c];
     __syncthreads();
     // 4. leader: admissibility of the average and theta (theta_1 for Euler)
+    double reb = 0.0;  // leader: rho e of the average (Euler)
     if (node == 0) {
-        double mn = INFINITY, mx = -INFINITY;
+        unsigned long long kmn = kKeyPosInf, kmx = kKeyNegInf;
         for (int q = 0; q < NN; ++q) {
-            mn = fmin(mn, S.red[lc][q][0]);
-            mx = fmax(mx, S.red[lc][q][1]);
+            kmn = umin64(kmn, S.red[lc][q][0]);
+            kmx = umax64(kmx, S.red[lc][q][1]);
         }
-        if (check_avg && active && !admissible<PHYS, DIM>(P, ub)) atomicOr(B.flag, 1);
+        const double mn = ordbits_inv(kmn), mx = ordbits_inv(kmx);
+        if constexpr (PHYS == PH_EULER) {
+            reb = rho_e<DIM>(ub);
+            if (check_avg && active && !(ub[0] >= P.eps && reb >= P.eps)) atomicOr(B.flag, 1);
+        } else {
+            if (check_avg && active && !admissible<PHYS, DIM>(P, ub)) atomicOr(B.flag, 1);
+        }
         double th = 1.0;
         if constexpr (PHYS == PH_EULER) {
             if (mn < P.eps) th = ratio01(ub[0] - P.eps, ub[0] - mn);
@@ -346,7 +440,7 @@ __device__ void limit_block(const Params &P, const Bufs &B, Smem<C> &S, int lc, 
     double th2 = 1.0;
     if constexpr (PHYS == PH_EULER) {
         // 5. rho e at S_K with the density already scaled by theta_1
-        double pm = INFINITY;
+        unsigned long long km = kKeyPosInf;
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
             int p = node + j * NN;
@@ -356,15 +450,15 @@ __device__ void limit_block(const Params &P, const Bufs &B, Smem<C> &S, int lc, 
                 for (int c = 0; c < M; ++c) v[c] = pts[j][c];
                 if (th1 < 1.0) v[0] = th1 * (v[0] - ub[0]) + ub[0];
                 double re = rho_e<DIM>(v);
-                pm = (re == re) ? fmin(pm, re) : -INFINITY;  // NaN counts as a violation
+                km = isnan_bits(re) ? kKeyNegInf : umin64(km, ordbits(re));  // NaN counts as a violation
             }
         }
-        S.red[lc][node][1] = pm;
+        S.red[lc][node][1] = km;
         __syncthreads();
         if (node == 0) {
-            double mn = INFINITY;
-            for (int q = 0; q < NN; ++q) mn = fmin(mn, S.red[lc][q][1]);
-            double reb = rho_e<DIM>(ub);
+            unsigned long long kmn = kKeyPosInf;
+            for (int q = 0; q < NN; ++q) kmn = umin64(kmn, S.red[lc][q][1]);
+            const double mn = ordbits_inv(kmn);
             S.th[lc][1] = (mn >= P.eps) ? 1.0 : ratio01(reb - P.eps, reb - mn) * kMargin;
         }
         __syncthreads();
@@ -628,7 +722,7 @@ __device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int b
     for (int i = 0; i < P.s; ++i) {
         if (P.slot[i] < 0) continue;
         const double *tr = B.tr + (size_t)P.slot[i] * M * P.ncell * NTR;
-        double uL[FPT][M], uR[FPT][M];
+        double uL[FPT][M], uR[FPT][M], riL[FPT], riR[FPT];
 #pragma unroll
         for (int j = 0; j < FPT; ++j) {
             int fp = node + j * NN;
@@ -655,7 +749,10 @@ __device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int b
                     uR[j][c] = upper ? ue[c] : ui[c];
                 }
                 int dir = face >> 1;
-                S.al[lc][fp] = fmax(speed_dir<PHYS, DIM>(P, uL[j], dir), speed_dir<PHYS, DIM>(P, uR[j], dir));
+                riL[j] = recip_rho<PHYS>(uL[j]);
+                riR[j] = recip_rho<PHYS>(uR[j]);
+                S.al[lc][fp] = fmax_nonneg(speed_dir_ri<PHYS, DIM>(P, uL[j], dir, riL[j]),
+                                           speed_dir_ri<PHYS, DIM>(P, uR[j], dir, riR[j]));
             } else if (fp < NTR) {
                 S.al[lc][fp] = 0.0;
             }
@@ -669,10 +766,10 @@ __device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int b
                 int dir = face >> 1;
                 double alpha = 0.0;  // per-edge LF viscosity: max over the edge's points
 #pragma unroll
-                for (int q = 0; q < NF; ++q) alpha = fmax(alpha, S.al[lc][face * NF + q]);
+                for (int q = 0; q < NF; ++q) alpha = fmax_nonneg(alpha, S.al[lc][face * NF + q]);
                 double fL[M], fR[M];
-                flux_dir<PHYS, DIM>(P, uL[j], dir, fL);
-                flux_dir<PHYS, DIM>(P, uR[j], dir, fR);
+                flux_dir_ri<PHYS, DIM>(P, uL[j], dir, riL[j], fL);
+                flux_dir_ri<PHYS, DIM>(P, uR[j], dir, riR[j], fR);
                 bool upper = face & 1;
 #pragma unroll
                 for (int c = 0; c < M; ++c) {
@@ -729,11 +826,12 @@ __device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int b
 #pragma unroll
     for (int j = 0; j < C::PPT; ++j) {
         int p = node + j * NN;
-        if (p < C::NSK && active) amax = fmax(amax, sk_rate<PHYS, DIM>(P, pts[j]));
+        if (p < C::NSK && active) amax = fmax_nonneg(amax, sk_rate<PHYS, DIM>(P, pts[j]));
     }
+    unsigned long long abits = dbits(amax);  // non-negative: the bits order as the values
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    if ((threadIdx.x & 31) == 0 && amax > 0.0) atomicMax(B.a0, dbits(amax));
+    for (int o = 16; o > 0; o >>= 1) abits = umax64(abits, __shfl_xor_sync(0xffffffffu, abits, o));
+    if ((threadIdx.x & 31) == 0 && abits > 0ull) atomicMax(B.a0, abits);
     store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
 }
 
@@ -916,11 +1014,12 @@ __device__ __forceinline__ void trouble_body(const Params &P, const Bufs &B, int
 #pragma unroll
     for (int j = 0; j < C::PPT; ++j) {
         int p = node + j * NN;
-        if (p < C::NSK && active) amax = fmax(amax, sk_rate<PHYS, DIM>(P, pts[j]));
+        if (p < C::NSK && active) amax = fmax_nonneg(amax, sk_rate<PHYS, DIM>(P, pts[j]));
     }
+    unsigned long long abits = dbits(amax);  // non-negative: the bits order as the values
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    if ((threadIdx.x & 31) == 0 && amax > 0.0) atomicMax(B.a0, dbits(amax));
+    for (int o = 16; o > 0; o >>= 1) abits = umax64(abits, __shfl_xor_sync(0xffffffffu, abits, o));
+    if ((threadIdx.x & 31) == 0 && abits > 0ull) atomicMax(B.a0, abits);
     store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
 }
 

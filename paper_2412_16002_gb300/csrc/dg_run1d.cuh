@@ -183,10 +183,9 @@ __global__ void __launch_bounds__(RunCfg1D<N, PHYS, NCBV>::NT) k_run1d(Params P,
                     } else {
                         continue;  // a face beyond the mesh: no own cell uses it
                     }
-                    double alpha = fmax(speed_dir<PHYS, 1>(P, uL, 0), speed_dir<PHYS, 1>(P, uR, 0));
                     double fL[M], fR[M];
-                    flux_dir<PHYS, 1>(P, uL, 0, fL);
-                    flux_dir<PHYS, 1>(P, uR, 0, fR);
+                    double alpha = fmax_nonneg(flux_speed_dir<PHYS, 1>(P, uL, 0, fL),
+                                               flux_speed_dir<PHYS, 1>(P, uR, 0, fR));
 #pragma unroll
                     for (int c = 0; c < M; ++c) {
                         double fhat = 0.5 * (fL[c] + fR[c]) - 0.5 * alpha * (uR[c] - uL[c]);
@@ -225,11 +224,12 @@ __global__ void __launch_bounds__(RunCfg1D<N, PHYS, NCBV>::NT) k_run1d(Params P,
 #pragma unroll
             for (int j = 0; j < C::PPT; ++j) {
                 int p = node + j * NN;
-                if (p < C::NSK && own) amax = fmax(amax, sk_rate<PHYS, 1>(P, pts[j]));
+                if (p < C::NSK && own) amax = fmax_nonneg(amax, sk_rate<PHYS, 1>(P, pts[j]));
             }
+            unsigned long long abits = dbits(amax);  // non-negative: the bits order as the values
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-            if ((threadIdx.x & 31) == 0 && amax > 0.0) atomicMax(B.a0, dbits(amax));
+            for (int o = 16; o > 0; o >>= 1) abits = umax64(abits, __shfl_xor_sync(0xffffffffu, abits, o));
+            if ((threadIdx.x & 31) == 0 && abits > 0ull) atomicMax(B.a0, abits);
             if (own) store_node<1, N, PHYS>(P, unew, gc, node, true, u);
             __syncthreads();
         }
