@@ -100,8 +100,10 @@ def algorithmic_flops(wl):
     2n per trace point per component; lift 5 per node per component per direction; stage
     combination 2 per node per component per nonzero a_ij; limiter: average 2 per node per
     component, S_K interpolation 2n per point per component, rho*e 6 per point and 10 per
-    theta; LF flux per face point per stage: 2 speeds (10), 2 fluxes, 8 per component;
-    u* accumulation 2 per node per component per nonzero b_i; a0 10 per S_K point."""
+    theta; the spectral radius (10) of every trace point of a stage with b_i != 0 (computed
+    with the trace flux that G needs anyway); LF flux per face point per such stage: 8 per
+    component (the two trace fluxes and radii are those of G's traces); u* accumulation 2
+    per node per component per nonzero b_i; a0 10 per S_K point."""
     d, n, m = wl.dim, wl.k + 1, wl.m
     nn = n ** d
     ntr = 2 * d * (n if d == 2 else 1)
@@ -111,8 +113,8 @@ def algorithmic_flops(wl):
     ff = flux_flops(wl.flux, d)
     g = nn * (ff * (2 if d == 2 else 1) * (1 if d == 2 else 1) + 2 * n * m * d + 5 * m * d) + ntr * (2 * n * m + ff)
     lim = 2 * nn * m + nsk * (2 * n * m) + (nsk * 6 + 20 if wl.flux == "euler" else 10)
-    inner = s * g + na * 2 * nn * m + (s - 1) * lim + nslot * 2 * nn * m
-    lf = ntr * nslot * (20 + 2 * ff + 8 * m)
+    inner = s * g + na * 2 * nn * m + (s - 1) * lim + nslot * 2 * nn * m + nslot * ntr * 10
+    lf = ntr * nslot * 8 * m
     final = lf + nn * m * 5 * d + lim + nsk * 10
     return inner, final
 

@@ -214,6 +214,7 @@ Bufs base_bufs(const crkdg_ctx *h) {
     B.unew = h->unew;
     B.tr = h->tr;
     B.tavg = h->tr ? h->tr + (size_t)h->tr_slots * h->m * h->ncell * h->ntr : nullptr;
+    B.tfs = h->tr ? h->tr + (size_t)h->tr_slots * h->m * h->ncell * (h->ntr + 1) : nullptr;
     B.flag = &h->scal->flag;
     B.nlim = &h->scal->nlim;
     B.thmin = &h->scal->thmin;
@@ -312,8 +313,10 @@ crkdg_status ensure_traces(crkdg_ctx *h, int slots) {
     if (h->tr) cudaFree(h->tr);
     h->tr = nullptr;
     h->tr_slots = 0;
-    // traces [slot][m][cell][face point], then the traced stages' cell averages [slot][m][cell]
-    size_t bytes = (size_t)slots * h->m * h->ncell * (h->ntr + 1) * sizeof(double);
+    // traces [slot][m][cell][face point], the traced stages' cell averages [slot][m][cell],
+    // then the traces' normal fluxes and spectral radii [slot][m + 1][cell][face point]
+    size_t bytes = ((size_t)slots * h->m * h->ncell * (h->ntr + 1) + (size_t)slots * (h->m + 1) * h->ncell * h->ntr) *
+                   sizeof(double);
     CK(h, cudaMalloc(&h->tr, bytes));
     h->tr_slots = slots;
     return CRKDG_OK;

@@ -48,6 +48,8 @@ constexpr unsigned long long kKeyNegInf = 0x000fffffffffffffull;
 __device__ __forceinline__ double ordbits_inv(unsigned long long k) {
     return bitsd((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k);
 }
+// x != 0.0 on the integer units (NaN counts as non-zero, as for the comparison)
+__device__ __forceinline__ bool nonzero_bits(double x) { return (dbits(x) << 1) != 0ull; }
 __device__ __forceinline__ bool isnan_bits(double x) {
     return (dbits(x) & 0x7fffffffffffffffull) > 0x7ff0000000000000ull;
 }
@@ -70,6 +72,38 @@ __device__ __forceinline__ double ratio01(double num, double den) {
 
 // ----------------------------------------------------------------------------- physics
 
+// Euler flux . e_dir and spectral radius given ri = 1/rho, written with explicit
+// roundings (fma, __dmul_rn, __dadd_rn): the compiler cannot contract them
+// differently where they are inlined, so a trace's flux stored by the inner kernel
+// equals, bit for bit, the same flux recomputed by the final kernel.
+template <int DIM>
+__device__ __forceinline__ void euler_flux_ri(const Params &P, const double *u, int dir, double ri, double *f) {
+    const double gm1 = P.gamma - 1.0;
+    if constexpr (DIM == 1) {
+        double w = __dmul_rn(u[1], ri);
+        double p = __dmul_rn(gm1, fma(-0.5 * u[1], w, u[2]));
+        f[0] = u[1];
+        f[1] = fma(u[1], w, p);
+        f[2] = __dmul_rn(__dadd_rn(u[2], p), w);
+    } else {
+        double wx = __dmul_rn(u[1], ri), wy = __dmul_rn(u[2], ri);
+        double p = __dmul_rn(gm1, fma(-0.5, fma(u[1], wx, __dmul_rn(u[2], wy)), u[3]));
+        double wd = dir == 0 ? wx : wy;
+        f[0] = u[1 + dir];
+        f[1] = dir == 0 ? fma(u[1], wd, p) : __dmul_rn(u[1], wd);
+        f[2] = dir == 1 ? fma(u[2], wd, p) : __dmul_rn(u[2], wd);
+        f[3] = __dmul_rn(__dadd_rn(u[3], p), wd);
+    }
+}
+template <int DIM>
+__device__ __forceinline__ double euler_speed_ri(const Params &P, const double *u, int dir, double ri) {
+    double kin = DIM == 1 ? __dmul_rn(u[1], u[1]) : fma(u[1], u[1], __dmul_rn(u[2], u[2]));
+    double p = __dmul_rn(P.gamma - 1.0, fma(-0.5 * kin, ri, u[DIM + 1]));
+    double c2 = __dmul_rn(__dmul_rn(P.gamma, p), ri);
+    double c = c2 > 0.0 ? sqrt(c2) : 0.0;
+    return __dadd_rn(fabs(__dmul_rn(u[1 + dir], ri)), c);
+}
+
 // flux f(u) . e_dir  (eq. claws; Euler eq. Euler, Euler-2)
 template <int PHYS, int DIM>
 __device__ __forceinline__ void flux_dir(const Params &P, const double *u, int dir, double *f) {
@@ -77,22 +111,8 @@ __device__ __forceinline__ void flux_dir(const Params &P, const double *u, int d
         f[0] = (dir == 0 ? P.velx : P.vely) * u[0];
     } else if constexpr (PHYS == PH_BURG) {
         f[0] = 0.5 * u[0] * u[0];
-    } else if constexpr (DIM == 1) {
-        double ri = 1.0 / u[0];
-        double w = u[1] * ri;
-        double p = (P.gamma - 1.0) * (u[2] - 0.5 * u[1] * w);
-        f[0] = u[1];
-        f[1] = u[1] * w + p;
-        f[2] = (u[2] + p) * w;
     } else {
-        double ri = 1.0 / u[0];
-        double wx = u[1] * ri, wy = u[2] * ri;
-        double p = (P.gamma - 1.0) * (u[3] - 0.5 * (u[1] * wx + u[2] * wy));
-        double wd = dir == 0 ? wx : wy;
-        f[0] = u[1 + dir];
-        f[1] = u[1] * wd + (dir == 0 ? p : 0.0);
-        f[2] = u[2] * wd + (dir == 1 ? p : 0.0);
-        f[3] = (u[3] + p) * wd;
+        euler_flux_ri<DIM>(P, u, dir, 1.0 / u[0], f);
     }
 }
 
@@ -128,12 +148,7 @@ __device__ __forceinline__ double speed_dir(const Params &P, const double *u, in
     } else if constexpr (PHYS == PH_BURG) {
         return fabs(u[0]);
     } else {
-        double ri = 1.0 / u[0];
-        double kin = DIM == 1 ? u[1] * u[1] : u[1] * u[1] + u[2] * u[2];
-        double p = (P.gamma - 1.0) * (u[DIM + 1] - 0.5 * kin * ri);
-        double c2 = P.gamma * p * ri;
-        double c = c2 > 0.0 ? sqrt(c2) : 0.0;
-        return fabs(u[1 + dir] * ri) + c;
+        return euler_speed_ri<DIM>(P, u, dir, 1.0 / u[0]);
     }
 }
 
@@ -144,20 +159,8 @@ template <int PHYS, int DIM>
 __device__ __forceinline__ void flux_dir_ri(const Params &P, const double *u, int dir, double ri, double *f) {
     if constexpr (PHYS != PH_EULER) {
         flux_dir<PHYS, DIM>(P, u, dir, f);
-    } else if constexpr (DIM == 1) {
-        double w = u[1] * ri;
-        double p = (P.gamma - 1.0) * (u[2] - 0.5 * u[1] * w);
-        f[0] = u[1];
-        f[1] = u[1] * w + p;
-        f[2] = (u[2] + p) * w;
     } else {
-        double wx = u[1] * ri, wy = u[2] * ri;
-        double p = (P.gamma - 1.0) * (u[3] - 0.5 * (u[1] * wx + u[2] * wy));
-        double wd = dir == 0 ? wx : wy;
-        f[0] = u[1 + dir];
-        f[1] = u[1] * wd + (dir == 0 ? p : 0.0);
-        f[2] = u[2] * wd + (dir == 1 ? p : 0.0);
-        f[3] = (u[3] + p) * wd;
+        euler_flux_ri<DIM>(P, u, dir, ri, f);
     }
 }
 template <int PHYS, int DIM>
@@ -165,11 +168,7 @@ __device__ __forceinline__ double speed_dir_ri(const Params &P, const double *u,
     if constexpr (PHYS != PH_EULER) {
         return speed_dir<PHYS, DIM>(P, u, dir);
     } else {
-        double kin = DIM == 1 ? u[1] * u[1] : u[1] * u[1] + u[2] * u[2];
-        double p = (P.gamma - 1.0) * (u[DIM + 1] - 0.5 * kin * ri);
-        double c2 = P.gamma * p * ri;
-        double c = c2 > 0.0 ? sqrt(c2) : 0.0;
-        return fabs(u[1 + dir] * ri) + c;
+        return euler_speed_ri<DIM>(P, u, dir, ri);
     }
 }
 template <int PHYS>
@@ -295,6 +294,7 @@ struct Smem {
     double avg[C::NCB][C::M];
     union {  // the limiter's reductions and the final kernel's edge speeds never overlap
         unsigned long long red[C::NCB][C::NN][2];  // ordbits keys
+        double ts[C::NCB][C::NTR];  // spectral radii of the traces (eval_G of a traced stage)
         double al[C::NCB][C::NTR];
     };
     double th[C::NCB][2];
@@ -524,10 +524,12 @@ __device__ void limit_block(const Params &P, const Bufs &B, Smem<C> &S, int lc, 
 // ----------------------------------------------------------------------------- G
 
 // G(u) at this thread's node (block collective).  trs receives the interior
-// trace states of this thread's face points.
+// trace states of this thread's face points; their normal fluxes stay in S.tf and,
+// with want_speed, their spectral radii go to S.ts (both read back by the thread
+// that computed them, for the final stage's Lax--Friedrichs flux of traced stages).
 template <class C>
 __device__ void eval_G(const Params &P, Smem<C> &S, int lc, int node, const double *u, double *g,
-                       double (&trs)[C::FPT][C::M]) {
+                       double (&trs)[C::FPT][C::M], bool want_speed = false) {
     constexpr int DIM = C::D, N = C::NP, PHYS = C::PH;
     constexpr int M = C::M, NN = C::NN, NF = C::NF, NTR = C::NTR, FPT = C::FPT;
     const NodalTables &T = c_tab[N - 2];
@@ -582,9 +584,11 @@ __device__ void eval_G(const Params &P, Smem<C> &S, int lc, int node, const doub
                 trs[j][c] = s;
             }
             double f[M];
-            flux_dir<PHYS, DIM>(P, trs[j], face >> 1, f);
+            const double ri = recip_rho<PHYS>(trs[j]);
+            flux_dir_ri<PHYS, DIM>(P, trs[j], face >> 1, ri, f);
 #pragma unroll
             for (int c = 0; c < M; ++c) S.tf[lc][fp][c] = f[c];
+            if (want_speed) S.ts[lc][fp] = speed_dir_ri<PHYS, DIM>(P, trs[j], face >> 1, ri);
         }
     }
     __syncthreads();
@@ -651,14 +655,15 @@ __device__ __forceinline__ void inner_body(const Params &P, const Bufs &B, int b
                 double v = un[c];
 #pragma unroll
                 for (int j = 0; j < i; ++j)
-                    if (P.A[i][j] != 0.0) v = fma(P.dt * P.A[i][j], gh[j][c], v);
+                    if (nonzero_bits(P.A[i][j])) v = fma(P.dt * P.A[i][j], gh[j][c], v);
                 cur[c] = v;
             }
             double pts[C::PPT][M];
             limit_block(P, B, S, lc, node, active, cur, pts, true, true);
         }
         double trs[FPT][M];
-        eval_G(P, S, lc, node, cur, gh[i], trs);
+        const bool keep_faces = P.slot[i] >= 0 && B.tfs != nullptr;
+        eval_G(P, S, lc, node, cur, gh[i], trs, keep_faces);
         if (P.slot[i] >= 0) {  // cell average of the traced stage value (outflow exterior state)
             const NodalTables &T = c_tab[N - 2];
             for (int c = node; c < M; c += NN) {
@@ -672,18 +677,24 @@ __device__ __forceinline__ void inner_body(const Params &P, const Bufs &B, int b
         if (P.mode == MODE_OP_G) {
 #pragma unroll
             for (int c = 0; c < M; ++c) acc[c] = gh[i][c];
-        } else if (P.b[i] != 0.0) {
+        } else if (nonzero_bits(P.b[i])) {
 #pragma unroll
             for (int c = 0; c < M; ++c) acc[c] = fma(P.dt * P.b[i], gh[i][c], acc[c]);
         }
         if (P.slot[i] >= 0 && active) {
             double *dst = B.tr + (size_t)P.slot[i] * M * P.ncell * NTR;
+            double *dfs = keep_faces ? B.tfs + (size_t)P.slot[i] * (M + 1) * P.ncell * NTR : nullptr;
 #pragma unroll
             for (int j = 0; j < FPT; ++j) {
                 int fp = node + j * NN;
                 if (fp < NTR) {
 #pragma unroll
                     for (int c = 0; c < M; ++c) dst[((size_t)c * P.ncell + cell) * NTR + fp] = trs[j][c];
+                    if (keep_faces) {  // this thread's own entries of S.tf and S.ts
+#pragma unroll
+                        for (int c = 0; c < M; ++c) dfs[((size_t)c * P.ncell + cell) * NTR + fp] = S.tf[lc][fp][c];
+                        dfs[((size_t)M * P.ncell + cell) * NTR + fp] = S.ts[lc][fp];
+                    }
                 }
             }
         }
@@ -700,7 +711,7 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_inner(Params P, Bufs 
 // limiter, the admissibility test and a0 of the new state.  Each face flux is
 // evaluated from the same ordered pair (lower side, upper side) by both cells
 // sharing the face, so the update is conservative to round-off.
-template <int DIM, int N, int PHYS>
+template <int DIM, int N, int PHYS, bool STORED = false>
 __device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int blk) {
     using C = Cfg<DIM, N, PHYS>;
     constexpr int M = C::M, NN = C::NN, NF = C::NF, NTR = C::NTR, FPT = C::FPT;
@@ -722,37 +733,49 @@ __device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int b
     for (int i = 0; i < P.s; ++i) {
         if (P.slot[i] < 0) continue;
         const double *tr = B.tr + (size_t)P.slot[i] * M * P.ncell * NTR;
-        double uL[FPT][M], uR[FPT][M], riL[FPT], riR[FPT];
+        // fluxes and spectral radii of interior traces: as the inner kernel stored them
+        // (STORED, B.tfs), else recomputed here; the exterior state of a boundary face
+        // always here
+        const double *tfs = STORED ? B.tfs + (size_t)P.slot[i] * (M + 1) * P.ncell * NTR : nullptr;
+        double ui[FPT][M], ue[FPT][M], riI[FPT], riE[FPT];
+        int nbr[FPT];
 #pragma unroll
         for (int j = 0; j < FPT; ++j) {
             int fp = node + j * NN;
+            nbr[j] = -1;
             if (fp < NTR && active) {
                 int face = fp / NF, pos = fp - face * NF;
-                double ui[M], ue[M];
 #pragma unroll
-                for (int c = 0; c < M; ++c) ui[c] = tr[((size_t)c * P.ncell + cell) * NTR + fp];
+                for (int c = 0; c < M; ++c) ui[j][c] = tr[((size_t)c * P.ncell + cell) * NTR + fp];
                 int nb = neighbour(P, cell, face);
+                nbr[j] = nb;
+                int ofp = (face ^ 1) * NF + pos;
                 if (nb >= 0) {
-                    int ofp = (face ^ 1) * NF + pos;
 #pragma unroll
-                    for (int c = 0; c < M; ++c) ue[c] = tr[((size_t)c * P.ncell + nb) * NTR + ofp];
+                    for (int c = 0; c < M; ++c) ue[j][c] = tr[((size_t)c * P.ncell + nb) * NTR + ofp];
                 } else {
                     double av[M];
 #pragma unroll
                     for (int c = 0; c < M; ++c) av[c] = B.tavg[((size_t)P.slot[i] * M + c) * P.ncell + cell];
-                    exterior_state<PHYS, DIM>(P, face, ui, av, ue);
-                }
-                bool upper = face & 1;  // R or T: the cell is on the lower side of the face
-#pragma unroll
-                for (int c = 0; c < M; ++c) {
-                    uL[j][c] = upper ? ui[c] : ue[c];
-                    uR[j][c] = upper ? ue[c] : ui[c];
+                    exterior_state<PHYS, DIM>(P, face, ui[j], av, ue[j]);
                 }
                 int dir = face >> 1;
-                riL[j] = recip_rho<PHYS>(uL[j]);
-                riR[j] = recip_rho<PHYS>(uR[j]);
-                S.al[lc][fp] = fmax_nonneg(speed_dir_ri<PHYS, DIM>(P, uL[j], dir, riL[j]),
-                                           speed_dir_ri<PHYS, DIM>(P, uR[j], dir, riR[j]));
+                double sI, sE;
+                if constexpr (STORED) {
+                    sI = tfs[((size_t)M * P.ncell + cell) * NTR + fp];
+                    if (nb >= 0) {
+                        sE = tfs[((size_t)M * P.ncell + nb) * NTR + ofp];
+                    } else {
+                        riE[j] = recip_rho<PHYS>(ue[j]);
+                        sE = speed_dir_ri<PHYS, DIM>(P, ue[j], dir, riE[j]);
+                    }
+                } else {
+                    riI[j] = recip_rho<PHYS>(ui[j]);
+                    riE[j] = recip_rho<PHYS>(ue[j]);
+                    sI = speed_dir_ri<PHYS, DIM>(P, ui[j], dir, riI[j]);
+                    sE = speed_dir_ri<PHYS, DIM>(P, ue[j], dir, riE[j]);
+                }
+                S.al[lc][fp] = fmax_nonneg(sI, sE);
             } else if (fp < NTR) {
                 S.al[lc][fp] = 0.0;
             }
@@ -762,20 +785,34 @@ __device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int b
         for (int j = 0; j < FPT; ++j) {
             int fp = node + j * NN;
             if (fp < NTR && active) {
-                int face = fp / NF;
+                int face = fp / NF, pos = fp - face * NF;
                 int dir = face >> 1;
                 double alpha = 0.0;  // per-edge LF viscosity: max over the edge's points
 #pragma unroll
                 for (int q = 0; q < NF; ++q) alpha = fmax_nonneg(alpha, S.al[lc][face * NF + q]);
-                double fL[M], fR[M];
-                flux_dir_ri<PHYS, DIM>(P, uL[j], dir, riL[j], fL);
-                flux_dir_ri<PHYS, DIM>(P, uR[j], dir, riR[j], fR);
-                bool upper = face & 1;
+                double fI[M], fE[M];
+                const int nb = nbr[j];
+                if constexpr (STORED) {
+#pragma unroll
+                    for (int c = 0; c < M; ++c) fI[c] = tfs[((size_t)c * P.ncell + cell) * NTR + fp];
+                    if (nb >= 0) {
+                        const int ofp = (face ^ 1) * NF + pos;
+#pragma unroll
+                        for (int c = 0; c < M; ++c) fE[c] = tfs[((size_t)c * P.ncell + nb) * NTR + ofp];
+                    } else {
+                        flux_dir_ri<PHYS, DIM>(P, ue[j], dir, riE[j], fE);
+                    }
+                } else {
+                    flux_dir_ri<PHYS, DIM>(P, ui[j], dir, riI[j], fI);
+                    flux_dir_ri<PHYS, DIM>(P, ue[j], dir, riE[j], fE);
+                }
+                bool upper = face & 1;  // R or T: the cell is on the lower side of the face
 #pragma unroll
                 for (int c = 0; c < M; ++c) {
-                    double fhat = 0.5 * (fL[c] + fR[c]) - 0.5 * alpha * (uR[j][c] - uL[j][c]);
-                    double fint = upper ? fL[c] : fR[c];
-                    dc[j][c] = fma(P.b[i], fhat - fint, dc[j][c]);
+                    const double uLc = upper ? ui[j][c] : ue[j][c], uRc = upper ? ue[j][c] : ui[j][c];
+                    const double fLc = upper ? fI[c] : fE[c], fRc = upper ? fE[c] : fI[c];
+                    double fhat = 0.5 * (fLc + fRc) - 0.5 * alpha * (uRc - uLc);
+                    dc[j][c] = fma(P.b[i], fhat - fI[c], dc[j][c]);
                 }
             }
         }
@@ -835,9 +872,9 @@ __device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int b
     store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
 }
 
-template <int DIM, int N, int PHYS>
+template <int DIM, int N, int PHYS, bool STORED>
 __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_final(Params P, Bufs B) {
-    final_body<DIM, N, PHYS>(P, B, blockIdx.x);
+    final_body<DIM, N, PHYS, STORED>(P, B, blockIdx.x);
 }
 
 // Limiter applied to a state (set-up projection, operator checks): un -> unew.
@@ -1148,7 +1185,12 @@ cudaError_t launch_one(int kernel, int nblocks, cudaStream_t st, const Params &P
     using C = Cfg<DIM, N, PHYS>;
     switch (kernel) {
     case K_INNER: k_inner<DIM, N, PHYS><<<nblocks, C::NT, 0, st>>>(P, B); break;
-    case K_FINAL: k_final<DIM, N, PHYS><<<nblocks, C::NT, 0, st>>>(P, B); break;
+    case K_FINAL:
+        if (B.tfs)
+            k_final<DIM, N, PHYS, true><<<nblocks, C::NT, 0, st>>>(P, B);
+        else
+            k_final<DIM, N, PHYS, false><<<nblocks, C::NT, 0, st>>>(P, B);
+        break;
     case K_LIMIT: k_limit<DIM, N, PHYS><<<nblocks, C::NT, 0, st>>>(P, B); break;
     case K_TROUBLE: k_trouble<DIM, N, PHYS><<<nblocks, C::NT, 0, st>>>(P, B); break;
     case K_FEATURES: k_features<DIM, N, PHYS><<<(P.ncell + 127) / 128, 128, 0, st>>>(P, B); break;

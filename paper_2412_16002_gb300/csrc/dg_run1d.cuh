@@ -80,6 +80,8 @@ __global__ void __launch_bounds__(RunCfg1D<N, PHYS, NCBV>::NT) k_run1d(Params P,
     __shared__ double sTr[MAXS][C::NCB][2][M];
     __shared__ double sAv[MAXS][C::NCB][M];  // cell averages of the traced stage values
     __shared__ double sFc[MAXS][C::NCB][2][M];  // per face: fhat - f(u_L), fhat - f(u_R)
+    __shared__ double sTf[MAXS][C::NCB][2][M];  // normal fluxes of the traces
+    __shared__ double sSp[MAXS][C::NCB][2];     // spectral radii of the traces
     const NodalTables &T = c_tab[N - 2];
     const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
     const int a = node;
@@ -125,21 +127,26 @@ __global__ void __launch_bounds__(RunCfg1D<N, PHYS, NCBV>::NT) k_run1d(Params P,
                         double v = u0[c];
 #pragma unroll
                         for (int j = 0; j < i; ++j)
-                            if (P.A[i][j] != 0.0) v = fma(dt * P.A[i][j], gh[j][c], v);
+                            if (nonzero_bits(P.A[i][j])) v = fma(dt * P.A[i][j], gh[j][c], v);
                         cur_u[c] = v;
                     }
                     double pts[C::PPT][M];
                     limit_block(P, B, S, lc, node, own, cur_u, pts, true, true);
                 }
                 double trs[C::FPT][M];
-                eval_G(P, S, lc, node, cur_u, gh[i], trs);
-                if (P.b[i] != 0.0) {
+                const bool traced = P.slot[i] >= 0;
+                eval_G(P, S, lc, node, cur_u, gh[i], trs, traced);
+                if (nonzero_bits(P.b[i])) {
 #pragma unroll
                     for (int c = 0; c < M; ++c) acc[c] = fma(dt * P.b[i], gh[i][c], acc[c]);
                 }
-                if (P.slot[i] >= 0 && node < 2) {
+                if (traced && node < 2) {
 #pragma unroll
-                    for (int c = 0; c < M; ++c) sTr[P.slot[i]][lc][node][c] = trs[0][c];
+                    for (int c = 0; c < M; ++c) {
+                        sTr[P.slot[i]][lc][node][c] = trs[0][c];
+                        sTf[P.slot[i]][lc][node][c] = S.tf[lc][node][c];  // written by this thread
+                    }
+                    sSp[P.slot[i]][lc][node] = S.ts[lc][node];
                 }
                 if (P.slot[i] >= 0) {  // S.u holds the stage values until the next stage's limiter
                     for (int c = node; c < M; c += NN) {
@@ -163,29 +170,44 @@ __global__ void __launch_bounds__(RunCfg1D<N, PHYS, NCBV>::NT) k_run1d(Params P,
                     const int rl = c0 - 1 + j, rr = rl + 1;  // unwrapped indices of the two cells
                     const bool el = periodic || (rl >= 0 && rl < P.ncell);
                     const bool er = periodic || (rr >= 0 && rr < P.ncell);
-                    double uL[M], uR[M];
+                    // interior sides: the trace, its flux and its spectral radius as the
+                    // traced stage's G evaluation computed them; exterior sides from the
+                    // boundary condition
+                    double uL[M], uR[M], fL[M], fR[M], sL, sR;
                     if (el && er) {
 #pragma unroll
                         for (int c = 0; c < M; ++c) {
                             uL[c] = sTr[q][j][1][c];
                             uR[c] = sTr[q][j + 1][0][c];
+                            fL[c] = sTf[q][j][1][c];
+                            fR[c] = sTf[q][j + 1][0][c];
                         }
+                        sL = sSp[q][j][1];
+                        sR = sSp[q][j + 1][0];
                     } else if (er) {  // the left side of the mesh: exterior state of side 0
                         double ui[M];
 #pragma unroll
-                        for (int c = 0; c < M; ++c) ui[c] = uR[c] = sTr[q][j + 1][0][c];
+                        for (int c = 0; c < M; ++c) {
+                            ui[c] = uR[c] = sTr[q][j + 1][0][c];
+                            fR[c] = sTf[q][j + 1][0][c];
+                        }
+                        sR = sSp[q][j + 1][0];
                         exterior_state<PHYS, 1>(P, 0, ui, sAv[q][j + 1], uL);
+                        sL = flux_speed_dir<PHYS, 1>(P, uL, 0, fL);
                     } else if (el) {  // the right side: exterior state of side 1
                         double ui[M];
 #pragma unroll
-                        for (int c = 0; c < M; ++c) ui[c] = uL[c] = sTr[q][j][1][c];
+                        for (int c = 0; c < M; ++c) {
+                            ui[c] = uL[c] = sTr[q][j][1][c];
+                            fL[c] = sTf[q][j][1][c];
+                        }
+                        sL = sSp[q][j][1];
                         exterior_state<PHYS, 1>(P, 1, ui, sAv[q][j], uR);
+                        sR = flux_speed_dir<PHYS, 1>(P, uR, 0, fR);
                     } else {
                         continue;  // a face beyond the mesh: no own cell uses it
                     }
-                    double fL[M], fR[M];
-                    double alpha = fmax_nonneg(flux_speed_dir<PHYS, 1>(P, uL, 0, fL),
-                                               flux_speed_dir<PHYS, 1>(P, uR, 0, fR));
+                    double alpha = fmax_nonneg(sL, sR);
 #pragma unroll
                     for (int c = 0; c < M; ++c) {
                         double fhat = 0.5 * (fL[c] + fR[c]) - 0.5 * alpha * (uR[c] - uL[c]);

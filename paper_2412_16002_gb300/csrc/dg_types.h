@@ -88,6 +88,8 @@ struct Bufs {
     double *unew;       // u^{n+1}
     double *tr;         // face traces of u~^(i): [slot][m][cell][face point]
     double *tavg;       // cell averages of the same u~^(i): [slot][m][cell] (outflow exterior state)
+    double *tfs = nullptr;  // optional: normal fluxes and spectral radii of the traces,
+                            // [slot][m + 1][cell][face point] (the final kernel recomputes them when null)
     int *flag;          // set when a stage average leaves B
     unsigned long long *nlim;   // limited cells
     unsigned long long *thmin;  // bits of the smallest theta (non-negative double)
