@@ -55,6 +55,18 @@ __device__ __forceinline__ bool isnan_bits(double x) {
 }
 __device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) { return a < b ? a : b; }
 __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
+// x > 0.0 (false for NaN)
+__device__ __forceinline__ bool positive_bits(double x) {
+    long long b = (long long)dbits(x);
+    return b > 0ll && b <= 0x7ff0000000000000ll;
+}
+// x >= y for y > 0 (false when x is NaN)
+__device__ __forceinline__ bool ge_pos_bits(double x, double y) {
+    long long b = (long long)dbits(x);
+    return b >= (long long)dbits(y) && b <= 0x7ff0000000000000ll;
+}
+// t < 1.0 for t in [0, 1] (a limiter's scaling factor)
+__device__ __forceinline__ bool below_one(double t) { return (dbits(t) & 0x7fffffffffffffffull) < 0x3ff0000000000000ull; }
 // fmax of two non-negative doubles (a NaN operand is ignored, as by fmax)
 __device__ __forceinline__ double fmax_nonneg(double a, double b) {
     if (isnan_bits(a)) return b;
@@ -100,7 +112,7 @@ __device__ __forceinline__ double euler_speed_ri(const Params &P, const double *
     double kin = DIM == 1 ? __dmul_rn(u[1], u[1]) : fma(u[1], u[1], __dmul_rn(u[2], u[2]));
     double p = __dmul_rn(P.gamma - 1.0, fma(-0.5 * kin, ri, u[DIM + 1]));
     double c2 = __dmul_rn(__dmul_rn(P.gamma, p), ri);
-    double c = c2 > 0.0 ? sqrt(c2) : 0.0;
+    double c = positive_bits(c2) ? sqrt(c2) : 0.0;
     return __dadd_rn(fabs(__dmul_rn(u[1 + dir], ri)), c);
 }
 
@@ -195,7 +207,7 @@ __device__ __forceinline__ double sk_rate(const Params &P, const double *u) {
         double kin = DIM == 1 ? u[1] * u[1] : u[1] * u[1] + u[2] * u[2];
         double p = (P.gamma - 1.0) * (u[DIM + 1] - 0.5 * kin * ri);
         double c2 = P.gamma * p * ri;
-        double c = c2 > 0.0 ? sqrt(c2) : 0.0;
+        double c = positive_bits(c2) ? sqrt(c2) : 0.0;
         double r = (fabs(u[1] * ri) + c) * (0.5 * P.rhx);
         if constexpr (DIM == 2) r = fma(fabs(u[2] * ri) + c, 0.5 * P.rhy, r);
         return r;
@@ -420,18 +432,18 @@ __device__ void limit_block(const Params &P, const Bufs &B, Smem<C> &S, int lc, 
         const double mn = ordbits_inv(kmn), mx = ordbits_inv(kmx);
         if constexpr (PHYS == PH_EULER) {
             reb = rho_e<DIM>(ub);
-            if (check_avg && active && !(ub[0] >= P.eps && reb >= P.eps)) atomicOr(B.flag, 1);
+            if (check_avg && active && !(ge_pos_bits(ub[0], P.eps) && ge_pos_bits(reb, P.eps))) atomicOr(B.flag, 1);
         } else {
             if (check_avg && active && !admissible<PHYS, DIM>(P, ub)) atomicOr(B.flag, 1);
         }
         double th = 1.0;
         if constexpr (PHYS == PH_EULER) {
-            if (mn < P.eps) th = ratio01(ub[0] - P.eps, ub[0] - mn);
+            if (!ge_pos_bits(mn, P.eps)) th = ratio01(ub[0] - P.eps, ub[0] - mn);
         } else {
             if (mx > P.hi) th = fmin(th, ratio01(P.hi - ub[0], mx - ub[0]));
             if (mn < P.lo) th = fmin(th, ratio01(ub[0] - P.lo, ub[0] - mn));
         }
-        S.th[lc][0] = th < 1.0 ? th * kMargin : th;
+        S.th[lc][0] = below_one(th) ? th * kMargin : th;
         S.th[lc][1] = 1.0;
         S.bad[lc] = 0;
     }
@@ -448,7 +460,7 @@ __device__ void limit_block(const Params &P, const Bufs &B, Smem<C> &S, int lc, 
                 double v[M];
 #pragma unroll
                 for (int c = 0; c < M; ++c) v[c] = pts[j][c];
-                if (th1 < 1.0) v[0] = th1 * (v[0] - ub[0]) + ub[0];
+                if (below_one(th1)) v[0] = th1 * (v[0] - ub[0]) + ub[0];
                 double re = rho_e<DIM>(v);
                 km = isnan_bits(re) ? kKeyNegInf : umin64(km, ordbits(re));  // NaN counts as a violation
             }
@@ -459,22 +471,22 @@ __device__ void limit_block(const Params &P, const Bufs &B, Smem<C> &S, int lc, 
             unsigned long long kmn = kKeyPosInf;
             for (int q = 0; q < NN; ++q) kmn = umin64(kmn, S.red[lc][q][1]);
             const double mn = ordbits_inv(kmn);
-            S.th[lc][1] = (mn >= P.eps) ? 1.0 : ratio01(reb - P.eps, reb - mn) * kMargin;
+            S.th[lc][1] = ge_pos_bits(mn, P.eps) ? 1.0 : ratio01(reb - P.eps, reb - mn) * kMargin;
         }
         __syncthreads();
         th2 = S.th[lc][1];
     }
     // 6. rescale towards the average
-    bool limited = (th1 < 1.0) || (th2 < 1.0);
+    bool limited = below_one(th1) || below_one(th2);
     double uo[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) uo[c] = u[c];
     auto apply = [&](double t2) {
         if constexpr (PHYS == PH_EULER) {
-            double r = th1 < 1.0 ? th1 * (uo[0] - ub[0]) + ub[0] : uo[0];
-            u[0] = t2 < 1.0 ? t2 * (r - ub[0]) + ub[0] : r;
+            double r = below_one(th1) ? th1 * (uo[0] - ub[0]) + ub[0] : uo[0];
+            u[0] = below_one(t2) ? t2 * (r - ub[0]) + ub[0] : r;
 #pragma unroll
-            for (int c = 1; c < M; ++c) u[c] = t2 < 1.0 ? t2 * (uo[c] - ub[c]) + ub[c] : uo[c];
+            for (int c = 1; c < M; ++c) u[c] = below_one(t2) ? t2 * (uo[c] - ub[c]) + ub[c] : uo[c];
         } else {
             double t = th1 * t2;
             u[0] = t < 1.0 ? t * (uo[0] - ub[0]) + ub[0] : uo[0];
