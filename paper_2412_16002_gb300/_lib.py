@@ -85,6 +85,7 @@ SYMBOLS = {
     "crkdg_troubled_flags": (C.c_int, [_H, C.c_void_p, C.c_int]),
     "crkdg_cell_averages": (C.c_int, [_H, C.c_void_p, C.c_int]),
     "crkdg_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "crkdg_mlp_fault": (C.c_int, [C.POINTER(C.c_int)]),
     "crkdg_mlp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "crkdg_mlp_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.c_void_p]),
     "crkdg_set_mlp": (C.c_int, [_H, C.c_void_p]),
