@@ -122,6 +122,17 @@ void build_tables(NodalTables *tab) {
             T.w1f[a] = (float)T.w1[a];
         }
         for (int q = 0; q < MAXN * MAXN; ++q) T.w2f[q] = (float)T.w2[q];
+        for (int q = 0; q < n * n; ++q) {
+            const int qa = q % n, qb = q / n;
+            T.mom2[q] = (3.0 * T.w1[qa]) * T.w1[qb];
+            for (int d = 0; d < 2; ++d) {
+                const int along = d == 0 ? qa : qb, across = d == 0 ? qb : qa;
+                T.trw2[d][0][q] = T.w1[across] * T.lp[along];
+                T.trw2[d][1][q] = T.w1[across] * T.lm[along];
+                T.pm2[d][q] = ((3.0 * T.w1[qa]) * T.w1[qb]) * T.xg[along];
+            }
+        }
+        for (int a = 0; a < n; ++a) T.pm1[a] = (3.0 * T.w1[a]) * T.xg[a];
     }
 }
 

@@ -987,6 +987,27 @@ __device__ __forceinline__ double minmod3d(double a, double b, double c) {
     if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
     return 0.0;
 }
+// minmod3d on the integer units (the same result): for values of one sign the one of
+// least magnitude has the smallest bit pattern
+__device__ __forceinline__ bool negative_bits(double x) {
+    const unsigned long long b = dbits(x);
+    return b > 0x8000000000000000ull && b <= 0xfff0000000000000ull;
+}
+__device__ __forceinline__ double minmod3_bits(double a, double b, double c) {
+    const bool pos = positive_bits(a) && positive_bits(b) && positive_bits(c);
+    const bool neg = negative_bits(a) && negative_bits(b) && negative_bits(c);
+    return (pos || neg) ? bitsd(umin64(dbits(a), umin64(dbits(b), dbits(c)))) : 0.0;
+}
+// The TVB-modified minmod test of one face-averaged trace deviation t against the
+// neighbour differences dp, dm and the threshold thr: true when minmod changes t, i.e.
+// (|t| <= thr ? t : minmod(t, dp, dm)) != t, on the integer units.  thr_ok = thr >= 0.
+__device__ __forceinline__ bool tvb_changes(double t, double dp, double dm, double thr, bool thr_ok) {
+    constexpr unsigned long long kAbs = 0x7fffffffffffffffull;
+    if (thr_ok && (dbits(t) & kAbs) <= (dbits(thr) & kAbs)) return false;
+    if (isnan_bits(t)) return true;  // a NaN deviation compares unequal to itself
+    const unsigned long long m = dbits(minmod3_bits(t, dp, dm)), tb = dbits(t);
+    return m != tb && ((m | tb) << 1) != 0ull;  // +0 and -0 compare equal
+}
 
 // Average of component c of the neighbour of `cell` across `side` (the averages are in
 // aux, [cell][m]); across a domain boundary, the boundary condition applied to the
@@ -1041,20 +1062,22 @@ __device__ __forceinline__ void trouble_body(const Params &P, const Bufs &B, int
         const double hi = nb_average<PHYS, DIM>(P, B.aux, cell, 2 * d + 1, c);
         double fr = 0.0, fl = 0.0, p1 = 0.0;
         for (int q = 0; q < NN; ++q) {
-            int qa = q % N, qb = DIM == 2 ? q / N : 0;
-            int along = d == 0 ? qa : qb, across = d == 0 ? qb : qa;
-            double wa = DIM == 2 ? T.w1[across] : 1.0;
             double v = S.u[lc][c][q];
-            fr = fma(wa * T.lp[along], v, fr);
-            fl = fma(wa * T.lm[along], v, fl);
-            p1 = fma(3.0 * T.w1[qa] * (DIM == 2 ? T.w1[qb] : 1.0) * T.xg[along], v, p1);
+            if constexpr (DIM == 2) {
+                fr = fma(T.trw2[d][0][q], v, fr);
+                fl = fma(T.trw2[d][1][q], v, fl);
+                p1 = fma(T.pm2[d][q], v, p1);
+            } else {
+                fr = fma(T.lp[q], v, fr);
+                fl = fma(T.lm[q], v, fl);
+                p1 = fma(T.pm1[q], v, p1);
+            }
         }
         double utR = fr - own, utL = own - fl;
         double dp = hi - own, dm = own - lo;
-        double mR = fabs(utR) <= thr ? utR : minmod3d(utR, dp, dm);
-        double mL = fabs(utL) <= thr ? utL : minmod3d(utL, dp, dm);
-        if (mR != utR || mL != utL) atomicOr(&sTr[lc], 1);
-        sP1[lc][d][c] = minmod3d(p1, dp, dm);
+        const bool thr_ok = thr >= 0.0;
+        if (tvb_changes(utR, dp, dm, thr, thr_ok) || tvb_changes(utL, dp, dm, thr, thr_ok)) atomicOr(&sTr[lc], 1);
+        sP1[lc][d][c] = minmod3_bits(p1, dp, dm);
     }
     __syncthreads();
     bool troubled = active && (P.ind_stage >= 2 ? B.tflags[cell] != 0 : sTr[lc] != 0);
@@ -1149,14 +1172,19 @@ __device__ __forceinline__ void features_body(const Params &P, const Bufs &B, in
         float *f = B.feat + (size_t)cell * 44;
 #pragma unroll
         for (int c = 0; c < M; ++c) {
-            double mean = 0.0, mx = -INFINITY, mn = INFINITY, amax = 0.0;
+            double mean = 0.0;
+            unsigned long long kmx = kKeyNegInf, kmn = kKeyPosInf, kab = 0ull;
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
                 mean += v[q][c];
-                mx = fmax(mx, v[q][c]);
-                mn = fmin(mn, v[q][c]);
-                amax = fmax(amax, fabs(v[q][c]));
+                if (!isnan_bits(v[q][c])) {  // fmax / fmin ignore NaN
+                    const unsigned long long k = ordbits(v[q][c]);
+                    kmx = umax64(kmx, k);
+                    kmn = umin64(kmn, k);
+                    kab = umax64(kab, dbits(v[q][c]) & 0x7fffffffffffffffull);
+                }
             }
+            const double mx = ordbits_inv(kmx), mn = ordbits_inv(kmn), amax = bitsd(kab);
             mean /= 9.0;
             double scale = 1.0 / (fmax(mx - mn, thr) + (1e-6 * amax + 1e-30));
 #pragma unroll
@@ -1166,7 +1194,7 @@ __device__ __forceinline__ void features_body(const Params &P, const Bufs &B, in
 #pragma unroll
             for (int q = 0; q < NN; ++q) {
                 int qa = q % N, qb = q / N;
-                double w = 3.0 * T.w1[qa] * T.w1[qb] * u[q];
+                double w = T.mom2[q] * u[q];
                 cx = fma(w, T.xg[qa], cx);
                 cy = fma(w, T.xg[qb], cy);
             }
@@ -1182,22 +1210,18 @@ __device__ __forceinline__ void features_body(const Params &P, const Bufs &B, in
             const double thr = P.tvb_M * h * h;
             const double *lo = v[d == 0 ? 3 : 1], *hi = v[d == 0 ? 5 : 7], *own = v[4];
 #pragma unroll
+            const bool thr_ok = thr >= 0.0;
             for (int c = 0; c < M; ++c) {
                 const double *uc = B.unew + ((size_t)c * P.ncell + cell) * NN;
                 double fr = 0.0, fl = 0.0;
                 for (int q = 0; q < NN; ++q) {
-                    int qa = q % N, qb = q / N;
-                    int along = d == 0 ? qa : qb, across = d == 0 ? qb : qa;
-                    double wa = T.w1[across];
                     double val = uc[q];
-                    fr = fma(wa * T.lp[along], val, fr);
-                    fl = fma(wa * T.lm[along], val, fl);
+                    fr = fma(T.trw2[d][0][q], val, fr);
+                    fl = fma(T.trw2[d][1][q], val, fl);
                 }
                 double utR = fr - own[c], utL = own[c] - fl;
                 double dp = hi[c] - own[c], dm = own[c] - lo[c];
-                double mR = fabs(utR) <= thr ? utR : minmod3d(utR, dp, dm);
-                double mL = fabs(utL) <= thr ? utL : minmod3d(utL, dp, dm);
-                if (mR != utR || mL != utL) trouble = 1;
+                if (tvb_changes(utR, dp, dm, thr, thr_ok) || tvb_changes(utL, dp, dm, thr, thr_ok)) trouble = 1;
             }
         }
         if (B.tflags) B.tflags[cell] = trouble;

@@ -44,6 +44,12 @@ struct NodalTables {
     double Igl[MAXN][MAXN];     // Igl[alpha][a] = l_a(xl_alpha)   (S_K interpolation)
     double w1[MAXN];            // w_a / 2                          (1D average weights)
     double w2[MAXN * MAXN];     // (w_a/2)(w_b/2) at node b*n+a      (2D average weights)
+    // products of the tables the troubled-cell and feature kernels weigh node values by,
+    // host-computed with the kernels' association of the factors (the sums are unchanged)
+    double mom2[MAXN * MAXN];        // (3 w1_a) w1_b at node b*n+a: 2D first moments
+    double trw2[2][2][MAXN * MAXN];  // [dir][R, L] w1_across l_along(+1 / -1): 2D face averages
+    double pm2[2][MAXN * MAXN];      // [dir] ((3 w1_a) w1_b) x_along: 2D first moments along dir
+    double pm1[MAXN];                // (3 w1_a) x_a: 1D first moment
     // FP32 copies for the split-precision path
     float Dhatf[MAXN][MAXN], lmf[MAXN], lpf[MAXN], liftmf[MAXN], liftpf[MAXN], Iglf[MAXN][MAXN];
     float w1f[MAXN], w2f[MAXN * MAXN];
