@@ -131,6 +131,8 @@ void build_tables(NodalTables *tab) {
                 T.trw2[d][1][q] = T.w1[across] * T.lm[along];
                 T.pm2[d][q] = ((3.0 * T.w1[qa]) * T.w1[qb]) * T.xg[along];
             }
+            T.momxf[q] = (float)(T.mom2[q] * T.xg[qa]);
+            T.momyf[q] = (float)(T.mom2[q] * T.xg[qb]);
         }
         for (int a = 0; a < n; ++a) T.pm1[a] = (3.0 * T.w1[a]) * T.xg[a];
     }
@@ -273,6 +275,7 @@ MixBufs base_xbufs(const crkdg_ctx *h) {
     X.aux = h->aux;
     X.tflags = h->tflags;
     X.prob = h->prob;
+    X.feat = h->feat;
     X.ntrb = &h->scal->ntrb;
     return X;
 }
@@ -669,7 +672,14 @@ crkdg_status crkdg_step(crkdg_t h, double dt, const crkdg_tableau *tab, crkdg_st
                     // decision is taken in the troubled-cell pass, unless features are wanted:
                     // then the FP64 feature kernel takes it on the merged nodal values
                     const bool learned = h->opt.indicator == CRKDG_IND_MLP;
-                    if (learned || h->harvest) {
+                    if (learned && !h->harvest) {
+                        // features from the split state; the troubled-cell pass takes the plain
+                        // decision itself and combines it with the network's
+                        CK(h, launch_x(h, KX_FEATURES, P, base_xbufs(h)));
+                        if (crkdg_mlp_forward(h->mlp, h->feat, h->ncell, h->prob, h->st) != CRKDG_OK)
+                            return fail(h, CRKDG_E_CUDA, "step: MLP forward failed");
+                        P.ind_stage = 4;
+                    } else if (h->harvest) {
                         MixBufs Xn = base_xbufs(h);
                         Xn.ub = h->xub[1 - h->xcur];
                         Xn.dv = h->xdv[1 - h->xcur];

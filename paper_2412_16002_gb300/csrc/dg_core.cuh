@@ -1123,6 +1123,70 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_trouble(Params P, Buf
 // 1e-6 max|v|, and the cell's first Legendre moments over the same den.  Layout
 // [cell][44]: 36 normalised averages ([comp][9], row-major, centre 4), then 8
 // normalised moments ([comp][x, y]).  Reads unew and the averages in aux.
+// The 36 stencil features of a 2D Euler cell (per component the 3x3 averages minus their
+// mean, times scale = 1 / (max(range, M hx hy) + 1e-6 max|v|)) from the cell averages
+// aux[cell][m]; v receives the stencil averages and scale the per-component factor.
+template <int PHYS>
+__device__ __forceinline__ void stencil_features(const Params &P, const double *aux, int cell, float *f,
+                                                 double (&v)[9][ncomp(PHYS, 2)], double (&scale)[ncomp(PHYS, 2)]) {
+    constexpr int DIM = 2, M = ncomp(PHYS, 2);
+    // 3x3 stencil; a position outside the domain takes the nearest in-domain cell's
+    // average with the boundary state of each crossed side applied (x side first)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            int cx = cell;
+            bool xout = false, yout = false;
+            if (dx != 0) {
+                int nb = neighbour(P, cell, dx < 0 ? 0 : 1);
+                if (nb >= 0) cx = nb; else xout = true;
+            }
+            int cy = cx;
+            if (dy != 0) {
+                int nb = neighbour(P, cx, dy < 0 ? 2 : 3);
+                if (nb >= 0) cy = nb; else yout = true;
+            }
+            double val[M], tmp[M];
+#pragma unroll
+            for (int c = 0; c < M; ++c) val[c] = aux[(size_t)cy * M + c];
+            if (xout) {
+                boundary_state<PHYS, DIM>(P, dx < 0 ? 0 : 1, val, tmp);
+#pragma unroll
+                for (int c = 0; c < M; ++c) val[c] = tmp[c];
+            }
+            if (yout) {
+                boundary_state<PHYS, DIM>(P, dy < 0 ? 2 : 3, val, tmp);
+#pragma unroll
+                for (int c = 0; c < M; ++c) val[c] = tmp[c];
+            }
+#pragma unroll
+            for (int c = 0; c < M; ++c) v[(dy + 1) * 3 + (dx + 1)][c] = val[c];
+        }
+    // per component: (v - mean) / den and slopes / den, den = max(range, M hx hy) + 1e-6 max|v|
+    const double thr = P.tvb_M * (2.0 / P.rhx) * (2.0 / P.rhy);
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+        double mean = 0.0;
+        unsigned long long kmx = kKeyNegInf, kmn = kKeyPosInf, kab = 0ull;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            mean += v[q][c];
+            if (!isnan_bits(v[q][c])) {  // fmax / fmin ignore NaN
+                const unsigned long long k = ordbits(v[q][c]);
+                kmx = umax64(kmx, k);
+                kmn = umin64(kmn, k);
+                kab = umax64(kab, dbits(v[q][c]) & 0x7fffffffffffffffull);
+            }
+        }
+        const double mx = ordbits_inv(kmx), mn = ordbits_inv(kmn), amax = bitsd(kab);
+        mean /= 9.0;
+        scale[c] = 1.0 / (fmax(mx - mn, thr) + (1e-6 * amax + 1e-30));
+#pragma unroll
+        for (int q = 0; q < 9; ++q) f[c * 9 + q] = (float)((v[q][c] - mean) * scale[c]);
+    }
+}
+
 template <int DIM, int N, int PHYS>
 __device__ __forceinline__ void features_body(const Params &P, const Bufs &B, int blk) {
     constexpr int M = ncomp(PHYS, DIM);
@@ -1133,62 +1197,11 @@ __device__ __forceinline__ void features_body(const Params &P, const Bufs &B, in
     } else {
         if (cell >= P.ncell) return;
         const NodalTables &T = c_tab[N - 2];
-        // 3x3 stencil; a position outside the domain takes the nearest in-domain cell's
-        // average with the boundary state of each crossed side applied (x side first)
-        double v[9][M];
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-                int cx = cell;
-                bool xout = false, yout = false;
-                if (dx != 0) {
-                    int nb = neighbour(P, cell, dx < 0 ? 0 : 1);
-                    if (nb >= 0) cx = nb; else xout = true;
-                }
-                int cy = cx;
-                if (dy != 0) {
-                    int nb = neighbour(P, cx, dy < 0 ? 2 : 3);
-                    if (nb >= 0) cy = nb; else yout = true;
-                }
-                double val[M], tmp[M];
-#pragma unroll
-                for (int c = 0; c < M; ++c) val[c] = B.aux[(size_t)cy * M + c];
-                if (xout) {
-                    boundary_state<PHYS, DIM>(P, dx < 0 ? 0 : 1, val, tmp);
-#pragma unroll
-                    for (int c = 0; c < M; ++c) val[c] = tmp[c];
-                }
-                if (yout) {
-                    boundary_state<PHYS, DIM>(P, dy < 0 ? 2 : 3, val, tmp);
-#pragma unroll
-                    for (int c = 0; c < M; ++c) val[c] = tmp[c];
-                }
-#pragma unroll
-                for (int c = 0; c < M; ++c) v[(dy + 1) * 3 + (dx + 1)][c] = val[c];
-            }
-        // per component: (v - mean) / den and slopes / den, den = max(range, M hx hy) + 1e-6 max|v|
-        const double thr = P.tvb_M * (2.0 / P.rhx) * (2.0 / P.rhy);
+        double v[9][M], scale[M];
+        stencil_features<PHYS>(P, B.aux, cell, B.feat + (size_t)cell * 44, v, scale);
         float *f = B.feat + (size_t)cell * 44;
 #pragma unroll
         for (int c = 0; c < M; ++c) {
-            double mean = 0.0;
-            unsigned long long kmx = kKeyNegInf, kmn = kKeyPosInf, kab = 0ull;
-#pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                mean += v[q][c];
-                if (!isnan_bits(v[q][c])) {  // fmax / fmin ignore NaN
-                    const unsigned long long k = ordbits(v[q][c]);
-                    kmx = umax64(kmx, k);
-                    kmn = umin64(kmn, k);
-                    kab = umax64(kab, dbits(v[q][c]) & 0x7fffffffffffffffull);
-                }
-            }
-            const double mx = ordbits_inv(kmx), mn = ordbits_inv(kmn), amax = bitsd(kab);
-            mean /= 9.0;
-            double scale = 1.0 / (fmax(mx - mn, thr) + (1e-6 * amax + 1e-30));
-#pragma unroll
-            for (int q = 0; q < 9; ++q) f[c * 9 + q] = (float)((v[q][c] - mean) * scale);
             const double *u = B.unew + ((size_t)c * P.ncell + cell) * NN;
             double cx = 0.0, cy = 0.0;
 #pragma unroll
@@ -1198,8 +1211,8 @@ __device__ __forceinline__ void features_body(const Params &P, const Bufs &B, in
                 cx = fma(w, T.xg[qa], cx);
                 cy = fma(w, T.xg[qb], cy);
             }
-            f[36 + 2 * c] = (float)(cx * scale);
-            f[37 + 2 * c] = (float)(cy * scale);
+            f[36 + 2 * c] = (float)(cx * scale[c]);
+            f[37 + 2 * c] = (float)(cy * scale[c]);
         }
         // the plain indicator's decision for this cell, with the troubled-cell kernel's
         // arithmetic: the label of harvested features and the fallback of the learned flags
@@ -1209,8 +1222,8 @@ __device__ __forceinline__ void features_body(const Params &P, const Bufs &B, in
             const double h = 2.0 / (d == 0 ? P.rhx : P.rhy);
             const double thr = P.tvb_M * h * h;
             const double *lo = v[d == 0 ? 3 : 1], *hi = v[d == 0 ? 5 : 7], *own = v[4];
-#pragma unroll
             const bool thr_ok = thr >= 0.0;
+#pragma unroll
             for (int c = 0; c < M; ++c) {
                 const double *uc = B.unew + ((size_t)c * P.ncell + cell) * NN;
                 double fr = 0.0, fl = 0.0;

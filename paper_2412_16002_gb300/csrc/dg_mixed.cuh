@@ -927,8 +927,9 @@ __device__ __forceinline__ int tvb_screen(float s, float E, float thr, float dp,
 
 // Troubled-cell pass of the split representation, on the unlimited u^{n+1} (X.ub_n,
 // X.dv_n, rewritten in place) with its averages in aux.  The decision is the plain
-// indicator's (ind_stage 0: taken here; 2: read from tflags; 3: combined with the
-// learned probabilities, p > 0.6 troubled, p < 0.4 smooth).  Taken here, it is the FP64
+// indicator's (ind_stage 0: taken here; 2: read from tflags; 3: read from tflags and
+// combined with the learned probabilities, p > 0.6 troubled, p < 0.4 smooth; 4: taken
+// here and combined with the learned probabilities).  Taken here, it is the FP64
 // decision on the merged nodal values ubar + (double)(dev - dbar): the face-averaged
 // trace deviations are estimated in FP32 from the deviations alone (the average
 // cancels in them), with the bound
@@ -975,7 +976,7 @@ __global__ void __launch_bounds__(C::NT) k_trouble_x(Params P, MixBufs X) {
         const double dp = hi - own, dm = own - lo;
         sD[lc][d][c][0] = dp;
         sD[lc][d][c][1] = dm;
-        if (P.ind_stage != 0) continue;
+        if (P.ind_stage != 0 && P.ind_stage != 4) continue;
         const float mean = S.mean[lc][c];
         float sR = 0.0f, sL = 0.0f, bR = 0.0f, bL = 0.0f, aR = 0.0f, aL = 0.0f, dmax = 0.0f;
 #pragma unroll
@@ -1022,8 +1023,8 @@ __global__ void __launch_bounds__(C::NT) k_trouble_x(Params P, MixBufs X) {
         if (trouble) atomicOr(&sTr[lc], 1);
     }
     __syncthreads();
-    bool troubled = active && (P.ind_stage == 0 ? sTr[lc] != 0 : X.tflags[cell] != 0);
-    if (P.ind_stage == 3 && active) {
+    bool troubled = active && ((P.ind_stage == 0 || P.ind_stage == 4) ? sTr[lc] != 0 : X.tflags[cell] != 0);
+    if ((P.ind_stage == 3 || P.ind_stage == 4) && active) {
         const float pr = X.prob[cell];
         troubled = pr > 0.6f ? true : (pr < 0.4f ? false : troubled);
     }
@@ -1200,6 +1201,46 @@ __global__ void __launch_bounds__(C::NT) k_scan_x(Params P, MixBufs X) {
     }
 }
 
+// Features of the learned indicator from the split state of the unlimited u^{n+1}
+// (2D Euler; one thread per cell): the stencil part from the FP64 averages in aux, as
+// the FP64 feature kernel; the first moments c_10, c_01 from the FP32 deviations,
+// sum_q ((3 w_a) w_b) x_a (dev_q - dbar) (the average's contribution is zero), in FP32.
+// The plain decision is left to the troubled-cell pass (ind_stage 4).
+template <class C>
+__global__ void __launch_bounds__(128) k_features_x(Params P, MixBufs X) {
+    constexpr int DIM = C::D, N = C::NP, PHYS = C::PH, M = C::M, NN = C::NN;
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if constexpr (DIM != 2 || PHYS != PH_EULER) {
+        return;
+    } else {
+        if (cell >= P.ncell) return;
+        const NodalTables &T = c_tab[N - 2];
+        double v[9][M], scale[M];
+        float *f = X.feat + (size_t)cell * 44;
+        stencil_features<PHYS>(P, X.aux, cell, f, v, scale);
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            const float *dv = X.dv_n + ((size_t)c * P.ncell + cell) * NN;
+            float d[NN];
+#pragma unroll
+            for (int q = 0; q < NN; ++q) d[q] = dv[q];
+            float dbar = 0.0f;
+#pragma unroll
+            for (int q = 0; q < NN; ++q) dbar = fmaf(T.w2f[q], d[q], dbar);
+            float cx = 0.0f, cy = 0.0f;
+#pragma unroll
+            for (int q = 0; q < NN; ++q) {
+                const float e = d[q] - dbar;
+                cx = fmaf(T.momxf[q], e, cx);
+                cy = fmaf(T.momyf[q], e, cy);
+            }
+            const float sc = (float)scale[c];
+            f[36 + 2 * c] = cx * sc;
+            f[37 + 2 * c] = cy * sc;
+        }
+    }
+}
+
 // Cell averages: aux[cell][m] = ubar
 template <class C>
 __global__ void k_avg_x(Params P, MixBufs X) {
@@ -1220,6 +1261,7 @@ cudaError_t launch_one_x(int kernel, int nblocks, cudaStream_t st, const Params 
     case KX_FINAL: k_final_x<C><<<nblocks, C::NT, 0, st>>>(P, X); break;
     case KX_SCAN: k_scan_x<C><<<nblocks, C::NT, 0, st>>>(P, X); break;
     case KX_TROUBLE: k_trouble_x<C><<<nblocks, C::NT, 0, st>>>(P, X); break;
+    case KX_FEATURES: k_features_x<C><<<(P.ncell + 127) / 128, 128, 0, st>>>(P, X); break;
     case KX_AVG: {
         int tot = P.ncell * C::M;
         k_avg_x<C><<<(tot + 255) / 256, 256, 0, st>>>(P, X);

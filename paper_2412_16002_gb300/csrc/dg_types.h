@@ -50,6 +50,7 @@ struct NodalTables {
     double trw2[2][2][MAXN * MAXN];  // [dir][R, L] w1_across l_along(+1 / -1): 2D face averages
     double pm2[2][MAXN * MAXN];      // [dir] ((3 w1_a) w1_b) x_along: 2D first moments along dir
     double pm1[MAXN];                // (3 w1_a) x_a: 1D first moment
+    float momxf[MAXN * MAXN], momyf[MAXN * MAXN];  // FP32 ((3 w1_a) w1_b) x_a, ... x_b: 2D first moments
     // FP32 copies for the split-precision path
     float Dhatf[MAXN][MAXN], lmf[MAXN], lpf[MAXN], liftmf[MAXN], liftpf[MAXN], Iglf[MAXN][MAXN];
     float w1f[MAXN], w2f[MAXN * MAXN];
@@ -84,7 +85,8 @@ struct Params {
     double tvb_M;     // TVB constant of the plain indicator
     int ind_stage;    // troubled-cell kernel: 0 decide and limit, 2 limit the given flags (the feature
                       // kernel decided), 3 combine the given plain flags with the learned
-                      // probabilities, then limit
+                      // probabilities, then limit; 4 (split path) decide, combine with the
+                      // learned probabilities, then limit
     ParamsF f;        // split-precision kernels only
 };
 
@@ -127,12 +129,13 @@ struct MixBufs {
     unsigned long long *nlim, *thmin, *a0, *ord;
     double *aux;
     int *tflags;              // troubled-cell flags (indicator on)
-    const float *prob;        // learned probabilities (ind_stage 3)
+    const float *prob;        // learned probabilities (ind_stage 3, 4)
+    float *feat;              // learned indicator's features [cell][44] (k_features_x)
     unsigned long long *ntrb; // troubled cells
 };
 
 enum MixKernelId { KX_SPLIT = 0, KX_MERGE = 1, KX_LIMIT = 2, KX_INNER = 3, KX_FINAL = 4, KX_SCAN = 5, KX_AVG = 6,
-                   KX_TROUBLE = 7 };
+                   KX_TROUBLE = 7, KX_FEATURES = 8 };
 
 // ---------------------------------------------------------------- ensembles (2D Euler)
 

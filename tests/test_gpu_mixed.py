@@ -290,3 +290,33 @@ def test_mixed_tvb_1d_against_oracle():
     print(f"blast1d_256_p2 split + TVB: {flagged} oracle flags, {differ} differ; L1 gap {gap:.3e}")
     assert flagged > 0 and differ <= 0.005 * 5 * 256
     assert gap < 1e-5
+
+
+def test_mixed_learned_features_from_the_split_state():
+    """The split path's learned indicator takes its features from the split state (the
+    stencil part from the FP64 averages, the first moments in FP32 from the deviations) and
+    leaves the plain decision to the troubled-cell pass.  With harvesting on, the same step
+    instead merges to FP64 nodal values and runs the FP64 feature kernel.  The two feature
+    sets agree to 1e-5 (features are O(1)); with a random network the learned flags and the
+    states then agree exactly (a flag could move only for a probability within ~1e-7 of 0.4
+    or 0.6)."""
+    from oracle import mlp
+
+    ga, wl = _riemann_pair("mixed", "mlp", tvb_M=10.0)
+    gb, _ = _riemann_pair("mixed", "mlp", tvb_M=10.0)
+    theta = torch.tensor(mlp.init_params(3), dtype=torch.float32, device="cuda")
+    ga.set_mlp(theta)
+    gb.set_mlp(theta)
+    gb.set_harvest(True)
+    flagged = 0
+    for _ in range(8):
+        dt = ga.max_dt(wl.cfl)
+        ia = ga.step(dt, wl.tableau)
+        ib = gb.step(dt, wl.tableau)
+        fa, fb = ga.last_features(), gb.last_features()
+        assert np.abs(fa - fb).max() < 1e-5, np.abs(fa - fb).max()
+        assert np.array_equal(ga.troubled_flags(), gb.troubled_flags())
+        assert ia["troubled"] == ib["troubled"]
+        flagged += ia["troubled"]
+    assert flagged > 0
+    assert np.array_equal(ga.get_state(), gb.get_state())
