@@ -74,15 +74,32 @@ __device__ __forceinline__ double fmax_nonneg(double a, double b) {
     return bitsd(umax64(dbits(a), dbits(b)));
 }
 
+// 1/x by the Newton-Raphson iteration r <- r + r (1 - x r) (quadratic convergence) from
+// the hardware's approximate reciprocal (rcp.approx.ftz.f64); two steps reach double
+// precision (within an ulp of the rounded quotient).  Arguments outside [2^-1000,
+// 2^1001) in magnitude (zero, subnormal, huge, inf, NaN) take the IEEE division.  On this
+// part a dependent FP64 operation costs 64 cycles and the IEEE reciprocal about seven.
+__device__ __forceinline__ double recip_nr(double x) {
+    const unsigned e = (unsigned)(dbits(x) >> 52) & 0x7ffu;
+    if (e < 1023u - 1000u || e > 1023u + 1000u) return 1.0 / x;
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double t = fma(-x, r, 1.0);
+    r = fma(r, t, r);
+    t = fma(-x, r, 1.0);
+    return fma(r, t, r);
+}
+
 // theta = num/den clamped to [0, 1]; a non-positive denominator gives 0
 __device__ __forceinline__ double ratio01(double num, double den) {
     if (!(den > 0.0)) return 0.0;
-    double t = num / den;
+    double t = num * recip_nr(den);
     if (!(t >= 0.0)) t = 0.0;
     return t > 1.0 ? 1.0 : t;
 }
 
 // ----------------------------------------------------------------------------- physics
+
 
 // Euler flux . e_dir and spectral radius given ri = 1/rho, written with explicit
 // roundings (fma, __dmul_rn, __dadd_rn): the compiler cannot contract them
@@ -124,7 +141,7 @@ __device__ __forceinline__ void flux_dir(const Params &P, const double *u, int d
     } else if constexpr (PHYS == PH_BURG) {
         f[0] = 0.5 * u[0] * u[0];
     } else {
-        euler_flux_ri<DIM>(P, u, dir, 1.0 / u[0], f);
+        euler_flux_ri<DIM>(P, u, dir, recip_nr(u[0]), f);
     }
 }
 
@@ -137,7 +154,7 @@ __device__ __forceinline__ void flux_xy(const Params &P, const double *u, double
     } else if constexpr (PHYS == PH_BURG) {
         fx[0] = fy[0] = 0.5 * u[0] * u[0];
     } else {
-        double ri = 1.0 / u[0];
+        double ri = recip_nr(u[0]);
         double wx = u[1] * ri, wy = u[2] * ri;
         double p = (P.gamma - 1.0) * (u[3] - 0.5 * (u[1] * wx + u[2] * wy));
         double ep = u[3] + p;
@@ -160,7 +177,7 @@ __device__ __forceinline__ double speed_dir(const Params &P, const double *u, in
     } else if constexpr (PHYS == PH_BURG) {
         return fabs(u[0]);
     } else {
-        return euler_speed_ri<DIM>(P, u, dir, 1.0 / u[0]);
+        return euler_speed_ri<DIM>(P, u, dir, recip_nr(u[0]));
     }
 }
 
@@ -185,7 +202,7 @@ __device__ __forceinline__ double speed_dir_ri(const Params &P, const double *u,
 }
 template <int PHYS>
 __device__ __forceinline__ double recip_rho(const double *u) {
-    if constexpr (PHYS == PH_EULER) return 1.0 / u[0];
+    if constexpr (PHYS == PH_EULER) return recip_nr(u[0]);
     return 0.0;
 }
 // both for one state; returns the spectral radius
@@ -203,7 +220,7 @@ __device__ __forceinline__ double flux_speed_dir(const Params &P, const double *
 template <int PHYS, int DIM>
 __device__ __forceinline__ double sk_rate(const Params &P, const double *u) {
     if constexpr (PHYS == PH_EULER) {
-        double ri = 1.0 / u[0];
+        double ri = recip_nr(u[0]);
         double kin = DIM == 1 ? u[1] * u[1] : u[1] * u[1] + u[2] * u[2];
         double p = (P.gamma - 1.0) * (u[DIM + 1] - 0.5 * kin * ri);
         double c2 = P.gamma * p * ri;
@@ -222,7 +239,7 @@ __device__ __forceinline__ double sk_rate(const Params &P, const double *u) {
 template <int DIM>
 __device__ __forceinline__ double rho_e(const double *u) {
     double kin = DIM == 1 ? u[1] * u[1] : u[1] * u[1] + u[2] * u[2];
-    return u[DIM + 1] - 0.5 * kin / u[0];
+    return u[DIM + 1] - (0.5 * kin) * recip_nr(u[0]);
 }
 
 // averages in B (scalar) or B^eps (Euler, rho >= eps and rho e >= eps); NaN fails
@@ -1181,7 +1198,7 @@ __device__ __forceinline__ void stencil_features(const Params &P, const double *
         }
         const double mx = ordbits_inv(kmx), mn = ordbits_inv(kmn), amax = bitsd(kab);
         mean /= 9.0;
-        scale[c] = 1.0 / (fmax(mx - mn, thr) + (1e-6 * amax + 1e-30));
+        scale[c] = recip_nr(fmax(mx - mn, thr) + (1e-6 * amax + 1e-30));
 #pragma unroll
         for (int q = 0; q < 9; ++q) f[c * 9 + q] = (float)((v[q][c] - mean) * scale[c]);
     }
