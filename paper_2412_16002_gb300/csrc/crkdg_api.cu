@@ -212,6 +212,7 @@ Params base_params(const crkdg_ctx *h) {
     P.hi = h->bounds.hi;
     P.eps = h->bounds.eps;
     P.tvb_M = h->opt.tvb_M;
+    tvb_thresholds(P);
     for (int s = 0; s < 4; ++s) {
         P.bc[s] = (h->dim == 1 && s >= 2) ? BC_OUTFLOW : h->mesh.bc[s];
         for (int c = 0; c < MAXM; ++c) P.bcs[s][c] = h->mesh.bc_state[s][c];
@@ -291,6 +292,8 @@ void fill_f32(Params &P) {
     F.lo = (float)P.lo;
     F.hi = (float)P.hi;
     F.eps = (float)P.eps;
+    F.thr[0] = (float)P.thr[0];
+    F.thr[1] = (float)P.thr[1];
     for (int s = 0; s < 4; ++s)
         for (int c = 0; c < MAXM; ++c) F.bcs[s][c] = (float)P.bcs[s][c];
     for (int i = 0; i < MAXS; ++i) {

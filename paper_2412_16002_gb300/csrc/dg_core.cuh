@@ -999,17 +999,14 @@ __global__ void k_avg(Params P, Bufs B) {
     B.aux[t] = s;
 }
 
-__device__ __forceinline__ double minmod3d(double a, double b, double c) {
-    if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(a, fmin(b, c));
-    if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
-    return 0.0;
-}
-// minmod3d on the integer units (the same result): for values of one sign the one of
-// least magnitude has the smallest bit pattern
+// x < 0.0 (false for -0 and NaN)
 __device__ __forceinline__ bool negative_bits(double x) {
     const unsigned long long b = dbits(x);
     return b > 0x8000000000000000ull && b <= 0xfff0000000000000ull;
 }
+// minmod(a, b, c): the argument of least magnitude when all three share one sign, else 0,
+// on the integer units (for values of one sign the one of least magnitude has the
+// smallest bit pattern)
 __device__ __forceinline__ double minmod3_bits(double a, double b, double c) {
     const bool pos = positive_bits(a) && positive_bits(b) && positive_bits(c);
     const bool neg = negative_bits(a) && negative_bits(b) && negative_bits(c);
@@ -1072,8 +1069,7 @@ __device__ __forceinline__ void trouble_body(const Params &P, const Bufs &B, int
     // decision and the limited first moment of its pairs
     for (int j = node; j < DIM * M && active; j += NN) {
         const int d = j / M, c = j - d * M;
-        const double h = 2.0 / (d == 0 ? P.rhx : P.rhy);
-        const double thr = P.tvb_M * h * h;
+        const double thr = P.thr[d];
         const double own = B.aux[(size_t)cell * M + c];
         const double lo = nb_average<PHYS, DIM>(P, B.aux, cell, 2 * d, c);
         const double hi = nb_average<PHYS, DIM>(P, B.aux, cell, 2 * d + 1, c);
@@ -1181,7 +1177,7 @@ __device__ __forceinline__ void stencil_features(const Params &P, const double *
             for (int c = 0; c < M; ++c) v[(dy + 1) * 3 + (dx + 1)][c] = val[c];
         }
     // per component: (v - mean) / den and slopes / den, den = max(range, M hx hy) + 1e-6 max|v|
-    const double thr = P.tvb_M * (2.0 / P.rhx) * (2.0 / P.rhy);
+    const double thr = P.thr_feat;
 #pragma unroll
     for (int c = 0; c < M; ++c) {
         double mean = 0.0;
@@ -1236,8 +1232,7 @@ __device__ __forceinline__ void features_body(const Params &P, const Bufs &B, in
         int trouble = 0;
 #pragma unroll
         for (int d = 0; d < 2; ++d) {
-            const double h = 2.0 / (d == 0 ? P.rhx : P.rhy);
-            const double thr = P.tvb_M * h * h;
+            const double thr = P.thr[d];
             const double *lo = v[d == 0 ? 3 : 1], *hi = v[d == 0 ? 5 : 7], *own = v[4];
             const bool thr_ok = thr >= 0.0;
 #pragma unroll

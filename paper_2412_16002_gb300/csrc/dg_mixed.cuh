@@ -997,10 +997,10 @@ __global__ void __launch_bounds__(C::NT) k_trouble_x(Params P, MixBufs X) {
         const float base = fabsf(S.ubf[lc][c]) + dmax;
         const float ER = 1.01f * (NN + 6) * 5.9604644775390625e-08f * bR + 1.1368683772161603e-13f * (1.01f + aR) * base;
         const float EL = 1.01f * (NN + 6) * 5.9604644775390625e-08f * bL + 1.1368683772161603e-13f * (1.01f + aL) * base;
-        const double h = 2.0 / (d == 0 ? P.rhx : P.rhy);
-        const double thr = P.tvb_M * h * h;
-        const float thrf = (float)thr, dpf = (float)dp, dmf = (float)dm;
-        const int sdp = dp > 0.0 ? 1 : (dp < 0.0 ? -1 : 0), sdm = dm > 0.0 ? 1 : (dm < 0.0 ? -1 : 0);
+        const double thr = P.thr[d];
+        const float thrf = P.f.thr[d], dpf = (float)dp, dmf = (float)dm;
+        const int sdp = positive_bits(dp) ? 1 : (negative_bits(dp) ? -1 : 0);
+        const int sdm = positive_bits(dm) ? 1 : (negative_bits(dm) ? -1 : 0);
         // the left deviation is ubar - avg_face(u_L) = -(face-averaged dev)
         const int rR = tvb_screen(sR, ER, thrf, dpf, dmf, sdp, sdm);
         const int rL = tvb_screen(-sL, EL, thrf, dpf, dmf, sdp, sdm);
@@ -1008,17 +1008,18 @@ __global__ void __launch_bounds__(C::NT) k_trouble_x(Params P, MixBufs X) {
         if (!trouble && (rR == 2 || rL == 2)) {  // FP64 on the merged values
             double fr = 0.0, fl = 0.0;
             for (int q = 0; q < NN; ++q) {
-                const int qa = q % N, qb = DIM == 2 ? q / N : 0;
-                const int along = d == 0 ? qa : qb, across = d == 0 ? qb : qa;
-                const double wa = DIM == 2 ? T.w1[across] : 1.0;
                 const double v = own + (double)(S.u[c][lc][q] - mean);
-                fr = fma(wa * T.lp[along], v, fr);
-                fl = fma(wa * T.lm[along], v, fl);
+                if constexpr (DIM == 2) {
+                    fr = fma(T.trw2[d][0][q], v, fr);
+                    fl = fma(T.trw2[d][1][q], v, fl);
+                } else {
+                    fr = fma(T.lp[q], v, fr);
+                    fl = fma(T.lm[q], v, fl);
+                }
             }
             const double utR = fr - own, utL = own - fl;
-            const double mR = fabs(utR) <= thr ? utR : minmod3d(utR, dp, dm);
-            const double mL = fabs(utL) <= thr ? utL : minmod3d(utL, dp, dm);
-            trouble = (mR != utR || mL != utL) ? 1 : 0;
+            const bool thr_ok = thr >= 0.0;
+            trouble = (tvb_changes(utR, dp, dm, thr, thr_ok) || tvb_changes(utL, dp, dm, thr, thr_ok)) ? 1 : 0;
         }
         if (trouble) atomicOr(&sTr[lc], 1);
     }
@@ -1039,12 +1040,10 @@ __global__ void __launch_bounds__(C::NT) k_trouble_x(Params P, MixBufs X) {
             const float mean = S.mean[lc][c];
             double p1 = 0.0;
             for (int q = 0; q < NN; ++q) {
-                const int qa = q % N, qb = DIM == 2 ? q / N : 0;
-                const int along = d == 0 ? qa : qb;
                 const double v = own + (double)(S.u[c][lc][q] - mean);
-                p1 = fma(3.0 * T.w1[qa] * (DIM == 2 ? T.w1[qb] : 1.0) * T.xg[along], v, p1);
+                p1 = fma(DIM == 2 ? T.pm2[d][q] : T.pm1[q], v, p1);
             }
-            sP1[lc][d][c] = minmod3d(p1, sD[lc][d][c][0], sD[lc][d][c][1]);
+            sP1[lc][d][c] = minmod3_bits(p1, sD[lc][d][c][0], sD[lc][d][c][1]);
         }
     }
     __syncthreads();

@@ -60,6 +60,7 @@ struct NodalTables {
 // the host at launch (the kernels then never convert a double parameter).
 struct ParamsF {
     float rhx, rhy, gamma, gm1, velx, vely, lo, hi, eps;
+    float thr[2];  // (float) of Params::thr
     float bcs[4][MAXM];
     float dtA[MAXS][MAXS];  // (float)(dt a_ij)
     float dtb[MAXS];        // (float)(dt b_i)
@@ -83,12 +84,22 @@ struct Params {
     int mode;
     int defer_limit;  // final kernel leaves the limiter to the troubled-cell kernel
     double tvb_M;     // TVB constant of the plain indicator
+    double thr[2];    // its thresholds M h_x^2, M h_y^2 (h_d = 2 / rh_d), set by tvb_thresholds
+    double thr_feat;  // M h_x h_y: the learned indicator's feature scale floor
     int ind_stage;    // troubled-cell kernel: 0 decide and limit, 2 limit the given flags (the feature
                       // kernel decided), 3 combine the given plain flags with the learned
                       // probabilities, then limit; 4 (split path) decide, combine with the
                       // learned probabilities, then limit
     ParamsF f;        // split-precision kernels only
 };
+
+// The TVB thresholds from rhx, rhy and tvb_M (host side, once per parameter set).
+inline void tvb_thresholds(Params &P) {
+    const double hx = 2.0 / P.rhx, hy = 2.0 / P.rhy;
+    P.thr[0] = P.tvb_M * hx * hx;
+    P.thr[1] = P.tvb_M * hy * hy;
+    P.thr_feat = P.tvb_M * (2.0 / P.rhx) * (2.0 / P.rhy);
+}
 
 struct Bufs {
     const double *un;   // u^n (nodal, state layout)
