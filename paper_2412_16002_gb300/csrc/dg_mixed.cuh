@@ -838,22 +838,40 @@ __global__ void __launch_bounds__(C::NT, (C::NT > 128 ? 2 : 4)) k_final_x(Params
             }
         return;
     }
-    // local conservation (Sec. 3.2): ubar^{n+1} = ubar^n - dt/|K| sum_faces sum_i b_i fhat^(i),
-    // each face point's FP64 term formed by its own thread, summed per cell in a fixed order
+    // local conservation (Sec. 3.2): ubar^{n+1} = ubar^n - dt/|K| sum_faces sum_i b_i fhat^(i).
+    // The FP32 face sums go to shared memory; one thread per (component, chunk of face
+    // points) accumulates its chunk in FP64 (fma with the FP64 weights), and the chunks
+    // are added in a fixed order: half the FP64 instructions of one thread per component
+    // summing every face point (each costs 64 cycles whatever the active lanes).
+    __syncthreads();  // every thread has read the face corrections in S.tf
 #pragma unroll
     for (int j = 0; j < FPT; ++j) {
         int fp = node + j * NN;
         if (fp < NTR)
 #pragma unroll
-            for (int c = 0; c < M; ++c) S.term[c][lc][fp] = S.kap[fp] * (double)fhs[j][c];
+            for (int c = 0; c < M; ++c) S.tf[c][lc][fp] = fhs[j][c];
+    }
+    __syncthreads();
+    constexpr int PARTS = NN >= 4 * M ? 4 : (NN >= 2 * M ? 2 : 1);
+    constexpr int CH = (NTR + PARTS - 1) / PARTS;
+    for (int k = node; k < M * PARTS; k += NN) {
+        const int c = k / PARTS, part = k - c * PARTS;
+        double g = 0.0;
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+            const int fp = part * CH + q;
+            if (fp < NTR) g = fma(S.kap[fp], (double)S.tf[c][lc][fp], g);
+        }
+        S.term[c][lc][part] = g;
     }
     __syncthreads();
     for (int c = node; c < M; c += NN) {
         float m = 0.0f;
         for (int q = 0; q < NN; ++q) m += S.w[c][lc][q];
         S.mean[lc][c] = m;
-        double g = 0.0;
-        for (int fp = 0; fp < NTR; ++fp) g += S.term[c][lc][fp];
+        double g = S.term[c][lc][0];
+#pragma unroll
+        for (int part = 1; part < PARTS; ++part) g += S.term[c][lc][part];
         double v = fma(P.dt, g, ub0[c]);
         S.ubd[lc][c] = v;
         S.ubf[lc][c] = (float)v;
