@@ -378,6 +378,7 @@ crkdg_status compute_a0(crkdg_ctx *h) {
     crkdg_status s = reset_scalars(h);
     if (s) return s;
     Params P = base_params(h);
+    P.mode = MODE_RATE;
     if (h->mixed) {
         CK(h, launch_x(h, KX_SCAN, P, base_xbufs(h)));
     } else {

@@ -952,6 +952,7 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_scan(Params P, Bufs B
     for (int c = 0; c < M; ++c) S.u[lc][c][node] = u[c];
     __syncthreads();
     double amax = 0.0, m0 = INFINITY, m1 = INFINITY;
+    const bool margins = P.mode != MODE_RATE;
 #pragma unroll
     for (int j = 0; j < C::PPT; ++j) {
         int p = node + j * NN;
@@ -959,6 +960,7 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_scan(Params P, Bufs B
             double v[M];
             sk_eval<DIM, N, M, NN>(S.u[lc], p, v);
             amax = fmax(amax, sk_rate<PHYS, DIM>(P, v));
+            if (!margins) continue;
             double a0m, a1m;
             if constexpr (PHYS == PH_EULER) {
                 a0m = v[0] - P.eps;
@@ -971,16 +973,22 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_scan(Params P, Bufs B
             m1 = (a1m == a1m) ? fmin(m1, a1m) : -INFINITY;
         }
     }
+    // extremes on the integer units: the rate is non-negative; the margins as ordbits keys
+    unsigned long long ab = dbits(amax), k0 = ordbits(m0), k1 = ordbits(m1);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-        m0 = fmin(m0, __shfl_xor_sync(0xffffffffu, m0, o));
-        m1 = fmin(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        ab = umax64(ab, __shfl_xor_sync(0xffffffffu, ab, o));
+        if (margins) {
+            k0 = umin64(k0, __shfl_xor_sync(0xffffffffu, k0, o));
+            k1 = umin64(k1, __shfl_xor_sync(0xffffffffu, k1, o));
+        }
     }
     if ((threadIdx.x & 31) == 0) {
-        if (amax > 0.0) atomicMax(B.a0, dbits(amax));
-        atomicMin(&B.ord[0], ordbits(m0));
-        atomicMin(&B.ord[1], ordbits(m1));
+        if (ab > 0ull) atomicMax(B.a0, ab);
+        if (margins) {
+            atomicMin(&B.ord[0], k0);
+            atomicMin(&B.ord[1], k1);
+        }
     }
 }
 

@@ -1183,16 +1183,26 @@ __global__ void __launch_bounds__(C::NT) k_scan_x(Params P, MixBufs X) {
     float amax = 0.0f;
     double m0 = INFINITY, m1 = INFINITY;
     const float rhx = P.f.rhx, rhy = P.f.rhy;
+    const bool margins = P.mode != MODE_RATE;
 #pragma unroll
     for (int j = 0; j < C::PPT; ++j) {
         int p = node + j * NN;
         if (p < C::NSK && active) {
             double v[M];
             float v32[M];
-            eval64_x(S, lc, p, ub, v, v32);
+            if (margins) {
+                eval64_x(S, lc, p, ub, v, v32);
+            } else {  // the FP32 value alone (eval64_x's v32)
+                float s[M];
+                sk_eval_f<C::D, C::NP, M, C::NN>(&S.u[0][lc][0], vec4<C>() ? &S.uT[0][lc][0] : nullptr,
+                                                 C::NCB * C::NN, p, s);
+#pragma unroll
+                for (int c = 0; c < M; ++c) v32[c] = S.ubf[lc][c] + (s[c] - S.mean[lc][c]);
+            }
             float r = speed_dir_f<PHYS, DIM>(P, v32, 0) * (0.5f * rhx);
             if constexpr (DIM == 2) r = fmaf(speed_dir_f<PHYS, DIM>(P, v32, 1), 0.5f * rhy, r);
             amax = fmaxf(amax, r);
+            if (!margins) continue;
             double a0m, a1m;
             if constexpr (PHYS == PH_EULER) {
                 a0m = v[0] - P.eps;
@@ -1205,16 +1215,21 @@ __global__ void __launch_bounds__(C::NT) k_scan_x(Params P, MixBufs X) {
             m1 = (a1m == a1m) ? fmin(m1, a1m) : -INFINITY;
         }
     }
+    unsigned long long k0 = ordbits(m0), k1 = ordbits(m1);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-        m0 = fmin(m0, __shfl_xor_sync(0xffffffffu, m0, o));
-        m1 = fmin(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        if (margins) {
+            k0 = umin64(k0, __shfl_xor_sync(0xffffffffu, k0, o));
+            k1 = umin64(k1, __shfl_xor_sync(0xffffffffu, k1, o));
+        }
     }
     if ((threadIdx.x & 31) == 0) {
         if (amax > 0.0f) atomicMax(X.a0, dbits((double)amax * (1.0 + 9.5367431640625e-07)));
-        atomicMin(&X.ord[0], ordbits(m0));
-        atomicMin(&X.ord[1], ordbits(m1));
+        if (margins) {
+            atomicMin(&X.ord[0], k0);
+            atomicMin(&X.ord[1], k1);
+        }
     }
 }
 

@@ -20,6 +20,7 @@ enum Mode {
     MODE_STEP = 0,   // one limited cRKDG step (Scheme 1L)
     MODE_OP_G = 1,   // inner kernel writes G(u) instead of the stage accumulation
     MODE_OP_F = 2,   // final kernel adds the face correction only (no limiter, no checks)
+    MODE_RATE = 3,   // scan kernels: the trial-step rate only (no bound margins)
 };
 
 __host__ __device__ constexpr int ncomp(int phys, int dim) { return phys == PH_EULER ? dim + 2 : 1; }
