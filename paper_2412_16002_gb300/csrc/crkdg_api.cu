@@ -213,6 +213,7 @@ Params base_params(const crkdg_ctx *h) {
     P.eps = h->bounds.eps;
     P.tvb_M = h->opt.tvb_M;
     tvb_thresholds(P);
+    screen_bounds(P);
     for (int s = 0; s < 4; ++s) {
         P.bc[s] = (h->dim == 1 && s >= 2) ? BC_OUTFLOW : h->mesh.bc[s];
         for (int c = 0; c < MAXM; ++c) P.bcs[s][c] = h->mesh.bc_state[s][c];

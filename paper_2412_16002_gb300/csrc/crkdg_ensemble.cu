@@ -426,6 +426,7 @@ crkdg_status crkdg_ensemble_create(int count, const crkdg_ens_problem *problems,
         P.eps = bounds->eps;
         P.tvb_M = e->opt.tvb_M;
         tvb_thresholds(P);
+        screen_bounds(P);
         for (int s = 0; s < 4; ++s) {
             P.bc[s] = q.mesh.bc[s];
             for (int c = 0; c < MAXM; ++c) P.bcs[s][c] = q.mesh.bc_state[s][c];

@@ -318,7 +318,10 @@ struct Cfg {
 template <class C>
 struct Smem {
     double u[C::NCB][C::M][C::NN];
-    double f[C::D][C::NCB][C::M][C::NN];
+    union {  // fluxes live inside eval_G only; the FP32 node copies inside the limiter only
+        double f[C::D][C::NCB][C::M][C::NN];
+        float uf[C::NCB][C::M][C::NN];
+    };
     double tf[C::NCB][C::NTR][C::M];
     double avg[C::NCB][C::M];
     union {  // the limiter's reductions and the final kernel's edge speeds never overlap
@@ -364,6 +367,72 @@ __device__ __forceinline__ void sk_eval(const double (&su)[M][NN], int p, double
                 v[c] = s;
             }
         }
+    }
+}
+
+// FP32 screen of the limiter.  v: the FP32 interpolation to S_K point p of the FP32
+// copies uf of the cell's FP64 node values; e: a bound on |FP64 interpolation - v| per
+// component, 4 (n + 3) 2^-24 sum_a |l_a| |uf_a| (the roundings of the nodes and the
+// weights to FP32, of the n FP32 and the n FP64 fused multiply-adds: (n + 3) 2^-24 of
+// that sum, taken 4 times).
+template <int DIM, int N, int M, int NN>
+__device__ __forceinline__ void sk_eval_screen(const float (&su)[M][NN], int p, float *v, float *e) {
+    const NodalTables &T = c_tab[N - 2];
+    constexpr int L = nlob(N);
+    constexpr float K = 4.0f * (N + 3) * 5.9604644775390625e-08f;
+    int beta = 0, al = p, stride = 1, off = 0;
+    if constexpr (DIM == 2) {
+        if (p < N * L) {
+            beta = p / L;
+            al = p - beta * L;
+            stride = 1;
+            off = beta * N;
+        } else {
+            const int q = p - N * L;
+            beta = q / L;
+            al = q - beta * L;
+            stride = N;
+            off = beta;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+        float s = 0.0f, a = 0.0f;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const float w = T.Iglf[al][k], x = su[c][off + k * stride];
+            s = fmaf(w, x, s);
+            a = fmaf(fabsf(w), fabsf(x), a);
+        }
+        v[c] = s;
+        e[c] = K * a;
+    }
+}
+
+// True when the FP32 value v (bound e per component on its distance to the FP64 value)
+// proves that the FP64 value lies in the bounds: scalar lo <= v <= hi; Euler rho >= eps
+// and rho e = E - |m|^2 / (2 rho) >= eps, with rho e bounded below by
+// (E - e_E) - (|m| + e_m)^2 / (2 (rho - e_rho)) less 2^-20 of its magnitudes (the FP32
+// rounding of this bound and the FP64 rounding of rho e).  NaN and inf never pass.
+template <int PHYS, int DIM>
+__device__ __forceinline__ bool screen_point(const Params &P, const float *v, const float *e) {
+    if (!P.scr_on) return false;
+    if constexpr (PHYS == PH_EULER) {
+        constexpr int M = DIM + 2;
+        const float rlo = v[0] - e[0];
+        if (!(rlo >= P.scr_eps && rlo <= 3.0e38f)) return false;
+        float m2 = 0.0f;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            const float ma = fabsf(v[1 + d]) + e[1 + d];
+            m2 = fmaf(ma, ma, m2);
+        }
+        const float kin = 0.5f * m2 / rlo;
+        const float elo = v[M - 1] - e[M - 1];
+        const float lb = (elo - kin) - 9.5367431640625e-07f * (fabsf(elo) + kin);
+        return lb >= P.scr_eps && lb <= 3.0e38f;
+    } else {
+        return v[0] - e[0] >= P.scr_lo && v[0] + e[0] <= P.scr_hi;
     }
 }
 
@@ -422,23 +491,62 @@ __device__ __forceinline__ double retry_factor(int attempt) {
 }
 
 // Scaling limiter of one stage (Prop. 2.4 scalar, eq. Euler-limiter1/2), block
-// collective.  u: this thread's node values (in/out).  pts: on return the values
-// at this thread's S_K points of the limited polynomial.  With check_avg the
+// collective.  u: this thread's node values (in/out).  pts (with need_pts): on return
+// the values at this thread's S_K points of the limited polynomial.  With check_avg the
 // admissibility of the cell average sets *B.flag (Sec. 4.1 restart test).
+//
+// Most cells need no limiting.  An FP32 screen (screen_point, with a bound on its
+// distance to the FP64 values) first tests every S_K point and the average; when it
+// clears every cell of the block, the FP64 limiter would leave all of them unchanged
+// (theta = 1, no flag), and it is skipped: the results are those of the FP64 path.
 template <class C>
 __device__ void limit_block(const Params &P, const Bufs &B, Smem<C> &S, int lc, int node, bool active,
-                            double *u, double (&pts)[C::PPT][C::M], bool check_avg, bool stats) {
+                            double *u, double (&pts)[C::PPT][C::M], bool check_avg, bool stats,
+                            bool need_pts = true) {
     constexpr int DIM = C::D, N = C::NP, PHYS = C::PH;
     constexpr int M = C::M, NN = C::NN, NSK = C::NSK, PPT = C::PPT;
     const NodalTables &T = c_tab[N - 2];
 
-    // 1. publish node values
+    // 1. publish node values (and FP32 copies for the screen)
 #pragma unroll
-    for (int c = 0; c < M; ++c) S.u[lc][c][node] = u[c];
+    for (int c = 0; c < M; ++c) {
+        S.u[lc][c][node] = u[c];
+        S.uf[lc][c][node] = (float)u[c];
+    }
     __syncthreads();
-    // 2. cell averages (Gauss weights; the mass matrix is exact)
+    // 2. cell averages (Gauss weights; the mass matrix is exact); FP32 screen of this
+    //    thread's S_K points
     cell_averages<C>(S.u[lc], node, [&](int c, double s) { S.avg[lc][c] = s; });
+    bool unsafe = false;
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+        int p = node + j * NN;
+        if (p < NSK) {
+            float v[M], e[M];
+            sk_eval_screen<DIM, N, M, NN>(S.uf[lc], p, v, e);
+            if (!screen_point<PHYS, DIM>(P, v, e)) unsafe = true;
+        }
+    }
     __syncthreads();
+    if (node == 0) {  // the average (FP32 rounding of the FP64 value: 2^-22 of it)
+        float v[M], e[M];
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            v[c] = (float)S.avg[lc][c];
+            e[c] = 2.384185791015625e-07f * fabsf(v[c]);
+        }
+        if (!screen_point<PHYS, DIM>(P, v, e)) unsafe = true;
+    }
+    if (!__syncthreads_or(unsafe)) {  // every cell of the block cleared
+        if (need_pts) {
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                int p = node + j * NN;
+                if (p < NSK) sk_eval<DIM, N, M, NN>(S.u[lc], p, pts[j]);
+            }
+        }
+        return;
+    }
     // 3. values at S_K and this thread's extremes (order-preserving integer keys)
     unsigned long long kmin = kKeyPosInf, kmax = kKeyNegInf;
 #pragma unroll
@@ -711,7 +819,7 @@ __device__ __forceinline__ void inner_body(const Params &P, const Bufs &B, int b
                 cur[c] = v;
             }
             double pts[C::PPT][M];
-            limit_block(P, B, S, lc, node, active, cur, pts, true, true);
+            limit_block(P, B, S, lc, node, active, cur, pts, true, true, false);
         }
         double trs[FPT][M];
         const bool keep_faces = P.slot[i] >= 0 && B.tfs != nullptr;
@@ -933,7 +1041,7 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_limit(Params P, Bufs 
     const bool active = cell < P.ncell;
     double u[C::M], pts[C::PPT][C::M];
     load_node<DIM, N, PHYS>(P, B.un, cell, node, active, u);
-    limit_block(P, B, S, lc, node, active, u, pts, false, false);
+    limit_block(P, B, S, lc, node, active, u, pts, false, false, false);
     store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
 }
 

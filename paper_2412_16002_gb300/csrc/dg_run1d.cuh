@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(RunCfg1D<N, PHYS, NCBV>::NT) k_run1d(Params P,
                         cur_u[c] = v;
                     }
                     double pts[C::PPT][M];
-                    limit_block(P, B, S, lc, node, own, cur_u, pts, true, true);
+                    limit_block(P, B, S, lc, node, own, cur_u, pts, true, true, false);
                 }
                 double trs[C::FPT][M];
                 const bool traced = P.slot[i] >= 0;

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 namespace crkdg {
@@ -87,6 +88,10 @@ struct Params {
     double tvb_M;     // TVB constant of the plain indicator
     double thr[2];    // its thresholds M h_x^2, M h_y^2 (h_d = 2 / rh_d), set by tvb_thresholds
     double thr_feat;  // M h_x h_y: the learned indicator's feature scale floor
+    // FP32 bounds of the FP64 limiter's screen, set by screen_bounds: eps and lo rounded up,
+    // hi rounded down (scr_on = 0: the screen clears nothing)
+    int scr_on;
+    float scr_eps, scr_lo, scr_hi;
     int ind_stage;    // troubled-cell kernel: 0 decide and limit, 2 limit the given flags (the feature
                       // kernel decided), 3 combine the given plain flags with the learned
                       // probabilities, then limit; 4 (split path) decide, combine with the
@@ -100,6 +105,28 @@ inline void tvb_thresholds(Params &P) {
     P.thr[0] = P.tvb_M * hx * hx;
     P.thr[1] = P.tvb_M * hy * hy;
     P.thr_feat = P.tvb_M * (2.0 / P.rhx) * (2.0 / P.rhy);
+}
+
+// The FP32 bounds of the FP64 limiter's screen (host side): floats on the safe side of
+// eps, lo and hi, moved a further 2^-20 inwards.
+inline float float_at_least(double x) {
+    float f = (float)x;
+    if ((double)f < x) f = nextafterf(f, INFINITY);
+    return f;
+}
+inline float float_at_most(double x) {
+    float f = (float)x;
+    if ((double)f > x) f = nextafterf(f, -INFINITY);
+    return f;
+}
+inline void screen_bounds(Params &P) {
+    const float in = 9.5367431640625e-07f;  // 2^-20
+    P.scr_eps = float_at_least(P.eps) * (1.0f + in);
+    P.scr_lo = float_at_least(P.lo);
+    P.scr_lo = P.scr_lo + in * fabsf(P.scr_lo);
+    P.scr_hi = float_at_most(P.hi);
+    P.scr_hi = P.scr_hi - in * fabsf(P.scr_hi);
+    P.scr_on = 1;
 }
 
 struct Bufs {
