@@ -38,32 +38,31 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Grid-wide barrier with a bounded wait (2 s of %globaltimer).  Returns false
-// when the wait expired; the caller then leaves its step loop.
-__device__ bool grid_barrier(RunCtl *R, unsigned nblocks) {
+// Grid-wide barrier on a counter that only grows: every block adds one per
+// barrier and waits until the count reaches `target` (the number of arrivals due
+// by the end of this barrier), so no block resets anything and the last arrival
+// wakes the others by its own add.  The fence before the add publishes the
+// block's writes (ordered before it by the block barrier); the acquire load
+// orders the reads after it.  Bounded wait (2 s of %globaltimer): returns false
+// when it expired, and the caller then leaves its step loop.
+__device__ bool grid_barrier(RunCtl *R, unsigned target) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *gen = &R->bar_gen;
-        unsigned g = *gen;  // read before arriving: the last arrival cannot pass us
-        __threadfence();
-        unsigned arrived = atomicAdd(&R->bar_count, 1u) + 1u;
         int ok = 1;
-        if (arrived == nblocks) {
-            atomicExch(&R->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&R->bar_gen, 1u);
-        } else {
-            unsigned long long t0 = global_ns();
-            while (*gen == g) {
-                if (global_ns() - t0 > 2000000000ull) {
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(40);
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(&R->bar_count) : "memory");
+        const unsigned long long t0 = global_ns();
+        for (;;) {
+            unsigned c;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(c) : "l"(&R->bar_count) : "memory");
+            if ((int)(c - target) >= 0) break;  // wrap-safe: the count never runs 2^31 ahead
+            if (global_ns() - t0 > 2000000000ull) {
+                ok = 0;
+                break;
             }
+            __nanosleep(40);
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
@@ -255,7 +254,7 @@ __global__ void __launch_bounds__(RunCfg1D<N, PHYS, NCBV>::NT) k_run1d(Params P,
             if (own) store_node<1, N, PHYS>(P, unew, gc, node, true, u);
             __syncthreads();
         }
-        if (!grid_barrier(R, gridDim.x + (unsigned)R->extra_arrivals)) {
+        if (!grid_barrier(R, (unsigned)(it + 1) * (gridDim.x + (unsigned)R->extra_arrivals))) {
             status = RUN_TIMEOUT;
             break;
         }

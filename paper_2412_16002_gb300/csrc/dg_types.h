@@ -246,8 +246,8 @@ struct RunCtl {
     double t_out, rate_out;
     int steps, restarts, cur_out, status;
     unsigned long long nlim_total;
-    // grid barrier
-    unsigned bar_count, bar_gen;
+    // grid barrier: arrivals so far (zero at launch)
+    unsigned bar_count, pad_;
     RunSlot slot[3];
 };
 
