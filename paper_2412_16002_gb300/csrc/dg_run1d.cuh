@@ -43,10 +43,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // by the end of this barrier), so no block resets anything and the last arrival
 // wakes the others by its own add.  The fence before the add publishes the
 // block's writes (ordered before it by the block barrier); the acquire load
-// orders the reads after it.  Bounded wait (2 s of %globaltimer): returns false
+// orders the reads after it.  The waiting thread then reads the attempt's
+// admissibility flag, rate and limited-cell count together (one round trip)
+// and hands them to the block.  Bounded wait (2 s of %globaltimer): returns false
 // when it expired, and the caller then leaves its step loop.
-__device__ bool grid_barrier(RunCtl *R, unsigned target) {
+struct SlotRead {
+    int flag;
+    unsigned long long rate, nlim;
+};
+__device__ bool grid_barrier(RunCtl *R, unsigned target, const RunSlot *SL, SlotRead &out) {
     __shared__ int s_ok;
+    __shared__ SlotRead s_rd;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
@@ -63,9 +70,13 @@ __device__ bool grid_barrier(RunCtl *R, unsigned target) {
             }
             __nanosleep(40);
         }
+        s_rd.flag = *(const volatile int *)&SL->flag;
+        s_rd.rate = *(const volatile unsigned long long *)&SL->rate;
+        s_rd.nlim = *(const volatile unsigned long long *)&SL->nlim;
         s_ok = ok;
     }
     __syncthreads();
+    out = s_rd;
     return s_ok != 0;
 }
 
@@ -254,11 +265,12 @@ __global__ void __launch_bounds__(RunCfg1D<N, PHYS, NCBV>::NT) k_run1d(Params P,
             if (own) store_node<1, N, PHYS>(P, unew, gc, node, true, u);
             __syncthreads();
         }
-        if (!grid_barrier(R, (unsigned)(it + 1) * (gridDim.x + (unsigned)R->extra_arrivals))) {
+        SlotRead rd;
+        if (!grid_barrier(R, (unsigned)(it + 1) * (gridDim.x + (unsigned)R->extra_arrivals), SL, rd)) {
             status = RUN_TIMEOUT;
             break;
         }
-        const int fl = *(volatile int *)&SL->flag;
+        const int fl = rd.flag;
         if (blockIdx.x == 0 && threadIdx.x == 0) {  // the slot used two attempts ahead
             RunSlot *Z = &R->slot[(it + 2) % 3];
             Z->flag = 0;
@@ -268,8 +280,8 @@ __global__ void __launch_bounds__(RunCfg1D<N, PHYS, NCBV>::NT) k_run1d(Params P,
         }
         ++it;
         if (fl == 0) {
-            const double rate = bitsd(*(volatile unsigned long long *)&SL->rate);
-            nlim_total += *(volatile unsigned long long *)&SL->nlim;
+            const double rate = bitsd(rd.rate);
+            nlim_total += rd.nlim;
             t += dt;
             if (t_end - t <= 1e-14 * fabs(t_end)) t = t_end;
             ++steps;
