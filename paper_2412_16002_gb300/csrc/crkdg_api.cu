@@ -592,14 +592,21 @@ crkdg_status crkdg_set_state(crkdg_t h, const double *nodal, size_t count, int o
             X = base_xbufs(h);
             X.dv_n = h->xdv[h->xcur];
             CK(h, launch_x(h, KX_LIMIT, P, X));
-        } else {
-            Bufs B = base_bufs(h);
-            B.un = h->unew;
-            B.unew = h->u;
-            CK(h, launch(h, K_LIMIT, P, B));
+            CK(h, cudaStreamSynchronize(h->st));
+            h->a0_valid = false;
+            return CRKDG_OK;
         }
-        CK(h, cudaStreamSynchronize(h->st));
-        h->a0_valid = false;
+        // FP64: the limiter also posts the trial-step rate of the limited state, so
+        // crkdg_max_dt needs no pass of its own
+        Bufs B = base_bufs(h);
+        B.un = h->unew;
+        B.unew = h->u;
+        P.mode = MODE_RATE;
+        CK(h, launch(h, K_LIMIT, P, B));
+        crkdg_status s = read_scalars(h);
+        if (s) return s;
+        h->a0 = from_bits(h->hs->a0);
+        h->a0_valid = true;
         return CRKDG_OK;
     } catch (...) {
         return CRKDG_E_OOM;

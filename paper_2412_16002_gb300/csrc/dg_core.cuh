@@ -1031,7 +1031,10 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_final(Params P, Bufs 
     final_body<DIM, N, PHYS, STORED>(P, B, blockIdx.x);
 }
 
-// Limiter applied to a state (set-up projection, operator checks): un -> unew.
+// Limiter applied to a state (set-up projection, operator checks): un -> unew.  In
+// MODE_RATE it also posts the wave-speed rate of the limited state to B.a0: the
+// limiter leaves this thread's S_K values of the final nodal values in pts, the
+// same interpolation of the same values that the scan kernel would take.
 template <int DIM, int N, int PHYS>
 __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_limit(Params P, Bufs B) {
     using C = Cfg<DIM, N, PHYS>;
@@ -1039,9 +1042,22 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_limit(Params P, Bufs 
     const int lc = threadIdx.x / C::NN, node = threadIdx.x - lc * C::NN;
     const int cell = blockIdx.x * C::NCB + lc;
     const bool active = cell < P.ncell;
+    const bool rate = P.mode == MODE_RATE;
     double u[C::M], pts[C::PPT][C::M];
     load_node<DIM, N, PHYS>(P, B.un, cell, node, active, u);
-    limit_block(P, B, S, lc, node, active, u, pts, false, false, false);
+    limit_block(P, B, S, lc, node, active, u, pts, false, false, rate);
+    if (rate) {
+        double amax = 0.0;
+#pragma unroll
+        for (int j = 0; j < C::PPT; ++j) {
+            int p = node + j * C::NN;
+            if (p < C::NSK && active) amax = fmax(amax, sk_rate<PHYS, DIM>(P, pts[j]));
+        }
+        unsigned long long abits = dbits(amax);  // non-negative: the bits order as the values
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) abits = umax64(abits, __shfl_xor_sync(0xffffffffu, abits, o));
+        if ((threadIdx.x & 31) == 0 && abits > 0ull) atomicMax(B.a0, abits);
+    }
     store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
 }
 
