@@ -129,6 +129,60 @@ constexpr bool vec4() {
     return C::D == 2 && C::NP == 4;
 }
 
+// Largest number of threads of one warp whose shared-memory words share a bank when
+// the threads (cell lc, node k < M * parts) read element (k % parts) * ch + q of component
+// k / parts's row of their cell, the rows of a component being R words long and the
+// components S words apart (word (k / parts) * S + lc * R + (k % parts) * ch + q).  These
+// are the per-cell sums over a cell's nodes or face points, one thread per component (or
+// per component and chunk); each extra thread on a bank costs one more wavefront.
+template <class C>
+constexpr int comp_bank_mult(int R, int S, int parts, int ch) {
+    int worst = 0;
+    for (int w = 0; w < C::NT; w += 32) {
+        int cnt[32] = {};
+        for (int t = w; t < w + 32 && t < C::NT; ++t) {
+            const int lc = t / C::NN, k = t - lc * C::NN;
+            if (k >= C::M * parts) continue;
+            const int c = k / parts, part = k - c * parts;
+            const int b = (c * S + lc * R + part * ch) % 32;
+            if (++cnt[b] > worst) worst = cnt[b];
+        }
+    }
+    return worst;
+}
+
+// Padding (in words) of the per-component rows of R words of every cell of a block that
+// spreads the per-cell sums over the banks: the smallest of 0..31 with the fewest
+// wavefronts (with parts > 1 the chunked face sums of the final stage count too).
+template <class C>
+constexpr int comp_pad(int R, int parts, int ch) {
+    int best = 0, bestm = 1 << 30;
+    for (int p = 0; p < 32; ++p) {
+        const int S = C::NCB * R + p;
+        const int m = comp_bank_mult<C>(R, S, 1, 0) + (parts > 1 ? comp_bank_mult<C>(R, S, parts, ch) : 0);
+        if (m < bestm) {
+            bestm = m;
+            best = p;
+        }
+    }
+    return best;
+}
+
+// One component's rows (R floats per cell) of a block's cells, followed by PAD unused
+// words; S.x[c][lc][q] indexes it like a [NCB][R] array.
+template <int NCB, int R, int PAD>
+struct PadRows {
+    float d[NCB * R + PAD];
+    __device__ __forceinline__ float *operator[](int lc) { return d + lc * R; }
+    __device__ __forceinline__ const float *operator[](int lc) const { return d + lc * R; }
+};
+
+// chunks of the final stage's FP64 face sums per component (see k_final_x)
+template <class C>
+constexpr int face_parts() {
+    return C::NN >= 4 * C::M ? 4 : (C::NN >= 2 * C::M ? 2 : 1);
+}
+
 template <class C>
 struct alignas(16) SmemX {
     // component-major ([m][cell][...]): a warp's threads (consecutive nodes or face points of
@@ -136,8 +190,12 @@ struct alignas(16) SmemX {
     float u[C::M][C::NCB][C::NN];     // node values (or deviations in the limiter)
     float uT[C::M][C::NCB][vec4<C>() ? C::NN : 1];  // the same, transposed (node a*n + b)
     float f[C::D][C::M][C::NCB][C::NN];  // fluxes; with vec4 the y-fluxes are transposed
-    float tf[C::M][C::NCB][C::NTR];   // trace fluxes / face corrections
-    float w[C::M][C::NCB][C::NN];     // weighted values for the per-cell FP32 means
+    // trace fluxes / face corrections; weighted values for the per-cell FP32 means (both
+    // padded per component for the per-cell sums)
+    PadRows<C::NCB, C::NTR,
+            comp_pad<C>(C::NTR, face_parts<C>(), (C::NTR + face_parts<C>() - 1) / face_parts<C>())>
+        tf[C::M];
+    PadRows<C::NCB, C::NN, comp_pad<C>(C::NN, 1, 0)> w[C::M];
     float ubf[C::NCB][C::M];          // FP32 copy of the averages
     float mean[C::NCB][C::M];
     double gb[C::NCB][C::M];          // FP64 face sums
@@ -862,7 +920,7 @@ __global__ void __launch_bounds__(C::NT, split_min_blocks<C>()) k_final_x(Params
             for (int c = 0; c < M; ++c) S.tf[c][lc][fp] = fhs[j][c];
     }
     __syncthreads();
-    constexpr int PARTS = NN >= 4 * M ? 4 : (NN >= 2 * M ? 2 : 1);
+    constexpr int PARTS = face_parts<C>();
     constexpr int CH = (NTR + PARTS - 1) / PARTS;
     for (int k = node; k < M * PARTS; k += NN) {
         const int c = k / PARTS, part = k - c * PARTS;
