@@ -683,13 +683,18 @@ __device__ __forceinline__ void load_x(const Params &P, const MixBufs &X, int ce
 }
 
 // Resident blocks per SM that the inner and final kernels' register budgets are sized
-// for.  These kernels are bound by FP32 and shared-memory latency, not by a pipe, so
-// more resident warps pay even at the price of a few spilled registers: 8 blocks of
-// 128 threads (Q^3) and 3 of 288 (Q^2) took the 2048^2 Q^3 step from 19.4 to 16.8 ms
-// and the 1024^2 Q^2 step from 2.75 to 2.27 ms, against 4 and 2.
+// for.  These kernels are bound by FP32, shared-memory and load latency, not by a pipe,
+// so more resident warps pay even at the price of a few spilled registers: 8 blocks of
+// 128 threads (Q^3) and 3 of 288 (Q^2) for the inner kernel, 10 and 4 for the final one,
+// took the 2048^2 Q^3 step from 19.4 to 15.8 ms and the 1024^2 Q^2 step from 2.75 to
+// 2.04 ms (with the padded rows below), against 4 and 2 for both.
 template <class C>
 constexpr int split_min_blocks() {
     return C::NT > 128 ? 3 : 8;
+}
+template <class C>
+constexpr int split_final_min_blocks() {
+    return C::NT > 128 ? 4 : 10;
 }
 
 // Inner stages of the split representation (cell-local).
@@ -789,7 +794,7 @@ __global__ void __launch_bounds__(C::NT, split_min_blocks<C>()) k_inner_x(Params
 // sum_i b_i fhat^(i) over the face points, deviations from the FP32 lift of
 // sum_i b_i (fhat^(i) - f(u_int^(i))); then the limiter and the trial-step rate.
 template <class C>
-__global__ void __launch_bounds__(C::NT, split_min_blocks<C>()) k_final_x(Params P, MixBufs X) {
+__global__ void __launch_bounds__(C::NT, split_final_min_blocks<C>()) k_final_x(Params P, MixBufs X) {
     constexpr int DIM = C::D, N = C::NP, PHYS = C::PH;
     constexpr int M = C::M, NN = C::NN, NF = C::NF, NTR = C::NTR, FPT = C::FPT;
     __shared__ SmemX<C> S;
