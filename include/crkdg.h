@@ -213,10 +213,12 @@ crkdg_status crkdg_troubled_flags(crkdg_t h, int *flags, int on_device);
 #define CRKDG_MLP_NPARAM 7105
 
 /* prob[r] = network(X[r]) for the n rows of X ([n][44]); enqueued on stream.  X must be
- * 16-byte aligned (rows are read as 16-byte vectors).  The two hidden layers run on the
+ * 16-byte aligned (tiles of 128 rows are moved by bulk asynchronous copies, which need
+ * 16-byte aligned addresses; CRKDG_E_ARG otherwise).  The two hidden layers run on the
  * tensor cores with the three-product TF32 split (FP32 accuracy).  If a wait for the
- * tensor cores runs out (1 s), the affected probabilities are NaN (the learned rule then
- * leaves those cells to the plain decision) and crkdg_mlp_fault reports it. */
+ * tensor cores or for a tile's copy runs out (1 s), the affected probabilities are NaN
+ * or unwritten (the learned rule leaves NaN cells to the plain decision) and
+ * crkdg_mlp_fault reports it. */
 crkdg_status crkdg_mlp_forward(const float *params, const float *X, int n, float *prob, void *stream);
 /* *fault = 1 if a crkdg_mlp_forward launch since the last call ran out of time waiting
  * for the tensor cores, else 0; clears the record (synchronises the device). */

@@ -48,7 +48,11 @@ constexpr int SZ_X = tile_bytes(TM, K1), SZ_H = tile_bytes(TM, NH), SZ_W1 = tile
               SZ_W2 = tile_bytes(NH, NH);
 constexpr int OFF_XH = 0, OFF_XL = OFF_XH + SZ_X, OFF_HH = OFF_XL + SZ_X, OFF_HL = OFF_HH + SZ_H,
               OFF_W1H = OFF_HL + SZ_H, OFF_W1L = OFF_W1H + SZ_W1, OFF_W2H = OFF_W1L + SZ_W1,
-              OFF_W2L = OFF_W2H + SZ_W2, SMEM_TC = OFF_W2L + SZ_W2;  // 172032 bytes
+              OFF_W2L = OFF_W2H + SZ_W2, OFF_XS = OFF_W2L + SZ_W2,
+              SZ_XS = TM * NIN * 4, SMEM_TC = OFF_XS + SZ_XS;  // 194560 bytes
+// OFF_XS: the raw features of the next tile (row-major, NIN floats a row), written by
+// one bulk asynchronous copy (the tensor memory accelerator's non-tensor form) per tile
+static_assert(OFF_XS % 16 == 0 && (NIN * 4) % 16 == 0, "bulk copies move 16-byte multiples");
 
 __device__ __forceinline__ int core_off(int row, int k, int rows) {
     return (((k >> 2) * (rows >> 3) + (row >> 3)) << 7) + ((row & 7) << 4) + ((k & 3) << 2);
@@ -117,10 +121,21 @@ __device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// One bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) from
+// global memory to this CTA's shared memory, completing on mbarrier `bar` (which
+// expects the bytes first).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 // Set when a wait for the tensor cores ran out (1 s); read and cleared by crkdg_mlp_fault.
 __device__ unsigned int g_mlp_fault;
 
-// Bounded wait for the MMAs of this tile (mbarrier phase `parity`): true when done.
+// Bounded wait (1 s) for the phase `parity` of an mbarrier (the MMAs of a tile, or a
+// tile's bulk copy): true when it completed.
 __device__ __forceinline__ bool wait_mma(uint32_t mbar, uint32_t parity) {
     const unsigned long long t0 = globaltimer();
     while (!mbar_try_wait(mbar, parity))
@@ -128,12 +143,14 @@ __device__ __forceinline__ bool wait_mma(uint32_t mbar, uint32_t parity) {
     return true;
 }
 
-__device__ __forceinline__ void load_row(const float *__restrict__ X, int n, int r, float *x) {
-    if (r < n) {
-        const float4 *src = reinterpret_cast<const float4 *>(X + (size_t)r * NIN);  // rows are 176-byte aligned
+// This thread's feature row from the staged tile (zeros past the last row): 16-byte
+// reads; eight consecutive rows 176 bytes apart fall on distinct banks.
+__device__ __forceinline__ void stage_row(const unsigned char *stage, int rows, int t, float *x) {
+    if (t < rows) {
+        const float4 *src = reinterpret_cast<const float4 *>(stage) + (size_t)t * (NIN / 4);
 #pragma unroll
         for (int q = 0; q < NIN / 4; ++q) {
-            float4 v = __ldg(src + q);
+            float4 v = src[q];
             x[4 * q] = v.x;
             x[4 * q + 1] = v.y;
             x[4 * q + 2] = v.z;
@@ -146,14 +163,15 @@ __device__ __forceinline__ void load_row(const float *__restrict__ X, int n, int
 }
 
 // Persistent: each CTA (128 threads, one per cell of a tile) walks tiles
-// blockIdx.x, blockIdx.x + gridDim.x, ...; the next tile's features are loaded
-// into registers while the current tile's MMAs run.
+// blockIdx.x, blockIdx.x + gridDim.x, ...; one thread issues the bulk copy of the
+// next tile's features into the staging buffer while the current tile's MMAs run,
+// and every thread reads its row from there once the copy's mbarrier completes.
 __global__ void __launch_bounds__(TM, 1) k_mlp_forward_tc(const float *__restrict__ theta,
                                                           const float *__restrict__ X, int n,
                                                           float *__restrict__ prob) {
     extern __shared__ __align__(1024) unsigned char smt[];
     __shared__ float sb1[NH], sb2[NH], sw3[NH];
-    __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ __align__(8) unsigned long long s_mbar, s_xbar;
     __shared__ uint32_t s_tmem;
     __shared__ int s_fault;
     const int t = threadIdx.x, warp = t >> 5;
@@ -179,11 +197,18 @@ __global__ void __launch_bounds__(TM, 1) k_mlp_forward_tc(const float *__restric
         sw3[t] = theta[OW3 + t];
     }
     const float b3 = theta[OB3];
-    const uint32_t mbar = smem_addr(&s_mbar);
+    const uint32_t mbar = smem_addr(&s_mbar), xbar = smem_addr(&s_xbar);
+    const uint32_t a_stage = smem_addr(smt + OFF_XS);
+    const int ntiles = (n + TM - 1) / TM;
+    auto tile_rows = [&](int tl) { return n - tl * TM < TM ? n - tl * TM : TM; };
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(xbar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fault = 0;
+        // the first tile's features (X is 16-byte aligned and rows are 176 bytes)
+        if ((int)blockIdx.x < ntiles)
+            bulk_load(a_stage, X + (size_t)blockIdx.x * TM * NIN, (uint32_t)(tile_rows(blockIdx.x) * NIN * 4), xbar);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
@@ -201,14 +226,23 @@ __global__ void __launch_bounds__(TM, 1) k_mlp_forward_tc(const float *__restric
     const uint32_t a_w1[2] = {smem_addr(smt + OFF_W1H), smem_addr(smt + OFF_W1L)};
     const uint32_t a_w2[2] = {smem_addr(smt + OFF_W2H), smem_addr(smt + OFF_W2L)};
     constexpr uint32_t LBO_A = (TM / 8) * 128, LBO_B = (NH / 8) * 128, SBO = 128;
-    uint32_t phase = 0;
+    uint32_t phase = 0, xphase = 0;
+    bool inflight = (int)blockIdx.x < ntiles;  // a bulk copy this thread has not seen complete
 
-    const int ntiles = (n + TM - 1) / TM;
     float x[NIN];
-    int tile = blockIdx.x;
-    if (tile < ntiles) load_row(X, n, tile * TM + t, x);
-    for (; tile < ntiles; tile += gridDim.x) {
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int r = tile * TM + t;
+        // this tile's features, staged by the bulk copy
+        const bool okx = wait_mma(xbar, xphase);
+        if (okx) {  // otherwise the copy may still land: drained below at the same phase
+            xphase ^= 1u;
+            inflight = false;
+        }
+        if (__syncthreads_or(!okx)) {
+            if (t == 0) s_fault = 1;
+            break;
+        }
+        stage_row(smt + OFF_XS, tile_rows(tile), t, x);
         // layer-1 A tile: this cell's features, split
 #pragma unroll
         for (int k = 0; k < K1; ++k) {
@@ -231,9 +265,13 @@ __global__ void __launch_bounds__(TM, 1) k_mlp_forward_tc(const float *__restric
             }
             mma_commit(mbar);
         }
-        // the next tile's features while the tensor cores work
+        // the next tile's features while the tensor cores work (every thread has read
+        // the staging buffer and fenced the async proxy before the barrier above)
         const int nxt = tile + gridDim.x;
-        if (nxt < ntiles) load_row(X, n, nxt * TM + t, x);
+        if (nxt < ntiles) {
+            if (t == 0) bulk_load(a_stage, X + (size_t)nxt * TM * NIN, (uint32_t)(tile_rows(nxt) * NIN * 4), xbar);
+            inflight = true;
+        }
         bool ok = wait_mma(mbar, phase);
         phase ^= 1u;
         tc_after_sync();
@@ -293,6 +331,8 @@ __global__ void __launch_bounds__(TM, 1) k_mlp_forward_tc(const float *__restric
         }
         tc_after_sync();
     }
+    // no copy may still be writing shared memory when the CTA exits
+    if (inflight && !wait_mma(xbar, xphase)) s_fault = 1;
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
@@ -414,7 +454,7 @@ crkdg_status crkdg_mlp_forward(const float *params, const float *X, int n, float
         configured_dev = dev;
     }
     const int ntiles = (n + TM - 1) / TM;
-    const int grid = ntiles < nsm ? ntiles : nsm;  // one CTA per SM (168 KB of shared memory each)
+    const int grid = ntiles < nsm ? ntiles : nsm;  // one CTA per SM (190 KB of shared memory each)
     k_mlp_forward_tc<<<grid, TM, SMEM_TC, (cudaStream_t)stream>>>(params, X, n, prob);
     return cudaGetLastError() == cudaSuccess ? CRKDG_OK : CRKDG_E_CUDA;
 }
