@@ -685,12 +685,12 @@ __device__ __forceinline__ void load_x(const Params &P, const MixBufs &X, int ce
 // Resident blocks per SM that the inner and final kernels' register budgets are sized
 // for.  These kernels are bound by FP32, shared-memory and load latency, not by a pipe,
 // so more resident warps pay even at the price of a few spilled registers: 8 blocks of
-// 128 threads (Q^3) and 3 of 288 (Q^2) for the inner kernel, 10 and 4 for the final one,
+// 128 threads (Q^3) and 4 of 288 (Q^2) for the inner kernel, 10 and 4 for the final one,
 // took the 2048^2 Q^3 step from 19.4 to 15.8 ms and the 1024^2 Q^2 step from 2.75 to
-// 2.04 ms (with the padded rows below), against 4 and 2 for both.
+// 2.00 ms (with the padded rows below), against 4 and 2 for both.
 template <class C>
 constexpr int split_min_blocks() {
-    return C::NT > 128 ? 3 : 8;
+    return C::NT > 128 ? 4 : 8;
 }
 template <class C>
 constexpr int split_final_min_blocks() {
