@@ -196,6 +196,16 @@ struct alignas(16) SmemX {
             comp_pad<C>(C::NTR, face_parts<C>(), (C::NTR + face_parts<C>() - 1) / face_parts<C>())>
         tf[C::M];
     PadRows<C::NCB, C::NN, comp_pad<C>(C::NN, 1, 0)> w[C::M];
+    // the per-cell sums read at most two words per bank (one wavefront, or two where a
+    // block's cells cannot all be spread; unpadded they were up to 4-way conflicts)
+    static_assert(comp_bank_mult<C>(C::NN, C::NCB * C::NN + comp_pad<C>(C::NN, 1, 0), 1, 0) <= 2,
+                  "per-cell sums of the weighted values conflict");
+    static_assert(comp_bank_mult<C>(C::NTR,
+                                    C::NCB * C::NTR +
+                                        comp_pad<C>(C::NTR, face_parts<C>(),
+                                                    (C::NTR + face_parts<C>() - 1) / face_parts<C>()),
+                                    1, 0) <= 2,
+                  "per-cell sums of the face fluxes conflict");
     float ubf[C::NCB][C::M];          // FP32 copy of the averages
     float mean[C::NCB][C::M];
     double gb[C::NCB][C::M];          // FP64 face sums
