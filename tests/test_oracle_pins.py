@@ -613,3 +613,157 @@ def test_outflow_corners_stay_stable():
     speed = np.sqrt(avg_a[..., 1] ** 2 + avg_a[..., 2] ** 2) / avg_a[..., 0]
     assert t > 0.8 and speed.max() < 1.2
     assert np.abs(avg_a - avg_b).max() < 1e-4
+
+
+# --------------------------------------------------------------------------- reflective walls, trial step
+
+
+def _mirror_x(U, m):
+    """Nodal 2D Euler state [m][ny][nx][n][n] -> its mirror image in x (cells and nodes reversed
+    along x, x-momentum negated)."""
+    V = U[:, :, ::-1, :, ::-1].copy()
+    V[1] = -V[1]
+    return V
+
+
+def _mirror_y(U, m):
+    V = U[:, ::-1, :, ::-1, :].copy()
+    V[2] = -V[2]
+    return V
+
+
+@pytest.mark.parametrize("axis", ["x", "y"])
+def test_reflective_walls_equal_mirror_symmetric_periodic_problem(axis):
+    """Example 4.7 walls: the exterior state of a reflective face is the interior trace with
+    the normal momentum negated.  A problem on [0,1]^2 with reflective walls on both sides of
+    one axis (periodic across the other) must then equal, on [0,1]^2, the periodic problem on
+    the doubled domain whose data are the mirror image across the wall (rho, tangential
+    momentum and E even, normal momentum odd): the doubled problem keeps that symmetry, and the
+    periodic neighbour across x = 0 (or y = 0) supplies exactly the negated-normal trace.  A
+    wrong sign, a wrong component or a wrong side in the reflect branch breaks the equality."""
+    k, nx, ny = 2, 8, 6
+    m = 4
+    U = inputs.random_euler(2, nx, ny, k, seed=41, osc=0.3).reshape(m, ny, nx, k + 1, k + 1)
+    # give the wall-normal momentum a clear sign near both walls, so the wall flux matters
+    if axis == "x":
+        bc_r = ("reflect", "reflect", "periodic", "periodic")
+        dom_r = (0.0, 1.0, 0.0, 1.0)
+        dom_p = (-1.0, 1.0, 0.0, 1.0)
+        big = np.concatenate([_mirror_x(U, m), U], axis=2)
+        sl = (slice(None), slice(None), slice(nx, 2 * nx))
+        nxp, nyp = 2 * nx, ny
+    else:
+        bc_r = ("periodic", "periodic", "reflect", "reflect")
+        dom_r = (0.0, 1.0, 0.0, 1.0)
+        dom_p = (0.0, 1.0, -1.0, 1.0)
+        big = np.concatenate([_mirror_y(U, m), U], axis=1)
+        sl = (slice(None), slice(ny, 2 * ny), slice(None))
+        nxp, nyp = nx, 2 * ny
+    o_r = Oracle(2, nx, ny, k, dom_r, "euler", bc=bc_r)
+    o_p = Oracle(2, nxp, nyp, k, dom_p, "euler", bc=("periodic",) * 4)
+    o_r.set_state(U)
+    o_p.set_state(big)
+    assert np.abs(o_p.get_state()[sl] - o_r.get_state()).max() < 1e-14
+    t = 0.0
+    for step in range(10):
+        dt = o_r.max_dt(0.1)
+        assert abs(o_p.max_dt(0.1) - dt) <= 1e-15 * dt  # the doubled problem has the same rates
+        rc1, _ = o_r.step(dt, HEUN3, t)
+        rc2, _ = o_p.step(dt, HEUN3, t)
+        assert rc1 == 0 and rc2 == 0
+        t += dt
+    a, b = o_r.get_state(), o_p.get_state()[sl]
+    for c in range(m):
+        assert np.abs(a[c] - b[c]).max() <= 1e-13 * np.abs(b[c]).max(), c
+    # the mirrored half stays the mirror image (the doubled problem really is symmetric)
+    full = o_p.get_state()
+    half = full[:, :, :nx] if axis == "x" else full[:, :ny]
+    mir = _mirror_x(half, m) if axis == "x" else _mirror_y(half, m)
+    assert np.abs(mir - b).max() <= 1e-13 * np.abs(b).max()
+    # and the walls did something: the result differs from the same data with outflow walls
+    o_o = Oracle(2, nx, ny, k, dom_r, "euler",
+                 bc=("outflow", "outflow", "periodic", "periodic") if axis == "x"
+                 else ("periodic", "periodic", "outflow", "outflow"))
+    o_o.set_state(U)
+    t = 0.0
+    for _ in range(10):
+        dt = o_o.max_dt(0.1)
+        o_o.step(dt, HEUN3, t)
+        t += dt
+    assert np.abs(o_o.get_state() - a).max() > 1e-6
+
+
+def test_reflective_walls_1d_equal_mirror_symmetric_periodic_problem():
+    k, nx, m = 2, 12, 3
+    U = inputs.random_euler(1, nx, 1, k, seed=43, osc=0.3).reshape(m, nx, k + 1)
+    M = U[:, ::-1, ::-1].copy()
+    M[1] = -M[1]
+    o_r = Oracle(1, nx, 1, k, (0.0, 1.0), "euler", bc=("reflect", "reflect", "outflow", "outflow"))
+    o_p = Oracle(1, 2 * nx, 1, k, (-1.0, 1.0), "euler", bc=("periodic",) * 4)
+    o_r.set_state(U)
+    o_p.set_state(np.concatenate([M, U], axis=1))
+    t = 0.0
+    for _ in range(12):
+        dt = o_r.max_dt(0.1)
+        o_r.step(dt, HEUN3, t)
+        o_p.step(dt, HEUN3, t)
+        t += dt
+    a, b = o_r.get_state(), o_p.get_state()[:, nx:]
+    for c in range(m):
+        assert np.abs(a[c] - b[c]).max() <= 1e-13 * np.abs(b[c]).max(), c
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_trial_step_closed_form_on_constant_states(dim):
+    """eq. (numerical_experiment:CFL) on a constant state, where every S_K point carries the
+    same state: 1D dt = CFL dx / (|w| + c); 2D (radii summed per direction) dt = CFL /
+    ((|w_x| + c)/h_x + (|w_y| + c)/h_y), c = sqrt(gamma p / rho).  The cells are not square and
+    w_x != w_y, so a swapped direction or cell size changes the value."""
+    gamma, cfl = 1.4, 0.178
+    rho, wx, wy, p = 0.7, -0.9, 0.35, 1.3
+    c = math.sqrt(gamma * p / rho)
+    k = 2
+    n = k + 1
+    if dim == 1:
+        nx, dom = 10, (0.0, 3.0)
+        E = p / (gamma - 1) + 0.5 * rho * wx * wx
+        U = np.empty((3, nx, n))
+        U[0], U[1], U[2] = rho, rho * wx, E
+        o = Oracle(1, nx, 1, k, dom, "euler", gamma=gamma, bc=("periodic",) * 4)
+        o.set_state(U)
+        hx = 3.0 / nx
+        expect = cfl * hx / (abs(wx) + c)
+    else:
+        nx, ny, dom = 8, 5, (0.0, 2.0, 0.0, 3.0)
+        E = p / (gamma - 1) + 0.5 * rho * (wx * wx + wy * wy)
+        U = np.empty((4, ny, nx, n, n))
+        U[0], U[1], U[2], U[3] = rho, rho * wx, rho * wy, E
+        o = Oracle(2, nx, ny, k, dom, "euler", gamma=gamma, bc=("periodic",) * 4)
+        o.set_state(U)
+        hx, hy = 2.0 / nx, 3.0 / ny
+        expect = cfl / ((abs(wx) + c) / hx + (abs(wy) + c) / hy)
+    got = o.max_dt(cfl)
+    assert abs(got - expect) <= 1e-14 * expect, (got, expect)
+
+
+@pytest.mark.parametrize("flux,dim", [("burgers", 1), ("burgers", 2), ("advection", 1), ("advection", 2)])
+def test_trial_step_closed_form_scalar_laws(flux, dim):
+    """Scalar laws: the spectral radius is |u| (Burgers, in every direction) or |a_d|
+    (advection), so on a constant state u0 dt = CFL / (sum_d radius_d / h_d)."""
+    cfl, u0, vel = 0.1, -0.8, (0.6, -1.7)
+    k, n = 1, 2
+    if dim == 1:
+        nx, dom = 9, (0.0, 2.0)
+        U = np.full((1, nx, n), u0)
+        hs = (2.0 / nx,)
+    else:
+        nx, ny, dom = 7, 4, (0.0, 2.0, 0.0, 1.0)
+        U = np.full((1, ny, nx, n, n), u0)
+        hs = (2.0 / nx, 1.0 / ny)
+    o = Oracle(dim, nx, ny if dim == 2 else 1, k, dom, flux, velocity=vel, bounds=(-1.0, 1.0),
+               bc=("periodic",) * 4)
+    o.set_state(U)
+    radii = [abs(u0)] * dim if flux == "burgers" else [abs(vel[d]) for d in range(dim)]
+    expect = cfl / sum(r / h for r, h in zip(radii, hs))
+    got = o.max_dt(cfl)
+    assert abs(got - expect) <= 1e-14 * expect, (got, expect)
