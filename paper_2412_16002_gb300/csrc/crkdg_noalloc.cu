@@ -12,7 +12,6 @@
 // host code its name is only a host-side stand-in, so the device address is
 // looked up with cudaGetSymbolAddress once per device (with that device
 // current) and passed to the kernels.
-#include <math.h>
 #include <string.h>
 
 #include <mutex>
@@ -31,79 +30,6 @@ std::mutex g_mu;
 double *g_ptr[kMaxDevices] = {};  // device address of the scratch array, per device
 bool g_tables[kMaxDevices] = {};
 
-// Closed-form Gauss / Gauss--Lobatto rules and the Lagrange tables on the Gauss
-// nodes (same definitions as the handle-based path, built here independently
-// so that no existing code path changes).
-void rules(int n, double *x, double *w, double *xl) {
-    if (n == 2) {
-        x[0] = -1.0 / sqrt(3.0); x[1] = -x[0];
-        w[0] = w[1] = 1.0;
-        xl[0] = -1.0; xl[1] = 1.0;
-    } else if (n == 3) {
-        x[0] = -sqrt(0.6); x[1] = 0.0; x[2] = sqrt(0.6);
-        w[0] = w[2] = 5.0 / 9.0; w[1] = 8.0 / 9.0;
-        xl[0] = -1.0; xl[1] = 0.0; xl[2] = 1.0;
-    } else {
-        double r = 2.0 / 7.0 * sqrt(6.0 / 5.0);
-        double a = sqrt(3.0 / 7.0 - r), b = sqrt(3.0 / 7.0 + r);
-        x[0] = -b; x[1] = -a; x[2] = a; x[3] = b;
-        w[1] = w[2] = (18.0 + sqrt(30.0)) / 36.0;
-        w[0] = w[3] = (18.0 - sqrt(30.0)) / 36.0;
-        xl[0] = -1.0; xl[1] = 0.0; xl[2] = 1.0;
-    }
-}
-
-double lag(int n, const double *x, int a, double t) {
-    double v = 1.0;
-    for (int b = 0; b < n; ++b)
-        if (b != a) v *= (t - x[b]) / (x[a] - x[b]);
-    return v;
-}
-
-double dlag(int n, const double *x, int a, double t) {
-    double s = 0.0;
-    for (int c = 0; c < n; ++c) {
-        if (c == a) continue;
-        double v = 1.0 / (x[a] - x[c]);
-        for (int b = 0; b < n; ++b)
-            if (b != a && b != c) v *= (t - x[b]) / (x[a] - x[b]);
-        s += v;
-    }
-    return s;
-}
-
-void tables(NodalTables *tab) {
-    for (int n = 2; n <= 4; ++n) {
-        NodalTables &T = tab[n - 2];
-        memset(&T, 0, sizeof(T));
-        int L = nlob(n);
-        rules(n, T.xg, T.wg, T.xl);
-        for (int a = 0; a < n; ++a) {
-            for (int q = 0; q < n; ++q) T.Dhat[a][q] = T.wg[q] * dlag(n, T.xg, a, T.xg[q]) / T.wg[a];
-            T.lm[a] = lag(n, T.xg, a, -1.0);
-            T.lp[a] = lag(n, T.xg, a, 1.0);
-            T.liftm[a] = T.lm[a] / T.wg[a];
-            T.liftp[a] = T.lp[a] / T.wg[a];
-            for (int al = 0; al < L; ++al) T.Igl[al][a] = lag(n, T.xg, a, T.xl[al]);
-            T.w1[a] = 0.5 * T.wg[a];
-        }
-        for (int b = 0; b < n; ++b)
-            for (int a = 0; a < n; ++a) T.w2[b * n + a] = 0.25 * T.wg[a] * T.wg[b];
-        for (int a = 0; a < MAXN; ++a) {
-            for (int q = 0; q < MAXN; ++q) {
-                T.Dhatf[a][q] = (float)T.Dhat[a][q];
-                T.Iglf[a][q] = (float)T.Igl[a][q];
-            }
-            T.lmf[a] = (float)T.lm[a];
-            T.lpf[a] = (float)T.lp[a];
-            T.liftmf[a] = (float)T.liftm[a];
-            T.liftpf[a] = (float)T.liftp[a];
-            T.w1f[a] = (float)T.w1[a];
-        }
-        for (int q = 0; q < MAXN * MAXN; ++q) T.w2f[q] = (float)T.w2[q];
-    }
-}
-
 // Once per device, with that device current: the scratch address and the tables.
 crkdg_status setup(int dev, int dim, double **ptr) {
     std::lock_guard<std::mutex> lock(g_mu);
@@ -114,8 +40,11 @@ crkdg_status setup(int dev, int dim, double **ptr) {
         g_ptr[dev] = (double *)p;
     }
     if (!g_tables[dev]) {
+        // The handle path's own table builder: the upload rewrites the constant tables
+        // that every handle on this device reads with the same bytes, so a handle
+        // created earlier keeps computing with complete, identical tables.
         NodalTables tab[3];
-        tables(tab);
+        crkdg_build_tables(tab);
         if (crkdg_upload_tables_1d(tab) != cudaSuccess) return CRKDG_E_CUDA;
         if (crkdg_upload_tables_2d(tab) != cudaSuccess) return CRKDG_E_CUDA;
         g_tables[dev] = true;
