@@ -5,8 +5,11 @@ Metric: cell-DOF updates per second per RK stage = cells * m(k+1)^d * s / time,
 counting every accepted time step (s stages + limiters + the final stage + the
 dt control).  One bench step = one cRKDG time step of the workload.
 
-Default workload (N=1): 1D Euler (gamma 1.4) blast tube on [0,9], 4096 cells,
-P^2, Heun-3 cRKDG with the positivity limiter, FP64, eps 1e-13, CFL 0.178.
+Default workload (N=1): the largest single-GPU configuration, the 2D Euler
+(gamma 1.4) Sedov-type blast on [0,1.1]^2, 2048 x 2048 cells, Q^3, four-stage
+fourth-order cRKDG (CFL 0.103), split precision: FP64 cell averages, limiter
+decisions, conservation sums and time step; FP32 operators.  Other
+configurations: --workload.
 
 Arms:
   --impl gb300      (default) the CUDA library through its C ABI.
@@ -49,7 +52,9 @@ WORKLOADS = {
     "riemann_1024_q2_mixed_mlp": dict(kind="riemann", nx=1024, k=2, precision="mixed", indicator="mlp"),
     "ensemble_64_riemann_mlp": dict(kind="ensemble", count=64, indicator="mlp"),
 }
-DEFAULT = "euler1d_blast_tube_4096_p2"
+DEFAULT = "sedov_2048_q3_mixed"
+# timed steps when --steps is not given
+DEFAULT_STEPS = {"euler1d": 2000, "burgers": 2000, "sedov": 50, "riemann": 100, "ensemble": 5}
 
 
 def launches_per_attempt(precision, indicator):
@@ -208,66 +213,144 @@ def read_traffic(kernel, workload):
     return None
 
 
-def oracle_rate(wl, budget_s=10.0, max_steps=10**6, name=None):
-    """Oracle (plain C, one host thread) on the same workload: DOF-stage updates / s.  Meshes
-    beyond 16384 cells are sampled as the same workload on a 64-cell-wide mesh."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_sample(name, nx=None):
+    """The workload the oracle steps: the full mesh when it has at most 16384 cells, else
+    the same workload on an nx-cell-wide mesh (64 by default; a bounded sample)."""
+    wl = make_workload(name)
+    if wl.cells > 16384:
+        wl = make_workload(name, nx=nx or 64)
+    return wl
+
+
+def reference_sample_width(name, total_steps, budget_s=150.0):
+    """Width of the reference arm's sample mesh, chosen so that total_steps oracle steps take
+    about budget_s: one calibration step on a 16-wide mesh, then the cost scaled by the cell
+    count (64 at most, 4 at least).  None for workloads small enough to run in full."""
+    if make_workload(name).cells <= 16384:
+        return None
+    n, el, _ = _oracle_worker(name, 1, 1, 0.0, 16)
+    per_cell = el / max(n, 1) / (16 * 16)
+    cells = budget_s / max(total_steps, 1) / max(per_cell, 1e-12)
+    return int(max(4, min(64, cells ** 0.5)))
+
+
+def _oracle_worker(name, warmup, steps, budget_s, nx=None):
+    """One host process: the oracle (plain C, one thread) steps the sample of `name`; returns
+    (accepted timed steps, seconds, units per step).  With steps None it runs until budget_s."""
+    sys.path.insert(0, ROOT)
     from oracle import HEUN3, MIDPOINT2, RK4, Oracle
 
     tabs = {"midpoint2": MIDPOINT2, "heun3": HEUN3, "rk4": RK4}
-    if wl.cells > 16384 and name is not None:
-        wl = make_workload(name, nx=64)
+    wl = oracle_sample(name, nx)
     o = Oracle(wl.dim, wl.nx, wl.ny, wl.k, wl.domain, wl.flux, gamma=wl.gamma, velocity=wl.velocity,
                bounds=wl.bounds, eps=wl.eps, bc=wl.bc, bc_state=wl.bc_state)
     o.set_state(wl.state)
     t = 0.0
-    steps = 0
+    for _ in range(warmup):
+        rc, info = o.step(o.max_dt(wl.cfl), tabs[wl.tableau], t)
+        t += info["dt_taken"]
+    n = 0
     t0 = time.perf_counter()
-    while steps < max_steps and time.perf_counter() - t0 < budget_s:
-        dt = o.max_dt(wl.cfl)
-        rc, info = o.step(dt, tabs[wl.tableau], t)
+    while (n < steps) if steps is not None else (time.perf_counter() - t0 < budget_s):
+        rc, info = o.step(o.max_dt(wl.cfl), tabs[wl.tableau], t)
         if rc != 0:
             break
         t += info["dt_taken"]
-        steps += 1
+        n += 1
     el = time.perf_counter() - t0
-    units = wl.cells * wl.dofs_per_cell * TAB_S[wl.tableau] * steps
-    return units / el, steps, el, wl
+    return n, el, wl.cells * wl.dofs_per_cell * TAB_S[wl.tableau]
+
+
+def oracle_throughput(name, procs, warmup=0, steps=None, budget_s=10.0, nx=None):
+    """Oracle throughput on `procs` host cores: procs independent processes (spawned, so no
+    CUDA state is inherited) each step their own copy of the sample; the job's time is the
+    slowest process's.  Returns (cell-DOF-stage/s, steps per process, seconds)."""
+    if procs == 1:
+        n, el, u = _oracle_worker(name, warmup, steps, budget_s, nx)
+        return n * u / el, n, el
+    import multiprocessing as mp
+
+    from oracle.oracle import build_oracle
+
+    build_oracle()  # once, before the workers load it
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        res = pool.starmap(_oracle_worker, [(name, warmup, steps, budget_s, nx)] * procs)
+    el = max(r[1] for r in res)
+    units = sum(r[0] * r[2] for r in res)
+    return units / el, min(r[0] for r in res), el
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline_record(name, budget_s):
+    """The oracle timed on one host core and on every host core (independent processes)."""
+    swl = oracle_sample(name)
+    mesh = f"{swl.nx}x{swl.ny}" if swl.dim == 2 else f"{swl.nx}"
+    cores = host_cores()
+    v1, n1, el1 = oracle_throughput(name, 1, budget_s=budget_s)
+    vp, np_, elp = oracle_throughput(name, cores, budget_s=budget_s) if cores > 1 else (v1, n1, el1)
+    return {"value": vp, "unit": "cell-DOF-stage/s", "cores": cores, "kind": "oracle",
+            "single_core_value": v1, "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "sample": f"{name} on a {mesh}-cell mesh from its initial state: {n1} steps on one core "
+                      f"({el1:.1f} s); then {cores} independent oracle processes, one per core, "
+                      f"at least {np_} steps each ({elp:.1f} s)"}
+
+
+def workload_config(name, wl, world):
+    """The config dict both arms print for a workload."""
+    return {"workload": name, "precision": WORKLOADS[name].get("precision", "fp64"),
+            "indicator": WORKLOADS[name].get("indicator", "off"), "cells": wl.cells, "k": wl.k, "m": wl.m,
+            "dofs_per_cell": wl.dofs_per_cell, "tableau": wl.tableau, "stages": TAB_S[wl.tableau],
+            "cfl": wl.cfl, "initial_state": "the workload's initial data at t = 0",
+            "l2": "GPU arm: L2 flushed (256 MB write) between timed steps" if wl.dim == 2 else
+                  "GPU arm: state L2-resident by design in the device-resident loop; L2 flushed before the timed launch",
+            "parallelism": f"replicas{world}"}
 
 
 def run_reference(args, wl, name):
     world, rank, _ = dist_setup()
     if rank != 0:
         return
-    from oracle import HEUN3, MIDPOINT2, RK4, Oracle
-
-    tabs = {"midpoint2": MIDPOINT2, "heun3": HEUN3, "rk4": RK4}
-    full = wl
-    if wl.cells > 16384:  # each step is a bounded sample: the same workload on a 64-wide mesh
-        wl = make_workload(name, nx=64)
-    o = Oracle(wl.dim, wl.nx, wl.ny, wl.k, wl.domain, wl.flux, gamma=wl.gamma, velocity=wl.velocity,
-               bounds=wl.bounds, eps=wl.eps, bc=wl.bc, bc_state=wl.bc_state)
-    o.set_state(wl.state)
-    t = 0.0
-    for _ in range(args.warmup):
-        rc, info = o.step(o.max_dt(wl.cfl), tabs[wl.tableau], t)
-        t += info["dt_taken"]
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        rc, info = o.step(o.max_dt(wl.cfl), tabs[wl.tableau], t)
-        t += info["dt_taken"]
-    el = time.perf_counter() - t0
-    units = wl.cells * wl.dofs_per_cell * TAB_S[wl.tableau] * args.steps
-    v = units / el
+    cores = host_cores()
+    nx = reference_sample_width(name, args.steps + args.warmup)
+    swl = oracle_sample(name, nx)
+    v, n, el = oracle_throughput(name, cores, warmup=args.warmup, steps=args.steps, nx=nx)
+    mesh = f"{swl.nx}x{swl.ny}" if swl.dim == 2 else f"{swl.nx}"
     line = {
         "impl": "reference", "metric": "cell-DOF updates/s per RK stage", "value": v,
         "unit": "cell-DOF-stage/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": name, "cells": wl.cells, "k": wl.k, "m": wl.m, "tableau": wl.tableau,
-                   "cfl": wl.cfl},
-        "cpu_baseline": {"value": v, "unit": "cell-DOF-stage/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} time steps of {name} on a {wl.nx}x{wl.ny} mesh "
-                                   f"(full mesh {full.nx}x{full.ny}) after {args.warmup} warm-up steps"},
+        "config": workload_config(name, wl, world),
+        "cpu_baseline": {"value": v, "unit": "cell-DOF-stage/s", "cores": cores, "kind": "oracle",
+                         "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+                         "sample": f"{cores} independent oracle processes, one per host core, each "
+                                   f"{args.steps} time steps of {name} on a {mesh} mesh (full mesh "
+                                   f"{wl.nx}x{wl.ny}) after {args.warmup} warm-up steps"},
         "e2e": {"value": v, "unit": "cell-DOF-stage/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -359,7 +442,7 @@ def run_gb300(args, wl, name):
 
     lib, h = g.lib, g.h
     nbytes = host_in.numel() * 8
-    e2e_steps = max(3, args.steps)
+    e2e_steps = max(3, args.steps if wl.dim == 1 else min(args.steps, 10))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -403,11 +486,8 @@ def run_gb300(args, wl, name):
             "vs_baseline": None,
             "dtype": "f64" if precision == "fp64" else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": name, "precision": precision, "indicator": indicator, "training": train,
-                       "cells": wl.cells, "k": wl.k, "m": wl.m, "dofs_per_cell": wl.dofs_per_cell,
-                       "tableau": wl.tableau, "stages": TAB_S[wl.tableau], "cfl": wl.cfl,
-                       "l2": l2_note, "parallelism": f"replicas{world}",
-                       "restarts_in_timed_steps": restarts, "t_after": t},
+            "config": workload_config(name, wl, world),
+            "run": {"training": train, "restarts_in_timed_steps": restarts, "t_after": t, "l2": l2_note},
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": read_traffic(dom, name),
@@ -421,11 +501,7 @@ def run_gb300(args, wl, name):
             "clocks": clocks,
         }
         if world == 1 and not args.no_cpu_baseline:
-            v, n, el, swl = oracle_rate(wl, budget_s=args.cpu_seconds, name=name)
-            mesh = f"{swl.nx}x{swl.ny}" if swl.dim == 2 else f"{swl.nx}"
-            line["cpu_baseline"] = {"value": v, "unit": "cell-DOF-stage/s", "cores": 1, "kind": "oracle",
-                                    "sample": f"{n} time steps of {name} on a {mesh}-cell mesh from the initial "
-                                              f"state ({el:.1f} s, one thread)"}
+            line["cpu_baseline"] = cpu_baseline_record(name, args.cpu_seconds)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -562,10 +638,8 @@ def run_ensemble(args, name):
             "clocks": clocks,
         }
         if world == 1 and not args.no_cpu_baseline:
-            v, n, el, swl = oracle_rate(make_workload(name, nx=64), budget_s=args.cpu_seconds)
-            line["cpu_baseline"] = {"value": v, "unit": "cell-DOF-stage/s", "cores": 1, "kind": "oracle",
-                                    "sample": f"{n} time steps of one Q^2 Riemann problem of the ensemble on a "
-                                              f"64x64 mesh ({el:.1f} s, one thread, no indicator)"}
+            line["cpu_baseline"] = cpu_baseline_record(name, args.cpu_seconds)
+            line["cpu_baseline"]["sample"] += " (one Q^2 Riemann problem of the ensemble, no indicator)"
         print(json.dumps(line))
     ens.close()
     if world > 1:
@@ -575,7 +649,7 @@ def run_ensemble(args, name):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
@@ -583,6 +657,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
+    if args.steps is None:
+        args.steps = DEFAULT_STEPS[WORKLOADS[args.workload]["kind"]]
     wl = make_workload(args.workload)
     if args.impl == "reference":
         run_reference(args, wl, args.workload)

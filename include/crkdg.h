@@ -131,7 +131,12 @@ typedef struct {
     long long cells_limited;  /* cells with theta < 1 over all stages of the accepted attempt */
     double theta_min;         /* smallest theta of the accepted attempt */
     long long troubled;       /* cells flagged by the indicator (0 if off) */
-    double mass_drift;        /* reserved (0) */
+    double mass_drift;        /* (M^{n+1} - M^n) / |M^n| for the first component's total
+                                 M = sum_K |K| ubar_K (mass, or the scalar), summed on the
+                                 device in a fixed order: the conservation error of the step
+                                 (round-off) when no side lets mass in or out (periodic,
+                                 reflect); with open sides it also holds the net boundary
+                                 inflow of the step.  Ensembles report 0. */
 } crkdg_step_info;
 
 /* Fill *opt with the defaults. */
@@ -378,8 +383,10 @@ const char *crkdg_ensemble_last_error(crkdg_ens_t e);
  *
  * The first call on each device does a one-time set-up with that device
  * current: it looks up the array's device address (cudaGetSymbolAddress) and
- * uploads the nodal tables (cudaMemcpyToSymbol).  Make that first call before
- * any stream capture.  Afterwards the call only enqueues two kernels on
+ * uploads the library's constant nodal tables (cudaMemcpyToSymbol), built by the
+ * same routine as a handle's, so handles that already exist on the device see
+ * the same bytes they uploaded themselves.  Make that first call before any
+ * stream capture.  Afterwards the call only enqueues two kernels on
  * cuda_stream (NULL: the legacy default stream) and returns without
  * synchronising.  It calls no cudaMalloc, cudaFree or other allocating routine.
  * Errors: CRKDG_E_ARG (bad mesh, kinds, pointers, or beyond the scratch size),

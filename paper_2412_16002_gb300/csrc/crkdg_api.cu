@@ -24,6 +24,7 @@ struct DevScal {
     unsigned long long a0;
     unsigned long long ord[2];
     unsigned long long ntrb;
+    double mass[MAXM];  // sum over cells of the cell averages, per component (fixed order)
 };
 
 uint64_t bits_of(double x) {
@@ -38,6 +39,41 @@ double from_bits(uint64_t u) {
 }
 double from_ordbits(uint64_t u) {
     return from_bits((u >> 63) ? (u & 0x7fffffffffffffffull) : ~u);
+}
+
+// ---------------------------------------------------------------- component totals
+// Deterministic sums over the cells of per-cell values x[cell * cs + comp * ms] (the cell
+// averages, in either buffer layout): block b sums cells [b * kSumCells, (b + 1) * kSumCells)
+// by a fixed pairwise tree, then one block adds the block sums in block order.  The result
+// does not depend on scheduling, so repeated runs give the same bits.
+constexpr int kSumThreads = 256, kSumCells = 4 * kSumThreads;
+
+__global__ void k_colsum_part(const double *x, long long cs, long long ms, int ncell, int m, double *part) {
+    __shared__ double sh[kSumThreads];
+    const int b = blockIdx.x, t = threadIdx.x;
+    for (int c = 0; c < m; ++c) {
+        double v = 0.0;
+        for (int j = 0; j < kSumCells / kSumThreads; ++j) {
+            long long cell = (long long)b * kSumCells + (long long)j * kSumThreads + t;
+            if (cell < ncell) v += x[cell * cs + c * ms];
+        }
+        sh[t] = v;
+        __syncthreads();
+        for (int w = kSumThreads / 2; w > 0; w >>= 1) {
+            if (t < w) sh[t] += sh[t + w];
+            __syncthreads();
+        }
+        if (t == 0) part[(size_t)b * m + c] = sh[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_colsum_final(const double *part, int nblk, int m, double *out) {
+    if (threadIdx.x < m) {
+        double v = 0.0;
+        for (int b = 0; b < nblk; ++b) v += part[(size_t)b * m + threadIdx.x];
+        out[threadIdx.x] = v;
+    }
 }
 
 // ---------------------------------------------------------------- nodal tables
@@ -179,6 +215,9 @@ struct crkdg_ctx {
     int run1d_chunk = 0;     // own cells per block chunk of the 1D step loop (0: automatic)
     RunCtl *ctl = nullptr;   // device control block of the 1D step loop
     RunCtl *hctl = nullptr;  // pinned host copy
+    double *mass_part = nullptr;  // block sums of the component totals
+    double mass_n[MAXM] = {};     // component totals of u^n (valid when mass_valid)
+    bool mass_valid = false;
     std::string err;
 };
 
@@ -326,6 +365,37 @@ crkdg_status read_scalars(crkdg_ctx *h) {
     return CRKDG_OK;
 }
 
+// Queue the component totals of a state into scal->mass (read by the next read_scalars).
+// FP64 path: the averages of the nodal state `nodal` (aux is overwritten); split path: the
+// stored FP64 averages `ub` ([m][cell]).
+crkdg_status queue_mass(crkdg_ctx *h, const double *nodal, const double *ub) {
+    const double *x;
+    long long cs, ms;
+    if (h->mixed) {
+        x = ub;
+        cs = 1;
+        ms = h->ncell;
+    } else {
+        Bufs B = base_bufs(h);
+        B.un = nodal;
+        CK(h, launch(h, K_AVG, base_params(h), B));
+        x = h->aux;
+        cs = h->m;
+        ms = 1;
+    }
+    const int nblk = (h->ncell + kSumCells - 1) / kSumCells;
+    k_colsum_part<<<nblk, kSumThreads, 0, h->st>>>(x, cs, ms, h->ncell, h->m, h->mass_part);
+    CK(h, cudaGetLastError());
+    k_colsum_final<<<1, 32, 0, h->st>>>(h->mass_part, nblk, h->m, h->scal->mass);
+    CK(h, cudaGetLastError());
+    return CRKDG_OK;
+}
+
+void take_mass(crkdg_ctx *h) {
+    for (int c = 0; c < h->m; ++c) h->mass_n[c] = h->hs->mass[c];
+    h->mass_valid = true;
+}
+
 crkdg_status ensure_traces(crkdg_ctx *h, int slots) {
     if (slots <= h->tr_slots) return CRKDG_OK;
     if (h->tr) cudaFree(h->tr);
@@ -471,6 +541,9 @@ crkdg_status crkdg_create(const crkdg_mesh *mesh, int k, int m, const crkdg_flux
         if (s == CRKDG_OK) chk(cudaMalloc(&h->ustar, bytes), "cudaMalloc state");
         if (s == CRKDG_OK) chk(cudaMalloc(&h->aux, (size_t)h->ncell * h->m * sizeof(double)), "cudaMalloc aux");
         if (s == CRKDG_OK) chk(cudaMalloc(&h->scal, sizeof(DevScal)), "cudaMalloc scalars");
+        if (s == CRKDG_OK)
+            chk(cudaMalloc(&h->mass_part, (size_t)((h->ncell + kSumCells - 1) / kSumCells) * h->m * sizeof(double)),
+                "cudaMalloc totals");
         if (s == CRKDG_OK) chk(cudaMallocHost(&h->hs, sizeof(DevScal)), "cudaMallocHost");
         if (s == CRKDG_OK) chk(cudaMallocHost(&h->hinit, sizeof(DevScal)), "cudaMallocHost");
         h->mixed = o.precision == CRKDG_PREC_MIXED;
@@ -814,6 +887,7 @@ static crkdg_status advance_1d(crkdg_t h, int nsteps, double cfl, double dt_fixe
         h->u = h->unew;
         h->unew = tmp;
     }
+    if (c->steps > 0) h->mass_valid = false;  // the loop keeps no component totals
     *t = c->t_out;
     if (steps_done) *steps_done = c->steps;
     if (restarts) *restarts = c->restarts;

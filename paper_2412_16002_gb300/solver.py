@@ -134,7 +134,7 @@ class Solver:
         info = L.StepInfo()
         self._chk(self.lib.crkdg_step(self.h, dt, C.byref(self._tab(tableau).c), C.byref(info)))
         return {"dt_taken": info.dt_taken, "restarts": info.restarts, "cells_limited": info.cells_limited,
-                "theta_min": info.theta_min, "troubled": info.troubled}
+                "theta_min": info.theta_min, "troubled": info.troubled, "mass_drift": info.mass_drift}
 
     def advance(self, nsteps, cfl, t_end, tableau="heun3", t=0.0):
         tt = C.c_double(t)
