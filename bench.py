@@ -1,5 +1,5 @@
 #!/usr/bin/env python
-"""Throughput of the cRKDG hot path on one GB300 (or N independent replicas).
+"""Throughput of the cRKDG hot path on one GB300 (or one mesh split over N GPUs).
 
 Metric: cell-DOF updates per second per RK stage = cells * m(k+1)^d * s / time,
 counting every accepted time step (s stages + limiters + the final stage + the
@@ -14,8 +14,11 @@ configurations: --workload.
 Arms:
   --impl gb300      (default) the CUDA library through its C ABI.
   --impl reference  the CPU oracle on the host cores (rank 0 only).
-Under torchrun each rank advances its own replica (weak scaling, no data-path
-collective); the reported time is the maximum over ranks.
+Under torchrun (N > 1) the workload's one mesh is split into N blocks, one per
+rank (strong scaling): one halo exchange per step plus the global trial step
+and restart decision (paper_2412_16002_gb300.decomp); the ensemble and the
+indicator workloads run N independent replicas instead (weak scaling).  The
+reported time is the maximum over ranks.
 """
 from __future__ import annotations
 
@@ -356,10 +359,140 @@ def run_reference(args, wl, name):
     print(json.dumps(line))
 
 
+def proc_grid(world, dim):
+    """px x py blocks for `world` ranks: 1D a row; 2D the most square factorisation, the longer
+    side along x."""
+    if dim == 1:
+        return world, 1
+    py = int(world ** 0.5)
+    while world % py:
+        py -= 1
+    return world // py, py
+
+
+def run_decomposed(args, wl, name):
+    """N > 1: the workload's one mesh split into N blocks, one per GPU (strong scaling): each
+    step one halo exchange of u^n's boundary layer (NCCL with device buffers, or gloo with
+    host-staged buffers), the global trial step (all-reduce MIN) and the global restart
+    decision (all-reduce of the flags).  Time: CUDA events on each rank's stream around the
+    K steps (host-side collectives included), maximum over ranks."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2412_16002_gb300.decomp import DomainSolver, Layout, TorchTransport
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist.init_process_group(args.dist_backend)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        from paper_2412_16002_gb300 import build
+
+        build()
+    dist.barrier()
+    from paper_2412_16002_gb300.solver import Solver
+
+    precision = WORKLOADS[name].get("precision", "fp64")
+    if WORKLOADS[name].get("indicator", "off") != "off":
+        raise SystemExit("the troubled-cell indicators are not available on subdomains")
+    px, py = proc_grid(world, wl.dim)
+    lay = Layout(wl.dim, wl.nx, wl.ny, px, py, rank, (wl.bc[0] == "periodic", wl.bc[2] == "periodic"))
+    ldom, lbc = lay.local_mesh(wl.domain, wl.bc)
+    stream = torch.cuda.current_stream()
+    g = Solver(wl.dim, lay.nxl, lay.nyl, wl.k, ldom, wl.flux, gamma=wl.gamma, velocity=wl.velocity,
+               bounds=wl.bounds, eps=wl.eps, bc=lbc, bc_state=wl.bc_state, stream=stream, precision=precision)
+    nccl = args.dist_backend == "nccl"
+    tr = TorchTransport(device=dev if nccl else None)
+    ds = DomainSolver(lay, g, tr, wl.domain, device_buffers=nccl, device=dev)
+    local_state = ds.local_block(wl.state)
+    g.set_state(torch.from_numpy(local_state).to(dev))
+    for _ in range(args.warmup):
+        ds.step(ds.max_dt(wl.cfl), wl.tableau)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    g.set_profiling(True)
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    dist.barrier()
+    torch.cuda.synchronize()
+    restarts = 0
+    ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = ds.step(ds.max_dt(wl.cfl), wl.tableau)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        restarts += info["restarts"]
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    kt, kn = g.kernel_times()
+    g.set_profiling(False)
+    units = wl.cells * wl.dofs_per_cell * TAB_S[wl.tableau] * args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = units / (ms_max / 1e3)
+
+    # end to end: each rank's local block host -> device, the steps, its state device -> host
+    host_in = torch.from_numpy(local_state.reshape(-1).copy()).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    import ctypes as C
+
+    e2e_steps = max(3, min(args.steps, 10))
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g._chk(g.lib.crkdg_set_state(g.h, C.c_void_p(host_in.data_ptr()), host_in.numel(), 0))
+        ds.step(ds.max_dt(wl.cfl), wl.tableau)
+        g._chk(g.lib.crkdg_get_state(g.h, C.c_void_p(host_out.data_ptr()), host_out.numel(), 0))
+    torch.cuda.synchronize()
+    t = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = wl.cells * wl.dofs_per_cell * TAB_S[wl.tableau] * e2e_steps / float(t.item())
+    nbytes = host_in.numel() * 8 * world  # every rank's local block (owned cells and halo ring)
+    if rank == 0:
+        inner_f, final_f = algorithmic_flops(wl)
+        avg_inner = kt["inner"] / max(kn["inner"], 1)
+        avg_final = kt["final"] / max(kn["final"], 1)
+        sfx = "_x" if precision == "mixed" else ""
+        dom_k, avg_ms, fl = ("k_inner" + sfx, avg_inner, inner_f) if avg_inner >= avg_final else \
+            ("k_final" + sfx, avg_final, final_f)
+        achieved = fl * lay.nxl * lay.nyl / (avg_ms / 1e3) / 1e12
+        peak = FP32_PEAK_TFLOPS if precision == "mixed" else FP64_PEAK_TFLOPS
+        cfg = workload_config(name, wl, world)
+        cfg["parallelism"] = f"domain{px}x{py}"
+        line = {
+            "metric": "cell-DOF updates/s per RK stage", "value": value, "unit": "cell-DOF-stage/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "f64" if precision == "fp64" else "f32+f64", "data": "synthetic", "config": cfg,
+            "run": {"backend": args.dist_backend, "halo_bytes_per_rank_step": ds.halo_bytes,
+                    "restarts_in_timed_steps": restarts, "rank0_local_cells": lay.nxl * lay.nyl},
+            "roofline": {"bound": "alu", "kernel": dom_k, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "note": "rank 0's dominant kernel over its local cells (owned block and halo ring)"},
+            "e2e": {"value": e2e_value, "unit": "cell-DOF-stage/s", "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes},
+            "gpu_launches": int(kn["inner"]) * 2 * world,
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    g.close()
+    dist.destroy_process_group()
+
+
 def run_gb300(args, wl, name):
     import torch
 
     world, rank, local = dist_setup()
+    if world > 1 and WORKLOADS[name]["kind"] != "ensemble" and WORKLOADS[name].get("indicator", "off") == "off":
+        return run_decomposed(args, wl, name)
     if world > 1:
         import torch.distributed as dist
 
@@ -655,6 +788,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dist-backend", default="nccl", choices=["nccl", "gloo"],
+                    help="N > 1: halo exchange over NCCL (device buffers) or gloo (host-staged)")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
     if args.steps is None:

@@ -279,6 +279,60 @@ crkdg_status crkdg_set_run1d_chunk(crkdg_t h, int cells);
 /* Number of doubles of the state. */
 size_t crkdg_state_size(crkdg_t h);
 
+/* ------------------------------------------------------------------------
+ * One step in two calls, for callers that decide acceptance across several
+ * handles (the subdomains of a decomposed mesh, below).  crkdg_step_attempt runs
+ * one attempt of size dt from u^n (no restart) and sets *violated to 1 if a
+ * stage's cell averages left B (Sec. 4.1 test), else 0; u^n is kept.
+ * crkdg_step_accept makes that attempt's result the new state (CRKDG_E_ARG if
+ * there is no attempt or it violated); info as for crkdg_step (restarts 0).
+ * To restart, call crkdg_step_attempt again with dt/2: crkdg_step is exactly
+ * this loop on one handle. */
+crkdg_status crkdg_step_attempt(crkdg_t h, double dt, const crkdg_tableau *tab, int *violated);
+crkdg_status crkdg_step_accept(crkdg_t h, crkdg_step_info *info);
+
+/* ------------------------------------------------------------------------
+ * Subdomains of a block-decomposed mesh (multi-GPU; Sec. 1 and the Compactness
+ * remark of Sec. 3.2: the inner stages need no neighbour data, so one exchange of
+ * u^n's boundary-cell layer per step suffices when the inner stages are
+ * recomputed on a one-cell halo).  A rank builds a handle on its own block of
+ * cells plus a one-cell halo ring on every side that borders another block (or
+ * wraps periodically), and marks its own cells with crkdg_set_subdomain: only
+ * those count in the admissibility flag, the limiter statistics, the trial-step
+ * rate (crkdg_max_dt), the bound margins and the totals; the halo cells are
+ * stepped as well (their inner stages are exactly those of the cells they
+ * copy, which the owned cells' final stage reads) and their results are
+ * discarded.  Each step the halo ring is refreshed from the neighbours' owned
+ * cells (crkdg_pack_cells on the sender, crkdg_unpack_cells on the receiver),
+ * the ranks agree on dt = min of their crkdg_max_dt, and on restarts through
+ * crkdg_step_attempt / crkdg_step_accept (OR of the violation flags).  The
+ * troubled-cell indicators are not available on a subdomain
+ * (CRKDG_E_UNSUPPORTED): they read a 3x3 stencil after the final stage, which
+ * needs a second exchange.
+ *
+ * crkdg_set_subdomain: the owned cells are [i0, i1) x [j0, j1) of this handle's
+ * mesh (1D: j ignored; the whole mesh restores the default).  global (nullable)
+ * is the undecomposed mesh this one is a window of: the cell sizes are then
+ * formed from it exactly as its own handle forms them, so the owned cells'
+ * arithmetic is bit-identical to the undecomposed run (a window's own
+ * (x1 - x0) / nx can differ in the last bit); CRKDG_E_ARG if the window's cells
+ * are not that mesh's cells. */
+crkdg_status crkdg_set_subdomain(crkdg_t h, const crkdg_mesh *global, int i0, int i1, int j0, int j1);
+/* Bytes of the packed form of `cells` cells: FP64 nodal values
+ * [m][rows][cols][n^d] doubles; split precision: the FP64 cell averages
+ * [m][rows][cols] doubles followed by the FP32 deviations [m][rows][cols][n^d]
+ * floats (the state's own representation, so a copy is exact).  0 on bad
+ * arguments. */
+size_t crkdg_cells_bytes(crkdg_t h, long long cells);
+/* Copy the cells of the box [i0, i1) x [j0, j1) of u^n into buf (pack) or from
+ * buf into u^n (unpack; no limiter is applied: the values come from another
+ * handle's state).  bytes must equal crkdg_cells_bytes of the box.  Host buffers
+ * (on_device 0) are complete / reusable when the call returns; device buffers
+ * are stream-ordered on the handle's stream. */
+crkdg_status crkdg_pack_cells(crkdg_t h, int i0, int i1, int j0, int j1, void *buf, size_t bytes, int on_device);
+crkdg_status crkdg_unpack_cells(crkdg_t h, int i0, int i1, int j0, int j1, const void *buf, size_t bytes,
+                                int on_device);
+
 /* Human-readable description of the last error on h (static string if h is NULL). */
 const char *crkdg_last_error(crkdg_t h);
 

@@ -98,6 +98,12 @@ SYMBOLS = {
     "crkdg_set_run1d_chunk": (C.c_int, [_H, C.c_int]),
     "crkdg_kernel_times": (C.c_int, [_H, _dp, C.POINTER(C.c_longlong)]),
     "crkdg_state_size": (C.c_size_t, [_H]),
+    "crkdg_step_attempt": (C.c_int, [_H, C.c_double, C.POINTER(Tableau), C.POINTER(C.c_int)]),
+    "crkdg_step_accept": (C.c_int, [_H, C.POINTER(StepInfo)]),
+    "crkdg_set_subdomain": (C.c_int, [_H, C.POINTER(Mesh), C.c_int, C.c_int, C.c_int, C.c_int]),
+    "crkdg_cells_bytes": (C.c_size_t, [_H, C.c_longlong]),
+    "crkdg_pack_cells": (C.c_int, [_H, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_int]),
+    "crkdg_unpack_cells": (C.c_int, [_H, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_int]),
     "crkdg_last_error": (C.c_char_p, [_H]),
     "crkdg_apply_F_noalloc": (C.c_int, [C.POINTER(Mesh), C.c_int, C.c_int, C.POINTER(Flux), C.c_void_p,
                                         C.c_void_p, C.c_void_p]),

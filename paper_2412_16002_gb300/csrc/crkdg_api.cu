@@ -48,14 +48,20 @@ double from_ordbits(uint64_t u) {
 // does not depend on scheduling, so repeated runs give the same bits.
 constexpr int kSumThreads = 256, kSumCells = 4 * kSumThreads;
 
-__global__ void k_colsum_part(const double *x, long long cs, long long ms, int ncell, int m, double *part) {
+// The cells summed are those of the box [i0, i0 + w) x [j0, j0 + count / w) of a mesh nx wide
+// (the whole mesh: i0 = j0 = 0, w = nx).
+__global__ void k_colsum_part(const double *x, long long cs, long long ms, int count, int nx, int i0, int j0, int w,
+                              int m, double *part) {
     __shared__ double sh[kSumThreads];
     const int b = blockIdx.x, t = threadIdx.x;
     for (int c = 0; c < m; ++c) {
         double v = 0.0;
         for (int j = 0; j < kSumCells / kSumThreads; ++j) {
-            long long cell = (long long)b * kSumCells + (long long)j * kSumThreads + t;
-            if (cell < ncell) v += x[cell * cs + c * ms];
+            long long r = (long long)b * kSumCells + (long long)j * kSumThreads + t;
+            if (r < count) {
+                const long long cell = (j0 + r / w) * (long long)nx + i0 + r % w;
+                v += x[cell * cs + c * ms];
+            }
         }
         sh[t] = v;
         __syncthreads();
@@ -215,6 +221,12 @@ struct crkdg_ctx {
     int run1d_chunk = 0;     // own cells per block chunk of the 1D step loop (0: automatic)
     RunCtl *ctl = nullptr;   // device control block of the 1D step loop
     RunCtl *hctl = nullptr;  // pinned host copy
+    bool pending = false;         // an attempt (crkdg_step_attempt) waits for crkdg_step_accept
+    double pending_dt = 0.0;
+    bool own_on = false;          // owned box of a subdomain (crkdg_set_subdomain)
+    int own[4] = {0, 0, 0, 0};
+    bool metric_on = false;       // cell sizes taken from the global mesh of a subdomain
+    double rhx_g = 0.0, rhy_g = 0.0;
     double *mass_part = nullptr;  // block sums of the component totals
     double mass_n[MAXM] = {};     // component totals of u^n (valid when mass_valid)
     bool mass_valid = false;
@@ -242,8 +254,8 @@ Params base_params(const crkdg_ctx *h) {
     P.nx = h->mesh.nx;
     P.ny = h->dim == 2 ? h->mesh.ny : 1;
     P.ncell = h->ncell;
-    P.rhx = 2.0 * h->mesh.nx / (h->mesh.x1 - h->mesh.x0);
-    P.rhy = h->dim == 2 ? 2.0 * h->mesh.ny / (h->mesh.y1 - h->mesh.y0) : 0.0;
+    P.rhx = h->metric_on ? h->rhx_g : 2.0 * h->mesh.nx / (h->mesh.x1 - h->mesh.x0);
+    P.rhy = h->dim == 2 ? (h->metric_on ? h->rhy_g : 2.0 * h->mesh.ny / (h->mesh.y1 - h->mesh.y0)) : 0.0;
     P.gamma = h->flux.gamma;
     P.velx = h->flux.velocity[0];
     P.vely = h->flux.velocity[1];
@@ -257,6 +269,8 @@ Params base_params(const crkdg_ctx *h) {
         P.bc[s] = (h->dim == 1 && s >= 2) ? BC_OUTFLOW : h->mesh.bc[s];
         for (int c = 0; c < MAXM; ++c) P.bcs[s][c] = h->mesh.bc_state[s][c];
     }
+    P.own_on = h->own_on ? 1 : 0;
+    for (int i = 0; i < 4; ++i) P.own[i] = h->own[i];
     for (int i = 0; i < MAXS; ++i) P.slot[i] = -1;
     return P;
 }
@@ -383,8 +397,15 @@ crkdg_status queue_mass(crkdg_ctx *h, const double *nodal, const double *ub) {
         cs = h->m;
         ms = 1;
     }
-    const int nblk = (h->ncell + kSumCells - 1) / kSumCells;
-    k_colsum_part<<<nblk, kSumThreads, 0, h->st>>>(x, cs, ms, h->ncell, h->m, h->mass_part);
+    int i0 = 0, j0 = 0, w = h->mesh.nx, count = h->ncell;
+    if (h->own_on) {
+        i0 = h->own[0];
+        j0 = h->own[2];
+        w = h->own[1] - h->own[0];
+        count = w * (h->own[3] - h->own[2]);
+    }
+    const int nblk = (count + kSumCells - 1) / kSumCells;
+    k_colsum_part<<<nblk, kSumThreads, 0, h->st>>>(x, cs, ms, count, h->mesh.nx, i0, j0, w, h->m, h->mass_part);
     CK(h, cudaGetLastError());
     k_colsum_final<<<1, 32, 0, h->st>>>(h->mass_part, nblk, h->m, h->scal->mass);
     CK(h, cudaGetLastError());
@@ -592,6 +613,7 @@ crkdg_status crkdg_destroy(crkdg_t h) {
     cudaFree(h->ustar);
     cudaFree(h->tr);
     cudaFree(h->aux);
+    cudaFree(h->mass_part);
     cudaFree(h->scal);
     cudaFreeHost(h->hs);
     cudaFreeHost(h->hinit);
@@ -665,7 +687,10 @@ crkdg_status crkdg_set_state(crkdg_t h, const double *nodal, size_t count, int o
             X = base_xbufs(h);
             X.dv_n = h->xdv[h->xcur];
             CK(h, launch_x(h, KX_LIMIT, P, X));
-            CK(h, cudaStreamSynchronize(h->st));
+            crkdg_status s = queue_mass(h, nullptr, h->xub[h->xcur]);
+            if (s == CRKDG_OK) s = read_scalars(h);
+            if (s) return s;
+            take_mass(h);
             h->a0_valid = false;
             return CRKDG_OK;
         }
@@ -676,8 +701,10 @@ crkdg_status crkdg_set_state(crkdg_t h, const double *nodal, size_t count, int o
         B.unew = h->u;
         P.mode = MODE_RATE;
         CK(h, launch(h, K_LIMIT, P, B));
-        crkdg_status s = read_scalars(h);
+        crkdg_status s = queue_mass(h, h->u, nullptr);
+        if (s == CRKDG_OK) s = read_scalars(h);
         if (s) return s;
+        take_mass(h);
         h->a0 = from_bits(h->hs->a0);
         h->a0_valid = true;
         return CRKDG_OK;
@@ -716,118 +743,167 @@ crkdg_status crkdg_max_dt(crkdg_t h, double cfl, double *dt) {
     }
 }
 
+}  // extern "C"
+
+namespace {
+
+// Parameters and trace buffers of a step with tableau tab (shared by crkdg_step and the
+// attempt / accept pair); with want_mass the totals of u^n are made current.
+crkdg_status prepare_step(crkdg_t h, double dt, const crkdg_tableau *tab, bool want_mass, Params &P) {
+    crkdg_status s = check_tableau(h, tab);
+    if (s) return s;
+    if (!(dt > 0.0) || !isfinite(dt)) return fail(h, CRKDG_E_ARG, "step: dt must be finite and > 0");
+    P = base_params(h);
+    P.s = tab->s;
+    P.mode = MODE_STEP;
+    P.defer_limit = h->opt.indicator != CRKDG_IND_OFF ? 1 : 0;
+    int ns = 0;
+    for (int i = 0; i < tab->s; ++i) {
+        P.b[i] = tab->b[i];
+        for (int j = 0; j < tab->s; ++j) P.A[i][j] = tab->A[i * tab->s + j];
+        P.slot[i] = tab->b[i] != 0.0 ? ns++ : -1;
+    }
+    P.nslot = ns;
+    s = h->mixed ? ensure_traces_x(h, ns > 0 ? ns : 1) : ensure_traces(h, ns > 0 ? ns : 1);
+    if (s) return s;
+    if (want_mass && !h->mass_valid) {
+        s = reset_scalars(h);
+        if (s == CRKDG_OK) s = queue_mass(h, h->u, h->mixed ? h->xub[h->xcur] : nullptr);
+        if (s == CRKDG_OK) s = read_scalars(h);
+        if (s) return s;
+        take_mass(h);
+    }
+    return CRKDG_OK;
+}
+
+// One attempt of size dt from u^n into the second state buffer; h->hs holds its flag and
+// statistics afterwards (synchronises the stream).
+crkdg_status attempt_once(crkdg_t h, Params &P, double dt, bool want_mass) {
+    const bool ind = h->opt.indicator != CRKDG_IND_OFF;
+    crkdg_status s;
+    P.dt = dt;
+    Bufs B = base_bufs(h);
+    B.un = h->u;
+    B.unew = h->unew;
+    s = reset_scalars(h);
+    if (s) return s;
+    if (h->prof) CK(h, cudaEventRecord(h->ev[0], h->st));
+    if (h->mixed) {
+        CK(h, launch_x(h, KX_INNER, P, base_xbufs(h)));
+    } else {
+        CK(h, launch(h, K_INNER, P, B));
+    }
+    if (h->prof) CK(h, cudaEventRecord(h->ev[1], h->st));
+    if (h->mixed) {
+        CK(h, launch_x(h, KX_FINAL, P, base_xbufs(h)));
+        if (ind) {
+            // the final stage left the unlimited u^{n+1} and its averages (aux); the plain
+            // decision is taken in the troubled-cell pass, unless features are wanted:
+            // then the FP64 feature kernel takes it on the merged nodal values
+            const bool learned = h->opt.indicator == CRKDG_IND_MLP;
+            if (learned && !h->harvest) {
+                // features from the split state; the troubled-cell pass takes the plain
+                // decision itself and combines it with the network's
+                CK(h, launch_x(h, KX_FEATURES, P, base_xbufs(h)));
+                if (crkdg_mlp_forward(h->mlp, h->feat, h->ncell, h->prob, h->st) != CRKDG_OK)
+                    return fail(h, CRKDG_E_CUDA, "step: MLP forward failed");
+                P.ind_stage = 4;
+            } else if (h->harvest) {
+                MixBufs Xn = base_xbufs(h);
+                Xn.ub = h->xub[1 - h->xcur];
+                Xn.dv = h->xdv[1 - h->xcur];
+                Xn.nod_out = h->unew;
+                CK(h, launch_x(h, KX_MERGE, P, Xn));
+                Bufs Bf = base_bufs(h);
+                Bf.unew = h->unew;
+                CK(h, launch(h, K_FEATURES, P, Bf));
+                if (learned && crkdg_mlp_forward(h->mlp, h->feat, h->ncell, h->prob, h->st) != CRKDG_OK)
+                    return fail(h, CRKDG_E_CUDA, "step: MLP forward failed");
+                P.ind_stage = learned ? 3 : 2;
+            } else {
+                P.ind_stage = 0;
+            }
+            CK(h, launch_x(h, KX_TROUBLE, P, base_xbufs(h)));
+            P.ind_stage = 0;
+        }
+    } else {
+        CK(h, launch(h, K_FINAL, P, B));
+        if (ind) {
+            const bool learned = h->opt.indicator == CRKDG_IND_MLP;
+            if (learned || h->harvest) {
+                // features and the plain decision of the unlimited state in one pass
+                CK(h, launch(h, K_FEATURES, P, B));
+                if (learned && crkdg_mlp_forward(h->mlp, h->feat, h->ncell, h->prob, h->st) != CRKDG_OK)
+                    return fail(h, CRKDG_E_CUDA, "step: MLP forward failed");
+                P.ind_stage = learned ? 3 : 2;  // (combine the learned flags and) limit the flagged cells
+            } else {
+                P.ind_stage = 0;
+            }
+            CK(h, launch(h, K_TROUBLE, P, B));
+        }
+    }
+    if (h->prof) CK(h, cudaEventRecord(h->ev[2], h->st));
+    if (want_mass) {
+        // component totals of the new state (after the event: not part of the kernel times)
+        s = queue_mass(h, h->unew, h->mixed ? h->xub[1 - h->xcur] : nullptr);
+        if (s) return s;
+    }
+    s = read_scalars(h);
+    if (s) return s;
+    if (h->prof) {
+        float t0 = 0.f, t1 = 0.f;
+        CK(h, cudaEventElapsedTime(&t0, h->ev[0], h->ev[1]));
+        CK(h, cudaEventElapsedTime(&t1, h->ev[1], h->ev[2]));
+        h->prof_ms[0] += t0;
+        h->prof_ms[1] += t1;
+        h->prof_n[0] += 1;
+        h->prof_n[1] += 1;
+    }
+    return CRKDG_OK;
+}
+
+// Accept the attempt in h->hs: the new state becomes u^n.
+void accept_attempt(crkdg_t h, double dt, int restarts, crkdg_step_info *info) {
+    if (h->mixed) {
+        h->xcur = 1 - h->xcur;
+    } else {
+        double *t = h->u;
+        h->u = h->unew;
+        h->unew = t;
+    }
+    h->a0 = from_bits(h->hs->a0);
+    h->a0_valid = true;
+    if (info) {
+        info->dt_taken = dt;
+        info->restarts = restarts;
+        info->cells_limited = (long long)h->hs->nlim;
+        info->theta_min = from_bits(h->hs->thmin);
+        info->troubled = (long long)h->hs->ntrb;
+        // relative change of the first component's total over the step
+        const double m0 = h->mass_n[0], m1 = h->hs->mass[0];
+        info->mass_drift = (m1 - m0) / (m0 != 0.0 ? fabs(m0) : 1.0);
+        take_mass(h);
+    } else {
+        h->mass_valid = false;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
 crkdg_status crkdg_step(crkdg_t h, double dt, const crkdg_tableau *tab, crkdg_step_info *info) {
     if (!h) return CRKDG_E_ARG;
     try {
-        crkdg_status s = check_tableau(h, tab);
+        Params P;
+        crkdg_status s = prepare_step(h, dt, tab, info != nullptr, P);
         if (s) return s;
-        if (!(dt > 0.0) || !isfinite(dt)) return fail(h, CRKDG_E_ARG, "step: dt must be finite and > 0");
-        Params P = base_params(h);
-        P.s = tab->s;
-        P.mode = MODE_STEP;
-        const bool ind = h->opt.indicator != CRKDG_IND_OFF;
-        P.defer_limit = ind ? 1 : 0;
-        int ns = 0;
-        for (int i = 0; i < tab->s; ++i) {
-            P.b[i] = tab->b[i];
-            for (int j = 0; j < tab->s; ++j) P.A[i][j] = tab->A[i * tab->s + j];
-            P.slot[i] = tab->b[i] != 0.0 ? ns++ : -1;
-        }
-        P.nslot = ns;
-        s = h->mixed ? ensure_traces_x(h, ns > 0 ? ns : 1) : ensure_traces(h, ns > 0 ? ns : 1);
-        if (s) return s;
-        Bufs B = base_bufs(h);
+        h->pending = false;
         for (int r = 0; r <= h->opt.max_halvings; ++r) {
-            P.dt = dt;
-            B.un = h->u;
-            B.unew = h->unew;
-            s = reset_scalars(h);
+            s = attempt_once(h, P, dt, info != nullptr);
             if (s) return s;
-            if (h->prof) CK(h, cudaEventRecord(h->ev[0], h->st));
-            if (h->mixed) {
-                CK(h, launch_x(h, KX_INNER, P, base_xbufs(h)));
-            } else {
-                CK(h, launch(h, K_INNER, P, B));
-            }
-            if (h->prof) CK(h, cudaEventRecord(h->ev[1], h->st));
-            if (h->mixed) {
-                CK(h, launch_x(h, KX_FINAL, P, base_xbufs(h)));
-                if (ind) {
-                    // the final stage left the unlimited u^{n+1} and its averages (aux); the plain
-                    // decision is taken in the troubled-cell pass, unless features are wanted:
-                    // then the FP64 feature kernel takes it on the merged nodal values
-                    const bool learned = h->opt.indicator == CRKDG_IND_MLP;
-                    if (learned && !h->harvest) {
-                        // features from the split state; the troubled-cell pass takes the plain
-                        // decision itself and combines it with the network's
-                        CK(h, launch_x(h, KX_FEATURES, P, base_xbufs(h)));
-                        if (crkdg_mlp_forward(h->mlp, h->feat, h->ncell, h->prob, h->st) != CRKDG_OK)
-                            return fail(h, CRKDG_E_CUDA, "step: MLP forward failed");
-                        P.ind_stage = 4;
-                    } else if (h->harvest) {
-                        MixBufs Xn = base_xbufs(h);
-                        Xn.ub = h->xub[1 - h->xcur];
-                        Xn.dv = h->xdv[1 - h->xcur];
-                        Xn.nod_out = h->unew;
-                        CK(h, launch_x(h, KX_MERGE, P, Xn));
-                        Bufs Bf = base_bufs(h);
-                        Bf.unew = h->unew;
-                        CK(h, launch(h, K_FEATURES, P, Bf));
-                        if (learned && crkdg_mlp_forward(h->mlp, h->feat, h->ncell, h->prob, h->st) != CRKDG_OK)
-                            return fail(h, CRKDG_E_CUDA, "step: MLP forward failed");
-                        P.ind_stage = learned ? 3 : 2;
-                    } else {
-                        P.ind_stage = 0;
-                    }
-                    CK(h, launch_x(h, KX_TROUBLE, P, base_xbufs(h)));
-                    P.ind_stage = 0;
-                }
-            } else {
-                CK(h, launch(h, K_FINAL, P, B));
-                if (ind) {
-                    const bool learned = h->opt.indicator == CRKDG_IND_MLP;
-                    if (learned || h->harvest) {
-                        // features and the plain decision of the unlimited state in one pass
-                        CK(h, launch(h, K_FEATURES, P, B));
-                        if (learned && crkdg_mlp_forward(h->mlp, h->feat, h->ncell, h->prob, h->st) != CRKDG_OK)
-                            return fail(h, CRKDG_E_CUDA, "step: MLP forward failed");
-                        P.ind_stage = learned ? 3 : 2;  // (combine the learned flags and) limit the flagged cells
-                    } else {
-                        P.ind_stage = 0;
-                    }
-                    CK(h, launch(h, K_TROUBLE, P, B));
-                }
-            }
-            if (h->prof) CK(h, cudaEventRecord(h->ev[2], h->st));
-            s = read_scalars(h);
-            if (s) return s;
-            if (h->prof) {
-                float t0 = 0.f, t1 = 0.f;
-                CK(h, cudaEventElapsedTime(&t0, h->ev[0], h->ev[1]));
-                CK(h, cudaEventElapsedTime(&t1, h->ev[1], h->ev[2]));
-                h->prof_ms[0] += t0;
-                h->prof_ms[1] += t1;
-                h->prof_n[0] += 1;
-                h->prof_n[1] += 1;
-            }
             if (h->hs->flag == 0) {
-                if (h->mixed) {
-                    h->xcur = 1 - h->xcur;
-                } else {
-                    double *t = h->u;
-                    h->u = h->unew;
-                    h->unew = t;
-                }
-                h->a0 = from_bits(h->hs->a0);
-                h->a0_valid = true;
-                if (info) {
-                    info->dt_taken = dt;
-                    info->restarts = r;
-                    info->cells_limited = (long long)h->hs->nlim;
-                    info->theta_min = from_bits(h->hs->thmin);
-                    info->troubled = (long long)h->hs->ntrb;
-                    info->mass_drift = 0.0;
-                }
+                accept_attempt(h, dt, r, info);
                 return CRKDG_OK;
             }
             dt *= 0.5;
@@ -836,6 +912,34 @@ crkdg_status crkdg_step(crkdg_t h, double dt, const crkdg_tableau *tab, crkdg_st
     } catch (...) {
         return CRKDG_E_OOM;
     }
+}
+
+crkdg_status crkdg_step_attempt(crkdg_t h, double dt, const crkdg_tableau *tab, int *violated) {
+    if (!h || !violated) return CRKDG_E_ARG;
+    try {
+        Params P;
+        h->pending = false;
+        crkdg_status s = prepare_step(h, dt, tab, true, P);
+        if (s) return s;
+        s = attempt_once(h, P, dt, true);
+        if (s) return s;
+        *violated = h->hs->flag != 0;
+        h->pending = true;
+        h->pending_dt = dt;
+        return CRKDG_OK;
+    } catch (...) {
+        return CRKDG_E_OOM;
+    }
+}
+
+crkdg_status crkdg_step_accept(crkdg_t h, crkdg_step_info *info) {
+    if (!h) return CRKDG_E_ARG;
+    if (!h->pending) return fail(h, CRKDG_E_ARG, "step_accept: no attempt to accept");
+    if (h->hs->flag != 0) return fail(h, CRKDG_E_ARG, "step_accept: the attempt left the admissible set");
+    h->pending = false;
+    crkdg_step_info tmp;
+    accept_attempt(h, h->pending_dt, 0, info ? info : &tmp);
+    return CRKDG_OK;
 }
 
 // 1D meshes: one persistent cooperative launch runs the whole step loop.
@@ -905,7 +1009,7 @@ crkdg_status crkdg_advance(crkdg_t h, int nsteps, double cfl, double t_end, cons
                            double *t, int *steps_done, int *restarts) {
     if (!h || !t) return CRKDG_E_ARG;
     if (!(cfl > 0.0)) return fail(h, CRKDG_E_ARG, "advance: cfl must be > 0");
-    if (h->dim == 1 && !h->mixed && h->opt.indicator == CRKDG_IND_OFF) {
+    if (h->dim == 1 && !h->mixed && h->opt.indicator == CRKDG_IND_OFF && !h->own_on) {
         try {
             return advance_1d(h, nsteps, cfl, 0.0, t_end, tab, t, steps_done, restarts);
         } catch (...) {
@@ -936,7 +1040,7 @@ crkdg_status crkdg_advance_fixed(crkdg_t h, int nsteps, double dt, double t_end,
                                  double *t, int *steps_done, int *restarts) {
     if (!h || !t) return CRKDG_E_ARG;
     if (!(dt > 0.0) || !isfinite(dt)) return fail(h, CRKDG_E_ARG, "advance_fixed: dt must be finite and > 0");
-    if (h->dim == 1 && !h->mixed && h->opt.indicator == CRKDG_IND_OFF) {
+    if (h->dim == 1 && !h->mixed && h->opt.indicator == CRKDG_IND_OFF && !h->own_on) {
         try {
             return advance_1d(h, nsteps, 0.0, dt, t_end, tab, t, steps_done, restarts);
         } catch (...) {
@@ -1122,6 +1226,117 @@ crkdg_status crkdg_total_mass(crkdg_t h, int comp, double *mass) {
     } catch (...) {
         return CRKDG_E_OOM;
     }
+}
+
+// ---------------------------------------------------------------- subdomains
+
+crkdg_status crkdg_set_subdomain(crkdg_t h, const crkdg_mesh *global, int i0, int i1, int j0, int j1) {
+    if (!h) return CRKDG_E_ARG;
+    if (h->dim == 1) {
+        j0 = 0;
+        j1 = 1;
+    }
+    if (!(0 <= i0 && i0 < i1 && i1 <= h->mesh.nx && 0 <= j0 && j0 < j1 && j1 <= h->mesh.ny))
+        return fail(h, CRKDG_E_ARG, "set_subdomain: need 0 <= i0 < i1 <= nx and 0 <= j0 < j1 <= ny");
+    if (h->opt.indicator != CRKDG_IND_OFF)
+        return fail(h, CRKDG_E_UNSUPPORTED, "set_subdomain: the troubled-cell indicators need a second exchange");
+    double rhx = 0.0, rhy = 0.0;
+    if (global) {
+        if (global->dim != h->dim || global->nx < 1 || (h->dim == 2 && global->ny < 1) ||
+            !(global->x1 > global->x0) || (h->dim == 2 && !(global->y1 > global->y0)))
+            return fail(h, CRKDG_E_ARG, "set_subdomain: bad global mesh");
+        // the global handle's own formula, so that the window's arithmetic is the same bits
+        rhx = 2.0 * global->nx / (global->x1 - global->x0);
+        rhy = h->dim == 2 ? 2.0 * global->ny / (global->y1 - global->y0) : 0.0;
+        const double lx = 2.0 * h->mesh.nx / (h->mesh.x1 - h->mesh.x0);
+        const double ly = h->dim == 2 ? 2.0 * h->mesh.ny / (h->mesh.y1 - h->mesh.y0) : 0.0;
+        if (fabs(lx - rhx) > 1e-9 * rhx || (h->dim == 2 && fabs(ly - rhy) > 1e-9 * rhy))
+            return fail(h, CRKDG_E_ARG, "set_subdomain: the local cells are not the global mesh's cells");
+    }
+    const bool whole = i0 == 0 && i1 == h->mesh.nx && j0 == 0 && j1 == h->mesh.ny;
+    h->own_on = !whole;
+    h->own[0] = i0;
+    h->own[1] = i1;
+    h->own[2] = j0;
+    h->own[3] = j1;
+    h->metric_on = global != nullptr;
+    h->rhx_g = rhx;
+    h->rhy_g = rhy;
+    h->a0_valid = false;
+    h->mass_valid = false;
+    h->pending = false;
+    return CRKDG_OK;
+}
+
+size_t crkdg_cells_bytes(crkdg_t h, long long cells) {
+    if (!h || cells < 0) return 0;
+    if (h->mixed) return (size_t)cells * h->m * (sizeof(double) + h->nn * sizeof(float));
+    return (size_t)cells * h->m * h->nn * sizeof(double);
+}
+
+namespace {
+
+// Copy the cells of the box [i0, i1) x [j0, j1) between the current state u^n and a packed
+// buffer (out: state -> buffer).  One strided copy per component and array.
+crkdg_status copy_cells(crkdg_t h, int i0, int i1, int j0, int j1, void *buf, size_t bytes, int on_device,
+                        bool out) {
+    if (!buf) return fail(h, CRKDG_E_ARG, "pack/unpack: NULL buffer");
+    if (h->dim == 1) {
+        j0 = 0;
+        j1 = 1;
+    }
+    if (!(0 <= i0 && i0 < i1 && i1 <= h->mesh.nx && 0 <= j0 && j0 < j1 && j1 <= h->mesh.ny))
+        return fail(h, CRKDG_E_ARG, "pack/unpack: box outside the mesh");
+    const long long w = i1 - i0, rows = j1 - j0, cells = w * rows;
+    if (bytes != crkdg_cells_bytes(h, cells)) return fail(h, CRKDG_E_ARG, "pack/unpack: wrong byte count");
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice
+                                          : (out ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
+    const size_t nx = (size_t)h->mesh.nx, nc = (size_t)h->ncell, nn = (size_t)h->nn;
+    char *pb = (char *)buf;
+    auto copy2d = [&](char *dev, size_t elem, size_t per_cell, char *packed) -> cudaError_t {
+        // device rows: component plane base + (j0 + r) nx + i0, pitch nx cells
+        char *d0 = dev + ((size_t)j0 * nx + i0) * per_cell * elem;
+        const size_t dpitch = nx * per_cell * elem, width = (size_t)w * per_cell * elem;
+        return out ? cudaMemcpy2DAsync(packed, width, d0, dpitch, width, rows, kind, h->st)
+                   : cudaMemcpy2DAsync(d0, dpitch, packed, width, width, rows, kind, h->st);
+    };
+    if (h->mixed) {
+        double *ub = h->xub[h->xcur];
+        float *dv = h->xdv[h->xcur];
+        for (int c = 0; c < h->m; ++c)
+            CK(h, copy2d((char *)(ub + (size_t)c * nc), sizeof(double), 1, pb + (size_t)c * cells * sizeof(double)));
+        char *pd = pb + (size_t)h->m * cells * sizeof(double);
+        for (int c = 0; c < h->m; ++c)
+            CK(h, copy2d((char *)(dv + (size_t)c * nc * nn), sizeof(float), nn, pd + (size_t)c * cells * nn * sizeof(float)));
+    } else {
+        for (int c = 0; c < h->m; ++c)
+            CK(h, copy2d((char *)(h->u + (size_t)c * nc * nn), sizeof(double), nn,
+                         pb + (size_t)c * cells * nn * sizeof(double)));
+    }
+    if (!on_device) CK(h, cudaStreamSynchronize(h->st));
+    if (!out) {
+        h->pending = false;
+        // cells inside the owned box change what the rate and the totals were taken over
+        const bool hits_own = !h->own_on || !(i1 <= h->own[0] || i0 >= h->own[1] || j1 <= h->own[2] || j0 >= h->own[3]);
+        if (hits_own) {
+            h->a0_valid = false;
+            h->mass_valid = false;
+        }
+    }
+    return CRKDG_OK;
+}
+
+}  // namespace
+
+crkdg_status crkdg_pack_cells(crkdg_t h, int i0, int i1, int j0, int j1, void *buf, size_t bytes, int on_device) {
+    if (!h) return CRKDG_E_ARG;
+    return copy_cells(h, i0, i1, j0, j1, buf, bytes, on_device, true);
+}
+
+crkdg_status crkdg_unpack_cells(crkdg_t h, int i0, int i1, int j0, int j1, const void *buf, size_t bytes,
+                                int on_device) {
+    if (!h) return CRKDG_E_ARG;
+    return copy_cells(h, i0, i1, j0, j1, const_cast<void *>(buf), bytes, on_device, false);
 }
 
 }  // extern "C"

@@ -802,6 +802,7 @@ __device__ __forceinline__ void inner_body(const Params &P, const Bufs &B, int b
     const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
     const int cell = blk * C::NCB + lc;
     const bool active = cell < P.ncell;
+    const bool own = active && owned(P, cell);  // counts in the flag and statistics
     double un[M], cur[M], acc[M], gh[MAXS][M];
     load_node<DIM, N, PHYS>(P, B.un, cell, node, active, un);
 #pragma unroll
@@ -819,7 +820,7 @@ __device__ __forceinline__ void inner_body(const Params &P, const Bufs &B, int b
                 cur[c] = v;
             }
             double pts[C::PPT][M];
-            limit_block(P, B, S, lc, node, active, cur, pts, true, true, false);
+            limit_block(P, B, S, lc, node, own, cur, pts, true, true, false);
         }
         double trs[FPT][M];
         const bool keep_faces = P.slot[i] >= 0 && B.tfs != nullptr;
@@ -877,6 +878,7 @@ __device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int b
     const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
     const int cell = blk * C::NCB + lc;
     const bool active = cell < P.ncell;
+    const bool own = active && owned(P, cell);  // counts in the flag, statistics and rate
     const int a = node % N, b = DIM == 2 ? node / N : 0;
     double u[M];
     load_node<DIM, N, PHYS>(P, B.ustar, cell, node, active, u);
@@ -1006,18 +1008,18 @@ __device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int b
             if (active) B.aux[(size_t)cell * M + c] = s;
         });
         __syncthreads();
-        if (node == 0 && active && !admissible<PHYS, DIM>(P, S.avg[lc])) atomicOr(B.flag, 1);
+        if (node == 0 && own && !admissible<PHYS, DIM>(P, S.avg[lc])) atomicOr(B.flag, 1);
         store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
         return;
     }
     double pts[C::PPT][M];
-    limit_block(P, B, S, lc, node, active, u, pts, true, true);
+    limit_block(P, B, S, lc, node, own, u, pts, true, true);
     // wave-speed rate of the new state over its S_K points (next trial step)
     double amax = 0.0;
 #pragma unroll
     for (int j = 0; j < C::PPT; ++j) {
         int p = node + j * NN;
-        if (p < C::NSK && active) amax = fmax_nonneg(amax, sk_rate<PHYS, DIM>(P, pts[j]));
+        if (p < C::NSK && own) amax = fmax_nonneg(amax, sk_rate<PHYS, DIM>(P, pts[j]));
     }
     unsigned long long abits = dbits(amax);  // non-negative: the bits order as the values
 #pragma unroll
@@ -1042,16 +1044,17 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_limit(Params P, Bufs 
     const int lc = threadIdx.x / C::NN, node = threadIdx.x - lc * C::NN;
     const int cell = blockIdx.x * C::NCB + lc;
     const bool active = cell < P.ncell;
+    const bool own = active && owned(P, cell);
     const bool rate = P.mode == MODE_RATE;
     double u[C::M], pts[C::PPT][C::M];
     load_node<DIM, N, PHYS>(P, B.un, cell, node, active, u);
-    limit_block(P, B, S, lc, node, active, u, pts, false, false, rate);
+    limit_block(P, B, S, lc, node, own, u, pts, false, false, rate);
     if (rate) {
         double amax = 0.0;
 #pragma unroll
         for (int j = 0; j < C::PPT; ++j) {
             int p = node + j * C::NN;
-            if (p < C::NSK && active) amax = fmax(amax, sk_rate<PHYS, DIM>(P, pts[j]));
+            if (p < C::NSK && own) amax = fmax(amax, sk_rate<PHYS, DIM>(P, pts[j]));
         }
         unsigned long long abits = dbits(amax);  // non-negative: the bits order as the values
 #pragma unroll
@@ -1070,6 +1073,7 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_scan(Params P, Bufs B
     const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
     const int cell = blockIdx.x * C::NCB + lc;
     const bool active = cell < P.ncell;
+    const bool own = active && owned(P, cell);
     double u[M];
     load_node<DIM, N, PHYS>(P, B.un, cell, node, active, u);
 #pragma unroll
@@ -1080,7 +1084,7 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_scan(Params P, Bufs B
 #pragma unroll
     for (int j = 0; j < C::PPT; ++j) {
         int p = node + j * NN;
-        if (p < C::NSK && active) {
+        if (p < C::NSK && own) {
             double v[M];
             sk_eval<DIM, N, M, NN>(S.u[lc], p, v);
             amax = fmax(amax, sk_rate<PHYS, DIM>(P, v));

@@ -715,6 +715,7 @@ __global__ void __launch_bounds__(C::NT, split_min_blocks<C>()) k_inner_x(Params
     const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
     const int cell = blockIdx.x * C::NCB + lc;
     const bool active = cell < P.ncell;
+    const bool own = active && owned(P, cell);  // counts in the flag, statistics and rate
     const Bufs B = scal_of<C>(X);
     init_kappa<C>(P, S);
     constexpr int CPT = (M + NN - 1) / NN;  // components owned by a component thread
@@ -765,7 +766,7 @@ __global__ void __launch_bounds__(C::NT, split_min_blocks<C>()) k_inner_x(Params
             }
             __syncthreads();
             float pts[C::PPT][M];
-            limit_x(P, B, S, lc, node, active, S.ubd[lc], dvc, true, true, pts);
+            limit_x(P, B, S, lc, node, own, S.ubd[lc], dvc, true, true, pts);
         }
         float trs[FPT][M];
         eval_G_x(P, S, lc, node, dvc, gd[i], trs);
@@ -812,6 +813,7 @@ __global__ void __launch_bounds__(C::NT, split_final_min_blocks<C>()) k_final_x(
     const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
     const int cell = blockIdx.x * C::NCB + lc;
     const bool active = cell < P.ncell;
+    const bool own = active && owned(P, cell);  // counts in the flag, statistics and rate
     const int a = node % N, b = DIM == 2 ? node / N : 0;
     const Bufs B = scal_of<C>(X);
     init_kappa<C>(P, S);
@@ -966,7 +968,7 @@ __global__ void __launch_bounds__(C::NT, split_final_min_blocks<C>()) k_final_x(
     for (int c = 0; c < M; ++c) dvn[c] = fmaf(fdt, corr[c] - S.mean[lc][c], dvs[c]);
     if (P.defer_limit) {  // the troubled-cell kernel limits; the averages' admissibility is tested here,
                           // the new averages also go to aux for the indicator
-        if (node == 0 && active && !screen_ok<PHYS, DIM>(P, S.ubf[lc], S.ubf[lc]) && !admissible<PHYS, DIM>(P, S.ubd[lc]))
+        if (node == 0 && own && !screen_ok<PHYS, DIM>(P, S.ubf[lc], S.ubf[lc]) && !admissible<PHYS, DIM>(P, S.ubd[lc]))
             atomicOr(B.flag, 1);
         if (active) {
             for (int c = node; c < M; c += NN) {
@@ -979,7 +981,7 @@ __global__ void __launch_bounds__(C::NT, split_final_min_blocks<C>()) k_final_x(
         return;
     }
     float pts[C::PPT][M];
-    limit_x(P, B, S, lc, node, active, S.ubd[lc], dvn, true, true, pts);
+    limit_x(P, B, S, lc, node, own, S.ubd[lc], dvn, true, true, pts);
     double ubn[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) ubn[c] = S.ubd[lc][c];
@@ -987,7 +989,7 @@ __global__ void __launch_bounds__(C::NT, split_final_min_blocks<C>()) k_final_x(
 #pragma unroll
     for (int j = 0; j < C::PPT; ++j) {
         int p = node + j * NN;
-        if (p < C::NSK && active) {
+        if (p < C::NSK && own) {
             float r = speed_dir_f<PHYS, DIM>(P, pts[j], 0) * (0.5f * rhx);
             if constexpr (DIM == 2) r = fmaf(speed_dir_f<PHYS, DIM>(P, pts[j], 1), 0.5f * rhy, r);
             amax = fmaxf(amax, r);
@@ -1235,6 +1237,7 @@ __global__ void __launch_bounds__(C::NT) k_limit_x(Params P, MixBufs X) {
     const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
     const int cell = blockIdx.x * C::NCB + lc;
     const bool active = cell < P.ncell;
+    const bool own = active && owned(P, cell);  // counts in the flag, statistics and rate
     const Bufs B = scal_of<C>(X);
     double ub[M];
     float dv[M], pts[C::PPT][M];
@@ -1244,7 +1247,7 @@ __global__ void __launch_bounds__(C::NT) k_limit_x(Params P, MixBufs X) {
         S.ubf[lc][c] = (float)ub[c];
     }
     __syncthreads();
-    limit_x(P, B, S, lc, node, active, S.ubd[lc], dv, false, false, pts);
+    limit_x(P, B, S, lc, node, own, S.ubd[lc], dv, false, false, pts);
     if (active)
 #pragma unroll
         for (int c = 0; c < M; ++c) X.dv_n[((size_t)c * P.ncell + cell) * NN + node] = dv[c];
@@ -1258,6 +1261,7 @@ __global__ void __launch_bounds__(C::NT) k_scan_x(Params P, MixBufs X) {
     const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
     const int cell = blockIdx.x * C::NCB + lc;
     const bool active = cell < P.ncell;
+    const bool own = active && owned(P, cell);  // counts in the flag, statistics and rate
     double ub[M];
     float dv[M];
     load_x<C>(P, X, cell, node, active, ub, dv);
@@ -1270,7 +1274,7 @@ __global__ void __launch_bounds__(C::NT) k_scan_x(Params P, MixBufs X) {
 #pragma unroll
     for (int j = 0; j < C::PPT; ++j) {
         int p = node + j * NN;
-        if (p < C::NSK && active) {
+        if (p < C::NSK && own) {
             double v[M];
             float v32[M];
             if (margins) {

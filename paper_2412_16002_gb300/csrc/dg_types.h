@@ -97,7 +97,20 @@ struct Params {
                       // probabilities, then limit; 4 (split path) decide, combine with the
                       // learned probabilities, then limit
     ParamsF f;        // split-precision kernels only
+    // Owned box of a subdomain (domain decomposition): cells [own[0], own[1]) x [own[2], own[3])
+    // of this mesh.  With own_on, only those cells count in the admissibility flag, the limiter
+    // statistics, the trial-step rate and the bound margins; the other cells (the halo ring)
+    // are still computed, so that the owned cells' final stage reads their traces.
+    int own_on;
+    int own[4];
 };
+
+// Cells outside the owned box are halo cells (never when own_on is 0).
+__host__ __device__ __forceinline__ bool owned(const Params &P, int cell) {
+    if (!P.own_on) return true;
+    const int cy = cell / P.nx, cx = cell - cy * P.nx;
+    return cx >= P.own[0] && cx < P.own[1] && cy >= P.own[2] && cy < P.own[3];
+}
 
 // The TVB thresholds from rhx, rhy and tvb_M (host side, once per parameter set).
 inline void tvb_thresholds(Params &P) {

@@ -38,6 +38,15 @@ def _is_torch(x):
     return type(x).__module__.startswith("torch")
 
 
+def _buf(b):
+    """(address, bytes, on_device) of a contiguous byte buffer (torch tensor or numpy array)."""
+    if _is_torch(b):
+        assert b.is_contiguous()
+        return b.data_ptr(), b.numel() * b.element_size(), 1 if b.is_cuda else 0
+    assert b.flags.c_contiguous
+    return b.ctypes.data, b.nbytes, 0
+
+
 class Solver:
     """A cRKDG problem on the GPU.
 
@@ -133,8 +142,48 @@ class Solver:
     def step(self, dt, tableau="heun3"):
         info = L.StepInfo()
         self._chk(self.lib.crkdg_step(self.h, dt, C.byref(self._tab(tableau).c), C.byref(info)))
+        return self._info(info)
+
+    @staticmethod
+    def _info(info):
         return {"dt_taken": info.dt_taken, "restarts": info.restarts, "cells_limited": info.cells_limited,
                 "theta_min": info.theta_min, "troubled": info.troubled, "mass_drift": info.mass_drift}
+
+    def step_attempt(self, dt, tableau="heun3"):
+        """One attempt from u^n (no restart); True if a stage's averages left B."""
+        v = C.c_int()
+        self._chk(self.lib.crkdg_step_attempt(self.h, dt, C.byref(self._tab(tableau).c), C.byref(v)))
+        return bool(v.value)
+
+    def step_accept(self):
+        info = L.StepInfo()
+        self._chk(self.lib.crkdg_step_accept(self.h, C.byref(info)))
+        return self._info(info)
+
+    # ---- subdomains ----------------------------------------------------------
+    def set_subdomain(self, box, global_mesh=None):
+        """Owned cells box = (i0, i1, j0, j1) of this mesh; global_mesh: dict(dim, nx, ny,
+        domain) of the undecomposed mesh whose cell sizes this window takes."""
+        gm = None
+        if global_mesh is not None:
+            gm = L.Mesh()
+            gm.dim, gm.nx, gm.ny = global_mesh["dim"], global_mesh["nx"], global_mesh.get("ny", 1)
+            dom = tuple(global_mesh["domain"]) + (0.0, 1.0)
+            gm.x0, gm.x1, gm.y0, gm.y1 = dom[:4]
+        self._chk(self.lib.crkdg_set_subdomain(self.h, C.byref(gm) if gm is not None else None, *box))
+
+    def cells_bytes(self, cells):
+        return int(self.lib.crkdg_cells_bytes(self.h, cells))
+
+    def pack_cells(self, box, buf):
+        """Copy the cells of box (i0, i1, j0, j1) of u^n into buf (a uint8 torch tensor on the
+        device, or a numpy uint8 array / pinned CPU tensor on the host)."""
+        ptr, nbytes, dev = _buf(buf)
+        self._chk(self.lib.crkdg_pack_cells(self.h, *box, C.c_void_p(ptr), nbytes, dev))
+
+    def unpack_cells(self, box, buf):
+        ptr, nbytes, dev = _buf(buf)
+        self._chk(self.lib.crkdg_unpack_cells(self.h, *box, C.c_void_p(ptr), nbytes, dev))
 
     def advance(self, nsteps, cfl, t_end, tableau="heun3", t=0.0):
         tt = C.c_double(t)
