@@ -276,6 +276,15 @@ crkdg_status crkdg_set_barrier_test(crkdg_t h, int extra);
  * same); only the time does. */
 crkdg_status crkdg_set_run1d_chunk(crkdg_t h, int cells);
 
+/* Split precision (CRKDG_PREC_MIXED), 2D Euler, k = 3: the inner stages run on the
+ * tensor cores (tcgen05.mma kind::tf32 with the three-product split, FP32-level
+ * accuracy) for tableaux whose A has only a sub-diagonal (eq. cRKDG2-4); on = 0
+ * runs them on the CUDA cores instead (both keep FP64 where the split path does;
+ * they differ by FP32 rounding).  On by default; other cases always use the CUDA
+ * cores.  A wait for the tensor cores that runs out (1 s) makes crkdg_step return
+ * CRKDG_E_TIMEOUT with the state at u^n. */
+crkdg_status crkdg_set_tensor_cores(crkdg_t h, int on);
+
 /* Number of doubles of the state. */
 size_t crkdg_state_size(crkdg_t h);
 

@@ -96,6 +96,7 @@ SYMBOLS = {
     "crkdg_set_profiling": (C.c_int, [_H, C.c_int]),
     "crkdg_set_barrier_test": (C.c_int, [_H, C.c_int]),
     "crkdg_set_run1d_chunk": (C.c_int, [_H, C.c_int]),
+    "crkdg_set_tensor_cores": (C.c_int, [_H, C.c_int]),
     "crkdg_kernel_times": (C.c_int, [_H, _dp, C.POINTER(C.c_longlong)]),
     "crkdg_state_size": (C.c_size_t, [_H]),
     "crkdg_step_attempt": (C.c_int, [_H, C.c_double, C.POINTER(Tableau), C.POINTER(C.c_int)]),

@@ -227,6 +227,7 @@ struct crkdg_ctx {
     int own[4] = {0, 0, 0, 0};
     bool metric_on = false;       // cell sizes taken from the global mesh of a subdomain
     double rhx_g = 0.0, rhy_g = 0.0;
+    bool tc_on = true;            // split path: inner stages on the tensor cores where built
     double *mass_part = nullptr;  // block sums of the component totals
     double mass_n[MAXM] = {};     // component totals of u^n (valid when mass_valid)
     bool mass_valid = false;
@@ -358,10 +359,21 @@ void fill_f32(Params &P) {
     F.dt = (float)P.dt;
 }
 
+// The tensor-core inner stages serve 2D Euler Q^3 steps whose tableau has only a
+// sub-diagonal (every tableau of the paper); other cases run k_inner_x.
+bool use_tc(const crkdg_ctx *h, const Params &P) {
+    if (!h->tc_on || h->dim != 2 || h->phys != PH_EULER || h->n != 4 || P.mode != MODE_STEP) return false;
+    for (int i = 0; i < P.s; ++i)
+        for (int j = 0; j + 1 < i; ++j)
+            if (P.A[i][j] != 0.0) return false;
+    return true;
+}
+
 cudaError_t launch_x(crkdg_ctx *h, int kernel, const Params &P0, const MixBufs &X) {
     if ((kernel == KX_INNER || kernel == KX_FINAL) && !slots_ok(P0, X.tr, X.tavg)) return cudaErrorInvalidValue;
     Params P = P0;
     fill_f32(P);
+    if (kernel == KX_INNER && use_tc(h, P)) return crkdg_launch_inner_tc(h->st, P, X);
     int ncb = cells_per_block(h->dim, h->n);
     int nblocks = (h->ncell + ncb - 1) / ncb;
     if (h->dim == 1) return crkdg_launch_mx_1d(kernel, h->n, h->phys, nblocks, h->st, P, X);
@@ -647,6 +659,12 @@ crkdg_status crkdg_set_profiling(crkdg_t h, int on) {
     return CRKDG_OK;
 }
 
+crkdg_status crkdg_set_tensor_cores(crkdg_t h, int on) {
+    if (!h) return CRKDG_E_ARG;
+    h->tc_on = on != 0;
+    return CRKDG_OK;
+}
+
 crkdg_status crkdg_set_run1d_chunk(crkdg_t h, int cells) {
     if (!h || cells < 0 || cells > 30) return CRKDG_E_ARG;
     h->run1d_chunk = cells;
@@ -850,6 +868,7 @@ crkdg_status attempt_once(crkdg_t h, Params &P, double dt, bool want_mass) {
     }
     s = read_scalars(h);
     if (s) return s;
+    if (h->hs->flag & 2) return fail(h, CRKDG_E_TIMEOUT, "step: a wait for the tensor cores ran out");
     if (h->prof) {
         float t0 = 0.f, t1 = 0.f;
         CK(h, cudaEventElapsedTime(&t0, h->ev[0], h->ev[1]));

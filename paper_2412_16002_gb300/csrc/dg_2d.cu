@@ -1,6 +1,7 @@
 // dg_2d.cu -- 2D instantiations of the FP64 cRKDG kernels (see dg_core.cuh).
 #include "dg_core.cuh"
 #include "dg_mixed.cuh"
+#include "dg_tc.cuh"
 
 using namespace crkdg;
 
@@ -16,4 +17,8 @@ cudaError_t crkdg_launch_2d(int kernel, int n, int phys, int nblocks, cudaStream
 cudaError_t crkdg_launch_mx_2d(int kernel, int n, int phys, int nblocks, cudaStream_t st, const Params &P,
                                const MixBufs &X) {
     return launch_dim_x<2>(kernel, n, phys, nblocks, st, P, X);
+}
+
+cudaError_t crkdg_launch_inner_tc(cudaStream_t st, const Params &P, const MixBufs &X) {
+    return launch_inner_tc(st, P, X);
 }

@@ -450,9 +450,13 @@ __device__ __forceinline__ bool screen_ok(const Params &P, const float *v, const
             dkin += 2.0f * fabsf(v[d]) * tiny_rel * (fabsf(v[d]) + fabsf(vb[d]));
         }
         float de = tiny_rel * (fabsf(v[DIM + 1]) + fabsf(vb[DIM + 1]));
-        float hk = 0.5f * kin / v[0];
+        // correctly rounded reciprocals instead of three quotients: one more rounding of
+        // 2^-24 in hk, far inside the 2^-18 allowance below; the error terms are bounds
+        // whose own rounding does not matter at this size
+        const float inv = __frcp_rn(v[0]), invd = __frcp_rn(v[0] - dr);
+        float hk = 0.5f * kin * inv;
         float re = v[DIM + 1] - hk;
-        float dre = de + 0.5f * dkin / (v[0] - dr) + hk * dr / (v[0] - dr) + re_rel * (fabsf(v[DIM + 1]) + hk);
+        float dre = de + (0.5f * dkin + hk * dr) * invd + re_rel * (fabsf(v[DIM + 1]) + hk);
         return re - dre >= epsf;
     } else {
         float mr = tiny_rel * (fabsf(v[0]) + fabsf(vb[0]));

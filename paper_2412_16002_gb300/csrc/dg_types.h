@@ -289,6 +289,9 @@ int crkdg_ens_occupancy(int kind, int n);
 int crkdg_ens_cells_per_block(int kind, int n);
 // which: 0 open a step (arg: size class or -1), 1 clear the counters, 2 close an attempt (arg: max_halvings)
 cudaError_t crkdg_ens_control(int which, cudaStream_t st, crkdg::EnsProblem *E, int np, crkdg::EnsCtl *ctl, int arg);
+// Inner stages of the split-precision path on the tensor cores (2D Euler, n = 4, MODE_STEP,
+// tableaux whose A has only a sub-diagonal; defined in dg_2d.cu).
+cudaError_t crkdg_launch_inner_tc(cudaStream_t st, const crkdg::Params &P, const crkdg::MixBufs &X);
 // Closed-form nodal tables for n = 2, 3, 4 (defined in crkdg_api.cu).
 void crkdg_build_tables(crkdg::NodalTables *tab);
 // Persistent 1D step loop (cooperative launch); chunk: own cells per block chunk (0: fill

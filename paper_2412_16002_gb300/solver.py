@@ -160,6 +160,9 @@ class Solver:
         self._chk(self.lib.crkdg_step_accept(self.h, C.byref(info)))
         return self._info(info)
 
+    def set_tensor_cores(self, on):
+        self._chk(self.lib.crkdg_set_tensor_cores(self.h, 1 if on else 0))
+
     # ---- subdomains ----------------------------------------------------------
     def set_subdomain(self, box, global_mesh=None):
         """Owned cells box = (i0, i1, j0, j1) of this mesh; global_mesh: dict(dim, nx, ny,

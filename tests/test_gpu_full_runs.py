@@ -1,0 +1,189 @@
+"""Full-length runs of the configurations to their end times on the GPU, with the invariants
+recorded at every step: the smallest S_K bound margin (>= 0), the conservation drift of the
+step, the restarts, and at the end the error against the FP64 oracle (1D, where the oracle
+finishes a full run in minutes) or against the FP64 GPU path (2D).  Each run takes minutes,
+so they are skipped unless CRKDG_FULL_RUNS=1; with CRKDG_RECORD_DIR set, each writes a JSON
+record there.
+
+Sec. 4.1's adaptive algorithm with the paper's end times: Burgers (workload 1) through its
+shock to t = 1.5, the 1D blast tube to t = 6, the Sedov-type blast (Example 4.7) to t = 1,
+the four-quadrant Riemann problem with the learned indicator to t = 0.2.
+"""
+import json
+import math
+import os
+import time
+
+import numpy as np
+import pytest
+
+from oracle import HEUN3, RK4, Oracle
+from paper_2412_16002_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+
+LONG = os.environ.get("CRKDG_FULL_RUNS") == "1"
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not LONG, reason="full-length runs: set CRKDG_FULL_RUNS=1")]
+TABS = {"heun3": HEUN3, "rk4": RK4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_16002_gb300 import build
+
+    build()
+
+
+def _record(rec):
+    d = os.environ.get("CRKDG_RECORD_DIR")
+    if d:
+        os.makedirs(d, exist_ok=True)
+        with open(os.path.join(d, "full_runs.jsonl"), "a") as f:
+            f.write(json.dumps(rec) + "\n")
+    print(json.dumps(rec))
+
+
+def _run_gpu(g, wl, t_end, closed):
+    """Steps of the trial-step rule clipped to t_end; per-step margins, drift, restarts."""
+    t, steps, restarts = 0.0, 0, 0
+    min_margin, max_drift, limited = math.inf, 0.0, 0
+    troubled = 0
+    t0 = time.perf_counter()
+    while t < t_end * (1.0 - 1e-14):
+        dt = min(g.max_dt(wl.cfl), t_end - t)
+        info = g.step(dt, wl.tableau)
+        t += info["dt_taken"]
+        steps += 1
+        restarts += info["restarts"]
+        limited += info["cells_limited"]
+        troubled += info["troubled"]
+        m = g.margins().min()
+        assert m >= 0.0, (steps, m)
+        min_margin = min(min_margin, m)
+        if closed:
+            assert abs(info["mass_drift"]) < 1e-13, (steps, info["mass_drift"])
+        max_drift = max(max_drift, abs(info["mass_drift"]))
+    return dict(t=t, steps=steps, restarts=restarts, min_margin=min_margin, max_abs_drift=max_drift,
+                cells_limited=limited, troubled=troubled, seconds=time.perf_counter() - t0)
+
+
+def _run_oracle(wl, t_end):
+    o = Oracle(wl.dim, wl.nx, wl.ny, wl.k, wl.domain, wl.flux, gamma=wl.gamma, velocity=wl.velocity,
+               bounds=wl.bounds, eps=wl.eps, bc=wl.bc, bc_state=wl.bc_state)
+    o.set_state(wl.state)
+    t, steps, restarts = o.run(t_end, wl.cfl, TABS[wl.tableau])
+    return o, dict(t=t, steps=steps, restarts=restarts)
+
+
+def _rel(a, b, m):
+    a, b = np.asarray(a).reshape(m, -1), np.asarray(b).reshape(m, -1)
+    linf = max(np.abs(a[c] - b[c]).max() / np.abs(b[c]).max() for c in range(m))
+    l1 = max(np.abs(a[c] - b[c]).sum() / np.abs(b[c]).sum() for c in range(m))
+    return linf, l1
+
+
+def _burgers_entropy(xs, t):
+    """Cell-centre values of the entropy solution of u0 = 0.5 + sin(pi x) on [0, 2] periodic
+    after the shock forms: characteristics on each side of the shock at x = 1 + 0.5 t (the
+    symmetry of u0 about its mean keeps the shock at the foot xi = 1)."""
+    xsh = 1.0 + 0.5 * t
+    out = []
+    for x in xs:
+        a, b = (-1.0, 1.0) if x < xsh else (1.0, 3.0)
+        g = lambda xi: xi + (0.5 + math.sin(math.pi * xi)) * t - x
+        for _ in range(80):
+            mid = 0.5 * (a + b)
+            a, b = (a, mid) if g(mid) > 0 else (mid, b)
+        out.append(0.5 + math.sin(math.pi * 0.5 * (a + b)))
+    return np.array(out)
+
+
+def test_burgers_to_t15_through_the_shock():
+    from paper_2412_16002_gb300.solver import Solver
+
+    wl = inputs.burgers_sine(200, 2)
+    g = Solver.from_workload(wl)
+    g.set_state(wl.state)
+    rec = _run_gpu(g, wl, 1.5, closed=True)
+    o, orec = _run_oracle(wl, 1.5)
+    assert rec["steps"] == orec["steps"] and rec["restarts"] == orec["restarts"] == 0
+    linf, l1 = _rel(g.get_state(), o.get_state(), 1)
+    xs = (np.arange(200) + 0.5) * 0.01
+    avg = np.asarray(g.averages()).reshape(200, -1)[:, 0]
+    l1_exact = float(np.mean(np.abs(avg - _burgers_entropy(xs, 1.5))) * 2.0)
+    rec.update(config="burgers_sine_200_p2", precision="fp64", t_end=1.5, oracle_steps=orec["steps"],
+               rel_linf_vs_oracle=linf, rel_l1_vs_oracle=l1, l1_vs_entropy_solution=l1_exact)
+    _record(rec)
+    assert linf < 1e-10
+    assert l1_exact < 0.02
+
+
+def test_blast_tube_to_t6():
+    """15034 steps to t = 6: the step count and restarts equal the oracle's, bounds and mass
+    hold every step.  The final states agree to the flow's own conditioning: the oracle run
+    against itself from initial data perturbed by 1e-16 (relative) ends 7.5e-5 apart in
+    relative L1 and 2.5e-3 in relative L-inf (momentum, at the shock and contact); the bounds
+    below are a few times that envelope."""
+    from paper_2412_16002_gb300.solver import Solver
+
+    wl = inputs.euler_blast_tube(4096, 2)
+    g = Solver.from_workload(wl)
+    g.set_state(wl.state)
+    rec = _run_gpu(g, wl, 6.0, closed=True)
+    o, orec = _run_oracle(wl, 6.0)
+    linf, l1 = _rel(g.get_state(), o.get_state(), 3)
+    rec.update(config="euler1d_blast_tube_4096_p2", precision="fp64", t_end=6.0, oracle_steps=orec["steps"],
+               oracle_restarts=orec["restarts"], rel_linf_vs_oracle=linf, rel_l1_vs_oracle=l1)
+    _record(rec)
+    assert rec["steps"] == orec["steps"] and rec["restarts"] == orec["restarts"]
+    assert l1 < 5e-4 and linf < 2e-2
+
+
+def _sedov_run(n, precision):
+    from paper_2412_16002_gb300.solver import Solver
+
+    wl = inputs.sedov(n, 3)
+    g = Solver.from_workload(wl, precision=precision)
+    g.set_state(torch.from_numpy(wl.state).cuda())
+    # the blast stays inside [0, 1.1]^2 up to t = 1: the outflow sides carry no mass, the walls
+    # none either, so every step conserves to round-off
+    rec = _run_gpu(g, wl, 1.0, closed=True)
+    return g, wl, rec
+
+
+@pytest.mark.parametrize("n", [1024, 2048])
+def test_sedov_to_t1_split_precision_against_fp64(n):
+    g, wl, rec = _sedov_run(n, "mixed")
+    avg = g.averages()
+    rec.update(config=f"sedov_{n}_q3", precision="mixed", t_end=1.0)
+    if n == 1024:
+        g64, _, rec64 = _sedov_run(n, "fp64")
+        ref = g64.averages()
+        rec.update(fp64_steps=rec64["steps"], fp64_restarts=rec64["restarts"], fp64_seconds=rec64["seconds"],
+                   fp64_min_margin=rec64["min_margin"], fp64_max_abs_drift=rec64["max_abs_drift"])
+        d = np.abs(avg[..., 0] - ref[..., 0]).sum() / np.abs(ref[..., 0]).sum()
+        rec["density_rel_l1_vs_fp64"] = float(d)
+    r = np.hypot(*np.meshgrid((np.arange(n) + 0.5) * 1.1 / n, (np.arange(n) + 0.5) * 1.1 / n, indexing="xy"))
+    rho = avg[..., 0]
+    rec["shock_radius"] = float(r[rho == rho.max()].mean())
+    rec["rho_max"] = float(rho.max())
+    _record(rec)
+    if n == 1024:
+        assert rec["density_rel_l1_vs_fp64"] < 5e-2
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_riemann_1024_learned_indicator_to_t02(precision):
+    import bench
+    from paper_2412_16002_gb300.solver import Solver
+
+    wl = inputs.riemann_quadrants(0, 1024, 2)
+    theta, train = bench.trained_indicator()
+    g = Solver.from_workload(wl, precision=precision, indicator="mlp")
+    g.set_mlp(theta)
+    g.set_state(torch.from_numpy(wl.state).cuda())
+    rec = _run_gpu(g, wl, 0.2, closed=False)
+    rec.update(config="riemann_1024_q2_mlp", precision=precision, t_end=0.2, training=train)
+    _record(rec)
