@@ -192,6 +192,8 @@ void orc_set_options(orc_problem *P, int limiter_on, int max_halvings) {
     P->max_halvings = max_halvings;
 }
 
+void orc_set_scheme(orc_problem *P, int standard) { P->standard = standard ? 1 : 0; }
+
 void orc_set_indicator(orc_problem *P, int on, double tvb_M) {
     P->indicator = on;
     P->tvb_M = tvb_M;
@@ -807,13 +809,13 @@ static int attempt_step(const orc_problem *P, const double *cn, double dt, int s
     memcpy(ut, cn, sizeof(double) * N); /* stage 1: u^(1) = u^n, already limited */
     if (u_stage) { memcpy(u_stage, cn, sizeof(double) * N); memcpy(ut_stage, cn, sizeof(double) * N); }
     for (int i = 1; i < s && !fail; ++i) {
-        /* u^(i) = u^n + dt sum_{j<i} a_ij G(ut^(j)) */
+        /* u^(i) = u^n + dt sum_{j<i} a_ij G(ut^(j)); the standard RKDG (eq. rkdg) takes F */
         memcpy(u, cn, sizeof(double) * N);
         for (int j = 0; j < i; ++j) {
             double a = A[i * s + j];
             if (a == 0.0) continue;
             if (!have_g[j]) {
-                orc_apply(P, ORC_OP_G, ut + N * j, Gs + N * j, t + cst[j] * dt);
+                orc_apply(P, P->standard ? ORC_OP_F : ORC_OP_G, ut + N * j, Gs + N * j, t + cst[j] * dt);
                 have_g[j] = 1;
             }
             for (size_t q = 0; q < N; ++q) u[q] += dt * a * Gs[N * j + q];

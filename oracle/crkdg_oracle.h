@@ -44,6 +44,7 @@ typedef struct orc_problem {
     double bc_state[4][ORC_MAXM];
     int limiter_on;          /* 1: scaling limiter after every stage */
     int indicator;           /* 1: TVB troubled-cell indicator + minmod shock limiter after the final stage */
+    int standard;            /* 1: standard RKDG (eq. rkdg): F in the inner stages as well */
     double tvb_M;            /* TVB constant of the indicator */
     int max_halvings;
     orc_exact_fn exact;
@@ -71,6 +72,9 @@ orc_problem *orc_create(int dim, int nx, int ny, int k, double x0, double x1, do
 void orc_destroy(orc_problem *P);
 void orc_set_exact(orc_problem *P, orc_exact_fn fn, void *ctx);
 void orc_set_options(orc_problem *P, int limiter_on, int max_halvings);
+/* scheme: 0 the compact RKDG (Scheme 1L: G in the inner stages, F in the final one), 1 the
+ * standard RKDG in Butcher form (eq. rkdg: F in every stage), with the same limiter */
+void orc_set_scheme(orc_problem *P, int standard);
 size_t orc_state_size(const orc_problem *P); /* doubles: ncell*m*n^dim */
 
 /* nodal (Gauss points, layout [m][ny][nx][n_y][n_x]) <-> modal */

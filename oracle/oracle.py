@@ -79,6 +79,7 @@ def _load():
     lib.orc_destroy.argtypes = [V]
     lib.orc_set_exact.argtypes = [V, _EXACT_FN, V]
     lib.orc_set_options.argtypes = [V, C.c_int, C.c_int]
+    lib.orc_set_scheme.argtypes = [V, C.c_int]
     lib.orc_state_size.argtypes = [V]
     lib.orc_state_size.restype = C.c_size_t
     lib.orc_nodal_to_modal.argtypes = [V, _dp, _dp]
@@ -154,7 +155,8 @@ class Oracle:
 
     def __init__(self, dim, nx, ny, k, domain, flux, gamma=1.4, velocity=(1.0, 0.0),
                  bounds=(0.0, 1.0), eps=1e-13, bc=("periodic",) * 4, bc_state=None,
-                 exact=None, limiter=True, max_halvings=20, indicator=False, tvb_M=10.0):
+                 exact=None, limiter=True, max_halvings=20, indicator=False, tvb_M=10.0,
+                 scheme="compact"):
         lib = _load()
         self.lib = lib
         x0, x1, y0, y1 = (tuple(domain) + (0.0, 1.0))[:4]
@@ -188,6 +190,7 @@ class Oracle:
             lib.orc_set_exact(self.h, self._exact_c, None)
         lib.orc_set_options(self.h, 1 if limiter else 0, max_halvings)
         lib.orc_set_indicator(self.h, 1 if indicator else 0, tvb_M)
+        lib.orc_set_scheme(self.h, 1 if scheme == "standard" else 0)
         self.c = np.zeros(self.N)
 
     def __del__(self):

@@ -320,3 +320,45 @@ def test_mixed_learned_features_from_the_split_state():
         flagged += ia["troubled"]
     assert flagged > 0
     assert np.array_equal(ga.get_state(), gb.get_state())
+
+
+@pytest.mark.parametrize("name", ["sedov_2048_q3", "riemann_1024_q2"])
+def test_mixed_full_size_sampled_cells(name):
+    """Full-size split-precision step (2048^2 Q^3 RK4 Sedov-type blast, whose inner stages run
+    on the tensor cores; 1024^2 Q^2 Heun-3 Riemann problem), launched as bench.py launches it:
+    sampled cells against the FP64 oracle on their 3x3 patch with the same dt, element by
+    element at the split path's operator tolerance (2e-5 of the component's scale), and the
+    cell averages (updated in FP64 from FP32 face fluxes) to 1e-6."""
+    from test_gpu_parity import _patch_oracle
+
+    from paper_2412_16002_gb300.solver import Solver
+
+    if name.startswith("sedov"):
+        wl = inputs.sedov_shell(2048, 3)
+        r = 0.3 / 1.1 * 2048
+        cells = [(0, 0), (2047, 2047), (0, 1000), (1000, 0), (int(r * 0.7071), int(r * 0.7071)),
+                 (int(r), 3), (3, int(r)), (int(r * 0.6), int(r * 0.8)), (700, 1500), (1200, 200)]
+    else:
+        wl = inputs.riemann_quadrants(3, 1024, 2)
+        cells = [(511, 511), (512, 512), (511, 512), (0, 0), (1023, 1023), (511, 100), (100, 512),
+                 (700, 511), (0, 511), (511, 1023)]
+    g = Solver.from_workload(wl, precision="mixed", stream=torch.cuda.current_stream())
+    g.set_state(torch.from_numpy(wl.state).cuda())
+    dt = g.max_dt(wl.cfl)
+    info = g.step(dt, wl.tableau)
+    assert info["restarts"] == 0
+    assert g.margins().min() >= 0.0
+    out = g.get_state()
+    n = wl.k + 1
+    w = np.polynomial.legendre.leggauss(n)[1] / 2.0
+    W = np.outer(w, w)
+    for cx, cy in cells:
+        o, px, py = _patch_oracle(wl, cx, cy, wl.state)
+        rc, io = o.step(dt, ORACLE_TABS[wl.tableau])
+        assert rc == 0 and io["restarts"] == 0
+        ref = o.get_state()[:, py, px]
+        got = out[:, cy, cx]
+        for c in range(4):
+            scale = max(np.abs(ref[c]).max(), np.abs(wl.state[c]).max() * 1e-3)
+            assert np.abs(got[c] - ref[c]).max() <= 2e-5 * scale, (cx, cy, c)
+            assert abs((W * got[c]).sum() - (W * ref[c]).sum()) <= 1e-6 * scale, (cx, cy, c)

@@ -767,3 +767,80 @@ def test_trial_step_closed_form_scalar_laws(flux, dim):
     expect = cfl / sum(r / h for r, h in zip(radii, hs))
     got = o.max_dt(cfl)
     assert abs(got - expect) <= 1e-14 * expect, (got, expect)
+
+
+# --------------------------------------------------------------------------- standard RKDG (eq. rkdg)
+
+
+def _operator_matrix(o, op):
+    """Columns: the oracle's op applied to each modal unit vector (the operator is linear for
+    linear advection)."""
+    N = o.N
+    Mx = np.zeros((N, N))
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = 1.0
+        Mx[:, j] = o.apply(op, e)
+    return Mx
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+@pytest.mark.parametrize("tab,order", [(MIDPOINT2, 2), (HEUN3, 3), (RK4, 4)])
+def test_standard_rkdg_linear_step_is_taylor_polynomial(dim, tab, order):
+    """eq. (rkdg) with F in every stage is the Runge--Kutta method applied to du/dt = F u.  For
+    linear advection F is a matrix, and an s-stage method of order s <= 4 advances by the
+    degree-s Taylor polynomial of dt F: one oracle step (limiter off) must equal
+    sum_m (dt F)^m u / m!.  The compact scheme differs (its inner stages use G), so the same
+    identity fails for it."""
+    k = 2
+    if dim == 1:
+        o = Oracle(1, 6, 1, k, (0.0, 1.0), "advection", velocity=(0.8, 0.0), bounds=(-1e9, 1e9),
+                   bc=("periodic",) * 4, limiter=False, scheme="standard")
+    else:
+        o = Oracle(2, 4, 3, k, (0.0, 1.0, 0.0, 0.75), "advection", velocity=(0.7, -0.4), bounds=(-1e9, 1e9),
+                   bc=("periodic",) * 4, limiter=False, scheme="standard")
+    F = _operator_matrix(o, "F")
+    rng = np.random.default_rng(5)
+    c0 = rng.standard_normal(o.N)
+    dt = 0.02
+    expect = np.zeros_like(c0)
+    term = c0.copy()
+    for m in range(order + 1):
+        expect += term
+        term = dt * (F @ term) / (m + 1)
+    o.c = c0.copy()
+    rc, info = o.step(dt, tab)
+    assert rc == 0 and info["restarts"] == 0
+    assert np.abs(o.c - expect).max() <= 1e-13 * np.abs(expect).max()
+    # the compact scheme (G in the inner stages) is a different polynomial
+    oc = Oracle(o.dim, o.nx, o.ny, k, (0.0, 1.0) if dim == 1 else (0.0, 1.0, 0.0, 0.75), "advection",
+                velocity=(0.8, 0.0) if dim == 1 else (0.7, -0.4), bounds=(-1e9, 1e9), bc=("periodic",) * 4,
+                limiter=False)
+    oc.c = c0.copy()
+    oc.step(dt, tab)
+    assert np.abs(oc.c - expect).max() > 1e-8 * np.abs(expect).max()
+
+
+def test_standard_rkdg_conservation_and_rate():
+    """Standard RKDG: global conservation on a periodic Euler mesh, and third-order
+    convergence (Q^2, Heun-3) on the smooth exact solution of Example 4.2 scenario II."""
+    U = inputs.random_euler(2, 8, 6, 2, seed=9, osc=0.5)
+    o = Oracle(2, 8, 6, 2, (0.0, 1.0, 0.0, 1.0), "euler", bc=("periodic",) * 4, scheme="standard")
+    o.set_state(U)
+    m0 = [o.total_mass(c) for c in range(4)]
+    t = 0.0
+    for _ in range(10):
+        rc, info = o.step(o.max_dt(0.1), HEUN3, t)
+        assert rc == 0
+        t += info["dt_taken"]
+    for c in range(4):
+        assert abs(o.total_mass(c) - m0[c]) <= 1e-13 * max(1.0, abs(m0[c]))
+    errs = []
+    for n in (8, 16):
+        wl = inputs.scenario2(n, 2)
+        o = Oracle(2, n, n, 2, wl.domain, "euler", bc=("periodic",) * 4, exact=_scenario2, scheme="standard")
+        o.set_state(wl.state)
+        o.run(0.1, 0.1, HEUN3)
+        errs.append(o.l2_error(0.1))
+    rate = math.log(errs[0] / errs[1]) / math.log(2)
+    assert 2.6 < rate < 3.5, (errs, rate)
