@@ -54,6 +54,9 @@ WORKLOADS = {
     "riemann_1024_q2_mixed_tvb": dict(kind="riemann", nx=1024, k=2, precision="mixed", indicator="tvb"),
     "riemann_1024_q2_mixed_mlp": dict(kind="riemann", nx=1024, k=2, precision="mixed", indicator="mlp"),
     "ensemble_64_riemann_mlp": dict(kind="ensemble", count=64, indicator="mlp"),
+    # the standard RKDG (F in every stage), for comparison with the compact scheme
+    "sedov_2048_q3_standard": dict(kind="sedov", nx=2048, k=3, scheme="standard"),
+    "riemann_1024_q2_standard": dict(kind="riemann", nx=1024, k=2, scheme="standard"),
 }
 DEFAULT = "sedov_2048_q3_mixed"
 # timed steps when --steps is not given
@@ -264,7 +267,8 @@ def _oracle_worker(name, warmup, steps, budget_s, nx=None):
     tabs = {"midpoint2": MIDPOINT2, "heun3": HEUN3, "rk4": RK4}
     wl = oracle_sample(name, nx)
     o = Oracle(wl.dim, wl.nx, wl.ny, wl.k, wl.domain, wl.flux, gamma=wl.gamma, velocity=wl.velocity,
-               bounds=wl.bounds, eps=wl.eps, bc=wl.bc, bc_state=wl.bc_state)
+               bounds=wl.bounds, eps=wl.eps, bc=wl.bc, bc_state=wl.bc_state,
+               scheme=WORKLOADS[name].get("scheme", "compact"))
     o.set_state(wl.state)
     t = 0.0
     for _ in range(warmup):
@@ -326,6 +330,7 @@ def cpu_baseline_record(name, budget_s):
 def workload_config(name, wl, world):
     """The config dict both arms print for a workload."""
     return {"workload": name, "precision": WORKLOADS[name].get("precision", "fp64"),
+            "scheme": WORKLOADS[name].get("scheme", "compact"),
             "indicator": WORKLOADS[name].get("indicator", "off"), "cells": wl.cells, "k": wl.k, "m": wl.m,
             "dofs_per_cell": wl.dofs_per_cell, "tableau": wl.tableau, "stages": TAB_S[wl.tableau],
             "cfl": wl.cfl, "initial_state": "the workload's initial data at t = 0",
@@ -516,7 +521,8 @@ def run_gb300(args, wl, name):
     train = None
     if indicator == "mlp":
         theta, train = trained_indicator()
-    g = Solver.from_workload(wl, stream=stream, precision=precision, indicator=indicator)
+    g = Solver.from_workload(wl, stream=stream, precision=precision, indicator=indicator,
+                             scheme=WORKLOADS[name].get("scheme", "compact"))
     if indicator == "mlp":
         g.set_mlp(theta)
     u0 = torch.from_numpy(wl.state).to(dev)
@@ -645,12 +651,12 @@ def run_gb300(args, wl, name):
 
 def trained_indicator(seeds=range(1000, 1004), n=256, steps=800, every=200, epochs=8):
     """The learned indicator's network, trained on the GPU by the library's kernels on about
-    1e6 cells labelled by the plain indicator in seeded 256^2 Q^2 Riemann runs (4 snapshots
-    per run at t ~ 0.05, 0.1, 0.15, 0.2).  Returns (params, summary)."""
+    1e6 cells labelled by the plain indicator in one ensemble run of seeded 256^2 Q^2 Riemann
+    problems (4 snapshots per problem at t ~ 0.05, 0.1, 0.15, 0.2).  Returns (params, summary)."""
     from paper_2412_16002_gb300 import indicator as ind
 
     t0 = time.perf_counter()
-    X, Y = ind.harvest(seeds, n=n, k=2, steps=steps, every=every)
+    X, Y = ind.harvest_ensemble(list(seeds), n=n, k=2, steps=steps, every=every)
     theta, hist = ind.train(X, Y, epochs=epochs)
     conf = ind.confusion(theta, X, Y)
     summary = {"cells": int(Y.numel()), "troubled_fraction": float(Y.mean().item()), "epochs": epochs,

@@ -60,6 +60,7 @@ enum { CRKDG_BC_PERIODIC = 0, CRKDG_BC_OUTFLOW = 1, CRKDG_BC_REFLECT = 2, CRKDG_
 enum { CRKDG_FLUX_ADVECTION = 0, CRKDG_FLUX_BURGERS = 1, CRKDG_FLUX_EULER = 2 };
 enum { CRKDG_PREC_FP64 = 0, CRKDG_PREC_MIXED = 1 };
 enum { CRKDG_IND_OFF = 0, CRKDG_IND_TVB = 1, CRKDG_IND_MLP = 2 };
+enum { CRKDG_SCHEME_COMPACT = 0, CRKDG_SCHEME_STANDARD = 1 };
 
 /* Mesh: the domain [x0,x1] (x [y0,y1] in 2D) cut into nx (x ny) equal cells.
  * bc[s] for the sides s = 0 left, 1 right, 2 bottom, 3 top; a periodic side
@@ -123,6 +124,12 @@ typedef struct {
     int indicator;      /* CRKDG_IND_* troubled-cell indicator (default off) */
     double tvb_M;       /* TVB constant of the plain indicator (default 10) */
     void *cuda_stream;  /* cudaStream_t to issue work on (NULL: default stream) */
+    int scheme;         /* CRKDG_SCHEME_COMPACT (default): the compact scheme above.
+                           CRKDG_SCHEME_STANDARD: the standard RKDG in Butcher form (eq. rkdg,
+                           Sec. 2.1), u^(i) = u~^n + dt sum_{j<i} a_ij F(u~^(j)), i.e. F (with
+                           its neighbour exchange) in every stage, the same scaling limiter
+                           and restart rule; for comparison with the compact scheme.  FP64
+                           precision, no indicator (CRKDG_E_UNSUPPORTED otherwise). */
 } crkdg_options;
 
 typedef struct {
@@ -399,6 +406,15 @@ crkdg_status crkdg_ensemble_step(crkdg_ens_t e, int *active);
 crkdg_status crkdg_ensemble_info(crkdg_ens_t e, int i, crkdg_ens_info *info);
 /* Network of the learned indicator (device pointer, CRKDG_MLP_NPARAM floats). */
 crkdg_status crkdg_ensemble_set_mlp(crkdg_ens_t e, const float *params);
+/* Training data for the learned indicator from ensemble runs (as crkdg_set_harvest for
+ * one handle): while on (indicator on), every step also keeps, per problem, the features
+ * of the unlimited final-stage state on which its plain TVB indicator decided
+ * (crkdg_ensemble_last_features, [ny][nx][44] floats) and, with the TVB indicator,
+ * those decisions (crkdg_ensemble_troubled_flags, one int per cell, the labels).  With
+ * the learned indicator the flags are its combined decisions. */
+crkdg_status crkdg_ensemble_set_harvest(crkdg_ens_t e, int on);
+crkdg_status crkdg_ensemble_last_features(crkdg_ens_t e, int i, float *feat, int on_device);
+crkdg_status crkdg_ensemble_troubled_flags(crkdg_ens_t e, int i, int *flags, int on_device);
 /* Time one attempt (inner and final kernels) per candidate tile size for every
  * (degree, size class) present, reps times each, keep the fastest and rebuild the
  * step graphs.  Problems' states are not changed.  chosen (nullable, 6 ints)

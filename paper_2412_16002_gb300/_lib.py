@@ -17,6 +17,7 @@ BC = {"periodic": 0, "outflow": 1, "reflect": 2, "dirichlet": 3}
 FLUX = {"advection": 0, "burgers": 1, "euler": 2}
 PREC = {"fp64": 0, "mixed": 1}
 INDICATOR = {"off": 0, "tvb": 1, "mlp": 2}
+SCHEME = {"compact": 0, "standard": 1}
 OPS = {"G": 0, "F": 1, "limit": 2}
 
 
@@ -39,7 +40,7 @@ class Tableau(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("max_halvings", C.c_int), ("indicator", C.c_int),
-                ("tvb_M", C.c_double), ("cuda_stream", C.c_void_p)]
+                ("tvb_M", C.c_double), ("cuda_stream", C.c_void_p), ("scheme", C.c_int)]
 
 
 class StepInfo(C.Structure):
@@ -117,6 +118,9 @@ SYMBOLS = {
     "crkdg_ensemble_step": (C.c_int, [_H, C.POINTER(C.c_int)]),
     "crkdg_ensemble_info": (C.c_int, [_H, C.c_int, C.POINTER(EnsInfo)]),
     "crkdg_ensemble_set_mlp": (C.c_int, [_H, C.c_void_p]),
+    "crkdg_ensemble_set_harvest": (C.c_int, [_H, C.c_int]),
+    "crkdg_ensemble_last_features": (C.c_int, [_H, C.c_int, C.c_void_p, C.c_int]),
+    "crkdg_ensemble_troubled_flags": (C.c_int, [_H, C.c_int, C.c_void_p, C.c_int]),
     "crkdg_ensemble_autotune": (C.c_int, [_H, C.c_int, C.POINTER(C.c_int)]),
     "crkdg_ensemble_plan": (C.c_int, [C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.c_int,
                                       C.POINTER(C.c_int), C.c_int]),

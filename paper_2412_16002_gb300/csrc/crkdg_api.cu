@@ -74,12 +74,16 @@ __global__ void k_colsum_part(const double *x, long long cs, long long ms, int c
     }
 }
 
+// One warp per component: lane l adds the block sums l, l + 32, ... in order, then a fixed
+// butterfly combines the lanes (the same order every run).
 __global__ void k_colsum_final(const double *part, int nblk, int m, double *out) {
-    if (threadIdx.x < m) {
-        double v = 0.0;
-        for (int b = 0; b < nblk; ++b) v += part[(size_t)b * m + threadIdx.x];
-        out[threadIdx.x] = v;
-    }
+    const int c = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (c >= m) return;
+    double v = 0.0;
+    for (int b = l; b < nblk; b += 32) v += part[(size_t)b * m + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (l == 0) out[c] = v;
 }
 
 // ---------------------------------------------------------------- nodal tables
@@ -228,6 +232,8 @@ struct crkdg_ctx {
     bool metric_on = false;       // cell sizes taken from the global mesh of a subdomain
     double rhx_g = 0.0, rhy_g = 0.0;
     bool tc_on = true;            // split path: inner stages on the tensor cores where built
+    double *fst = nullptr;        // standard RKDG: F of each stage, then two stage buffers
+    int fst_slots = 0;
     double *mass_part = nullptr;  // block sums of the component totals
     double mass_n[MAXM] = {};     // component totals of u^n (valid when mass_valid)
     bool mass_valid = false;
@@ -391,6 +397,32 @@ crkdg_status read_scalars(crkdg_ctx *h) {
     return CRKDG_OK;
 }
 
+// Stage combination of the standard RKDG (eq. rkdg): out = un + sum_j c_j F_j over the state,
+// the terms added in stage order.
+struct Combo {
+    const double *f[MAXS];
+    double c[MAXS];
+    int nf;
+};
+__global__ void k_combine(const double *__restrict__ un, Combo cb, size_t count, double *__restrict__ out) {
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += (size_t)gridDim.x * blockDim.x) {
+        double v = un[q];
+        for (int j = 0; j < cb.nf; ++j) v = fma(cb.c[j], cb.f[j][q], v);
+        out[q] = v;
+    }
+}
+
+crkdg_status ensure_fstages(crkdg_ctx *h, int s) {
+    const int need = s + 2;
+    if (need <= h->fst_slots) return CRKDG_OK;
+    if (h->fst) cudaFree(h->fst);
+    h->fst = nullptr;
+    h->fst_slots = 0;
+    CK(h, cudaMalloc(&h->fst, (size_t)need * h->nstate * sizeof(double)));
+    h->fst_slots = need;
+    return CRKDG_OK;
+}
+
 // Queue the component totals of a state into scal->mass (read by the next read_scalars).
 // FP64 path: the averages of the nodal state `nodal` (aux is overwritten); split path: the
 // stored FP64 averages `ub` ([m][cell]).
@@ -419,7 +451,7 @@ crkdg_status queue_mass(crkdg_ctx *h, const double *nodal, const double *ub) {
     const int nblk = (count + kSumCells - 1) / kSumCells;
     k_colsum_part<<<nblk, kSumThreads, 0, h->st>>>(x, cs, ms, count, h->mesh.nx, i0, j0, w, h->m, h->mass_part);
     CK(h, cudaGetLastError());
-    k_colsum_final<<<1, 32, 0, h->st>>>(h->mass_part, nblk, h->m, h->scal->mass);
+    k_colsum_final<<<1, 32 * MAXM, 0, h->st>>>(h->mass_part, nblk, h->m, h->scal->mass);
     CK(h, cudaGetLastError());
     return CRKDG_OK;
 }
@@ -507,6 +539,7 @@ void crkdg_options_default(crkdg_options *opt) {
     opt->indicator = CRKDG_IND_OFF;
     opt->tvb_M = 10.0;
     opt->cuda_stream = nullptr;
+    opt->scheme = CRKDG_SCHEME_COMPACT;
 }
 
 crkdg_status crkdg_create(const crkdg_mesh *mesh, int k, int m, const crkdg_flux *flux,
@@ -539,6 +572,9 @@ crkdg_status crkdg_create(const crkdg_mesh *mesh, int k, int m, const crkdg_flux
     if (o.indicator < CRKDG_IND_OFF || o.indicator > CRKDG_IND_MLP || !(o.tvb_M >= 0.0)) return CRKDG_E_ARG;
     if (o.indicator != CRKDG_IND_OFF && flux->kind != CRKDG_FLUX_EULER) return CRKDG_E_UNSUPPORTED;
     if (o.indicator == CRKDG_IND_MLP && mesh->dim != 2) return CRKDG_E_UNSUPPORTED;
+    if (o.scheme != CRKDG_SCHEME_COMPACT && o.scheme != CRKDG_SCHEME_STANDARD) return CRKDG_E_ARG;
+    if (o.scheme == CRKDG_SCHEME_STANDARD && (o.precision != CRKDG_PREC_FP64 || o.indicator != CRKDG_IND_OFF))
+        return CRKDG_E_UNSUPPORTED;
 
     crkdg_ctx *h = new (std::nothrow) crkdg_ctx();
     if (!h) return CRKDG_E_OOM;
@@ -626,6 +662,7 @@ crkdg_status crkdg_destroy(crkdg_t h) {
     cudaFree(h->tr);
     cudaFree(h->aux);
     cudaFree(h->mass_part);
+    cudaFree(h->fst);
     cudaFree(h->scal);
     cudaFreeHost(h->hs);
     cudaFreeHost(h->hinit);
@@ -784,6 +821,10 @@ crkdg_status prepare_step(crkdg_t h, double dt, const crkdg_tableau *tab, bool w
     P.nslot = ns;
     s = h->mixed ? ensure_traces_x(h, ns > 0 ? ns : 1) : ensure_traces(h, ns > 0 ? ns : 1);
     if (s) return s;
+    if (h->opt.scheme == CRKDG_SCHEME_STANDARD) {
+        s = ensure_fstages(h, tab->s);
+        if (s) return s;
+    }
     if (want_mass && !h->mass_valid) {
         s = reset_scalars(h);
         if (s == CRKDG_OK) s = queue_mass(h, h->u, h->mixed ? h->xub[h->xcur] : nullptr);
@@ -794,9 +835,113 @@ crkdg_status prepare_step(crkdg_t h, double dt, const crkdg_tableau *tab, bool w
     return CRKDG_OK;
 }
 
+// F(in) -> out with the operator kernels (the inner kernel's G plus the final kernel's face
+// correction, as crkdg_apply_operator); traces in slot 0.
+crkdg_status apply_F(crkdg_t h, const double *in, double *out) {
+    Params P = base_params(h);
+    P.s = 1;
+    P.dt = 1.0;
+    P.b[0] = 1.0;
+    P.slot[0] = 0;
+    P.nslot = 1;
+    P.mode = MODE_OP_G;
+    Bufs B = base_bufs(h);
+    B.un = in;
+    B.ustar = h->ustar;
+    CK(h, launch(h, K_INNER, P, B));
+    P.mode = MODE_OP_F;
+    B.unew = out;
+    CK(h, launch(h, K_FINAL, P, B));
+    return CRKDG_OK;
+}
+
+crkdg_status combine(crkdg_t h, const double *un, const Combo &cb, double *out) {
+    const size_t n = h->nstate;
+    int grid = (int)((n + 255) / 256);
+    if (grid > 65535) grid = 65535;
+    k_combine<<<grid, 256, 0, h->st>>>(un, cb, n, out);
+    CK(h, cudaGetLastError());
+    return CRKDG_OK;
+}
+
+// One attempt of the standard RKDG (eq. rkdg): every stage value is u^n plus its combination of
+// the previous stages' F (each F with its own neighbour exchange), tested and limited like the
+// compact scheme's stages; the result lands in h->unew.
+crkdg_status attempt_standard(crkdg_t h, const Params &Ps, double dt, bool want_mass) {
+    crkdg_status s = reset_scalars(h);
+    if (s) return s;
+    const int ns = Ps.s;
+    double *F = h->fst, *comb = h->fst + (size_t)ns * h->nstate, *ut = comb + h->nstate;
+    bool need[MAXS] = {};
+    for (int j = 0; j < ns; ++j) {
+        need[j] = Ps.b[j] != 0.0;
+        for (int i = j + 1; i < ns; ++i) need[j] = need[j] || Ps.A[i][j] != 0.0;
+    }
+    if (h->prof) CK(h, cudaEventRecord(h->ev[0], h->st));
+    for (int i = 0; i < ns; ++i) {
+        const double *stage = h->u;  // u~^(1) = u~^n
+        if (i > 0) {
+            Combo cb;
+            memset(&cb, 0, sizeof(cb));
+            for (int j = 0; j < i; ++j)
+                if (Ps.A[i][j] != 0.0) {
+                    cb.f[cb.nf] = F + (size_t)j * h->nstate;
+                    cb.c[cb.nf++] = dt * Ps.A[i][j];
+                }
+            s = combine(h, h->u, cb, comb);
+            if (s) return s;
+            Params P = base_params(h);
+            P.mode = MODE_LIMIT_CHECK;
+            Bufs B = base_bufs(h);
+            B.un = comb;
+            B.unew = ut;
+            CK(h, launch(h, K_LIMIT, P, B));
+            stage = ut;
+        }
+        if (need[i]) {
+            s = apply_F(h, stage, F + (size_t)i * h->nstate);
+            if (s) return s;
+        }
+    }
+    if (h->prof) CK(h, cudaEventRecord(h->ev[1], h->st));
+    Combo cb;
+    memset(&cb, 0, sizeof(cb));
+    for (int i = 0; i < ns; ++i)
+        if (Ps.b[i] != 0.0) {
+            cb.f[cb.nf] = F + (size_t)i * h->nstate;
+            cb.c[cb.nf++] = dt * Ps.b[i];
+        }
+    s = combine(h, h->u, cb, comb);
+    if (s) return s;
+    Params P = base_params(h);
+    P.mode = MODE_LIMIT_FINAL;
+    Bufs B = base_bufs(h);
+    B.un = comb;
+    B.unew = h->unew;
+    CK(h, launch(h, K_LIMIT, P, B));
+    if (h->prof) CK(h, cudaEventRecord(h->ev[2], h->st));
+    if (want_mass) {
+        s = queue_mass(h, h->unew, nullptr);
+        if (s) return s;
+    }
+    s = read_scalars(h);
+    if (s) return s;
+    if (h->prof) {
+        float t0 = 0.f, t1 = 0.f;
+        CK(h, cudaEventElapsedTime(&t0, h->ev[0], h->ev[1]));
+        CK(h, cudaEventElapsedTime(&t1, h->ev[1], h->ev[2]));
+        h->prof_ms[0] += t0;
+        h->prof_ms[1] += t1;
+        h->prof_n[0] += 1;
+        h->prof_n[1] += 1;
+    }
+    return CRKDG_OK;
+}
+
 // One attempt of size dt from u^n into the second state buffer; h->hs holds its flag and
 // statistics afterwards (synchronises the stream).
 crkdg_status attempt_once(crkdg_t h, Params &P, double dt, bool want_mass) {
+    if (h->opt.scheme == CRKDG_SCHEME_STANDARD) return attempt_standard(h, P, dt, want_mass);
     const bool ind = h->opt.indicator != CRKDG_IND_OFF;
     crkdg_status s;
     P.dt = dt;
@@ -1028,7 +1173,8 @@ crkdg_status crkdg_advance(crkdg_t h, int nsteps, double cfl, double t_end, cons
                            double *t, int *steps_done, int *restarts) {
     if (!h || !t) return CRKDG_E_ARG;
     if (!(cfl > 0.0)) return fail(h, CRKDG_E_ARG, "advance: cfl must be > 0");
-    if (h->dim == 1 && !h->mixed && h->opt.indicator == CRKDG_IND_OFF && !h->own_on) {
+    if (h->dim == 1 && !h->mixed && h->opt.indicator == CRKDG_IND_OFF && !h->own_on &&
+        h->opt.scheme == CRKDG_SCHEME_COMPACT) {
         try {
             return advance_1d(h, nsteps, cfl, 0.0, t_end, tab, t, steps_done, restarts);
         } catch (...) {
@@ -1059,7 +1205,8 @@ crkdg_status crkdg_advance_fixed(crkdg_t h, int nsteps, double dt, double t_end,
                                  double *t, int *steps_done, int *restarts) {
     if (!h || !t) return CRKDG_E_ARG;
     if (!(dt > 0.0) || !isfinite(dt)) return fail(h, CRKDG_E_ARG, "advance_fixed: dt must be finite and > 0");
-    if (h->dim == 1 && !h->mixed && h->opt.indicator == CRKDG_IND_OFF && !h->own_on) {
+    if (h->dim == 1 && !h->mixed && h->opt.indicator == CRKDG_IND_OFF && !h->own_on &&
+        h->opt.scheme == CRKDG_SCHEME_COMPACT) {
         try {
             return advance_1d(h, nsteps, 0.0, dt, t_end, tab, t, steps_done, restarts);
         } catch (...) {

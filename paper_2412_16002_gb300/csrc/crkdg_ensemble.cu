@@ -337,7 +337,7 @@ crkdg_status crkdg_ensemble_create(int count, const crkdg_ens_problem *problems,
         crkdg_options_default(&e->opt);
     }
     if (m != 4 || flux->kind != CRKDG_FLUX_EULER || !(flux->gamma > 1.0)) return bail(CRKDG_E_ARG);
-    if (e->opt.precision != CRKDG_PREC_FP64) return bail(CRKDG_E_UNSUPPORTED);
+    if (e->opt.precision != CRKDG_PREC_FP64 || e->opt.scheme != CRKDG_SCHEME_COMPACT) return bail(CRKDG_E_UNSUPPORTED);
     if (e->opt.indicator < CRKDG_IND_OFF || e->opt.indicator > CRKDG_IND_MLP || e->opt.max_halvings < 0)
         return bail(CRKDG_E_ARG);
     if (!(bounds->eps > 0.0)) return bail(CRKDG_E_ARG);
@@ -597,6 +597,38 @@ crkdg_status crkdg_ensemble_set_mlp(crkdg_ens_t e, const float *params) {
     if (!e || !params) return CRKDG_E_ARG;
     if (!e->mlp) return efail(e, CRKDG_E_ARG, "ensemble set_mlp: the indicator is off");
     ECK(e, cudaMemcpyAsync(e->mlp, params, sizeof(float) * CRKDG_MLP_NPARAM, cudaMemcpyDeviceToDevice, e->st));
+    ECK(e, cudaStreamSynchronize(e->st));
+    return CRKDG_OK;
+}
+
+crkdg_status crkdg_ensemble_set_harvest(crkdg_ens_t e, int on) {
+    if (!e) return CRKDG_E_ARG;
+    if (on && (e->opt.indicator == CRKDG_IND_OFF || !e->arena_feat))
+        return efail(e, CRKDG_E_ARG, "ensemble set_harvest: needs an indicator");
+    if (e->harvest != (on != 0)) {
+        e->harvest = on != 0;
+        e->graphs_valid = false;  // the step graph gains (or drops) the feature pass
+    }
+    return CRKDG_OK;
+}
+
+crkdg_status crkdg_ensemble_last_features(crkdg_ens_t e, int i, float *feat, int on_device) {
+    if (!e || !feat || i < 0 || i >= e->np) return CRKDG_E_ARG;
+    if (!e->arena_feat) return efail(e, CRKDG_E_ARG, "ensemble last_features: the indicator is off");
+    const EnsProblem &p = e->hprob[i];
+    const size_t n = (size_t)p.P.ncell * CRKDG_MLP_NIN;
+    ECK(e, cudaMemcpyAsync(feat, p.feat, n * sizeof(float), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           e->st));
+    ECK(e, cudaStreamSynchronize(e->st));
+    return CRKDG_OK;
+}
+
+crkdg_status crkdg_ensemble_troubled_flags(crkdg_ens_t e, int i, int *flags, int on_device) {
+    if (!e || !flags || i < 0 || i >= e->np) return CRKDG_E_ARG;
+    if (!e->arena_flags) return efail(e, CRKDG_E_ARG, "ensemble troubled_flags: the indicator is off");
+    const EnsProblem &p = e->hprob[i];
+    ECK(e, cudaMemcpyAsync(flags, p.tflags, (size_t)p.P.ncell * sizeof(int),
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, e->st));
     ECK(e, cudaStreamSynchronize(e->st));
     return CRKDG_OK;
 }

@@ -1045,10 +1045,11 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_limit(Params P, Bufs 
     const int cell = blockIdx.x * C::NCB + lc;
     const bool active = cell < P.ncell;
     const bool own = active && owned(P, cell);
-    const bool rate = P.mode == MODE_RATE;
+    const bool rate = P.mode == MODE_RATE || P.mode == MODE_LIMIT_FINAL;
+    const bool check = P.mode == MODE_LIMIT_CHECK || P.mode == MODE_LIMIT_FINAL;  // standard RKDG stages
     double u[C::M], pts[C::PPT][C::M];
     load_node<DIM, N, PHYS>(P, B.un, cell, node, active, u);
-    limit_block(P, B, S, lc, node, own, u, pts, false, false, rate);
+    limit_block(P, B, S, lc, node, own, u, pts, check, check, rate);
     if (rate) {
         double amax = 0.0;
 #pragma unroll

@@ -90,6 +90,37 @@ __device__ __forceinline__ float speed_dir_f(const Params &P, const float *u, in
     }
 }
 
+// Normal flux and the spectral radius |w . nu| + c of one state together (the final stage
+// needs both at every face point): one reciprocal and one pressure per state.
+template <int PHYS, int DIM>
+__device__ __forceinline__ float flux_speed_dir_f(const Params &P, const float *u, int dir, float *f) {
+    if constexpr (PHYS != PH_EULER) {
+        flux_dir_f<PHYS, DIM>(P, u, dir, f);
+        return speed_dir_f<PHYS, DIM>(P, u, dir);
+    } else {
+        const float ri = 1.0f / u[0];
+        float p;
+        if constexpr (DIM == 1) {
+            const float w = u[1] * ri;
+            p = P.f.gm1 * (u[2] - 0.5f * u[1] * w);
+            f[0] = u[1];
+            f[1] = u[1] * w + p;
+            f[2] = (u[2] + p) * w;
+        } else {
+            const float wx = u[1] * ri, wy = u[2] * ri;
+            p = P.f.gm1 * (u[3] - 0.5f * (u[1] * wx + u[2] * wy));
+            const float wd = dir == 0 ? wx : wy;
+            f[0] = u[1 + dir];
+            f[1] = u[1] * wd + (dir == 0 ? p : 0.0f);
+            f[2] = u[2] * wd + (dir == 1 ? p : 0.0f);
+            f[3] = (u[3] + p) * wd;
+        }
+        const float c2 = P.f.gamma * p * ri;
+        const float c = c2 > 0.0f ? sqrtf(c2) : 0.0f;
+        return fabsf(u[1 + dir] * ri) + c;
+    }
+}
+
 template <int PHYS, int DIM>
 __device__ __forceinline__ void boundary_state_f(const Params &P, int side, const float *ui, float *ue) {
     constexpr int M = ncomp(PHYS, DIM);
@@ -117,6 +148,39 @@ __device__ __forceinline__ void exterior_state_f(const Params &P, int side, cons
         for (int c = 0; c < M; ++c) ue[c] = avg[c];
     } else {
         boundary_state_f<PHYS, DIM>(P, side, ui, ue);
+    }
+}
+
+// Near vacuum an FP32 density formed as ubar_f + d (ubar_f the FP32 average, d the point's
+// deviation) may have lost its sign or most of its digits to rounding; 1 / rho then gives
+// an infinite or meaningless velocity.  True when rho is not above 2^-20 (|ubar_f| + |d|),
+// beyond which its relative error is below 2^-3: the caller then evaluates that point's
+// density (or the whole point) in FP64 from ubar + (double)d.
+__device__ __forceinline__ bool rho_ill(float rho, float ubf0, float d0) {
+    return !(rho > 9.5367431640625e-07f * (fabsf(ubf0) + fabsf(d0)));
+}
+
+// Euler fluxes at a point whose FP32 density is ill-conditioned: the FP64 state ub + (double)d
+// (d the FP32 deviations), the FP64 flux, rounded to FP32.  Out of line: it is rare, and the
+// kernels that call it are bound by instruction fetch.
+template <int DIM>
+__device__ __noinline__ void flux_xy_fallback(const Params &P, const double *ub, const float *d, float *fx,
+                                                 float *fy) {
+    constexpr int M = DIM + 2;
+    double u[M], gx[M], gy[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) u[c] = ub[c] + (double)d[c];
+    if constexpr (DIM == 2) {
+        flux_xy<PH_EULER>(P, u, gx, gy);
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            fx[c] = (float)gx[c];
+            fy[c] = (float)gy[c];
+        }
+    } else {
+        flux_dir<PH_EULER, DIM>(P, u, 0, gx);
+#pragma unroll
+        for (int c = 0; c < M; ++c) fx[c] = (float)gx[c];
     }
 }
 
@@ -321,7 +385,11 @@ __device__ void eval_G_x(const Params &P, SmemX<C> &S, int lc, int node, const f
         float u[M], fx[M], fy[M];
 #pragma unroll
         for (int c = 0; c < M; ++c) u[c] = S.ubf[lc][c] + dv[c];
-        if constexpr (DIM == 2) {
+        bool ill = false;
+        if constexpr (PHYS == PH_EULER) ill = rho_ill(u[0], S.ubf[lc][0], dv[0]);
+        if (ill) {  // near vacuum: this node's flux in FP64
+            if constexpr (PHYS == PH_EULER) flux_xy_fallback<DIM>(P, S.ubd[lc], dv, fx, fy);
+        } else if constexpr (DIM == 2) {
             flux_xy_f<PHYS>(P, u, fx, fy);
         } else {
             flux_dir_f<PHYS, DIM>(P, u, 0, fx);
@@ -393,6 +461,14 @@ __device__ void eval_G_x(const Params &P, SmemX<C> &S, int lc, int node, const f
                     for (int q = 0; q < N; ++q) s = fmaf(l[q], S.u[c][lc][q * N + pos], s);
                 }
                 trs[j][c] = s;
+            }
+            if constexpr (PHYS == PH_EULER) {
+                // in a step the stage values are limited and a face point is an S_K point, so
+                // its density is >= eps; near vacuum the FP32 interpolation of the node values
+                // can lose that to rounding: keep it at least the FP32 value of eps.  (Operator
+                // evaluations take unlimited data, whose traces keep their own sign.)
+                if (P.mode == MODE_STEP && rho_ill(trs[j][0], S.ubf[lc][0], trs[j][0] - S.ubf[lc][0]))
+                    trs[j][0] = fmaxf(trs[j][0], P.scr_eps);
             }
             float f[M];
             flux_dir_f<PHYS, DIM>(P, trs[j], face >> 1, f);
@@ -659,6 +735,24 @@ __device__ void limit_x(const Params &P, const Bufs &B, SmemX<C> &S, int lc, int
         atomicAdd(B.nlim, 1ull);
         atomicMin(B.thmin, dbits(tr > 0.0 ? tr : 0.0));
     }
+    if constexpr (PHYS == PH_EULER) {
+        // cells the screen could not clear are near the bounds: the S_K values handed back
+        // (the callers' trial-step rate) are the rounded FP64 evaluation, whose density is
+        // >= eps, not the FP32 sum, which near vacuum can be ~0 and make 1 / rho blow up
+        if (cell_unsafe) {
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                int p = node + j * NN;
+                if (p < NSK) {
+                    double v[M];
+                    float v32[M];
+                    eval64_x(S, lc, p, ub, v, v32);
+#pragma unroll
+                    for (int c = 0; c < M; ++c) pts[j][c] = (float)v[c];
+                }
+            }
+        }
+    }
 }
 
 // ----------------------------------------------------------------------------- kernels
@@ -819,6 +913,9 @@ __global__ void __launch_bounds__(C::NT, split_final_min_blocks<C>()) k_final_x(
     const bool active = cell < P.ncell;
     const bool own = active && owned(P, cell);  // counts in the flag, statistics and rate
     const int a = node % N, b = DIM == 2 ? node / N : 0;
+    // one face point per thread, NF a power of two, whole cells per warp: the NF points of a face
+    // are NF consecutive lanes (2D, Q^3)
+    constexpr bool kFaceLanes = NTR == NN && (NF & (NF - 1)) == 0 && NF > 1 && 32 % NN == 0;
     const Bufs B = scal_of<C>(X);
     init_kappa<C>(P, S);
     double ub0[M];
@@ -838,7 +935,8 @@ __global__ void __launch_bounds__(C::NT, split_final_min_blocks<C>()) k_final_x(
         if (P.slot[i] < 0) continue;
         const float *tr = X.tr + (size_t)P.slot[i] * M * P.ncell * NTR;
         const float bi = P.f.b[i];
-        float uL[FPT][M], uR[FPT][M];
+        // per face point: the interior and exterior normal fluxes and the jump u_R - u_L
+        float fin[FPT][M], fex[FPT][M], du[FPT][M], sp[FPT];
 #pragma unroll
         for (int j = 0; j < FPT; ++j) {
             int fp = node + j * NN;
@@ -858,42 +956,58 @@ __global__ void __launch_bounds__(C::NT, split_final_min_blocks<C>()) k_final_x(
                     for (int c = 0; c < M; ++c) av[c] = X.tavg[((size_t)P.slot[i] * M + c) * P.ncell + cell];
                     exterior_state_f<PHYS, DIM>(P, face, ui, av, ue);
                 }
-                bool upper = face & 1;
+                const bool upper = face & 1;  // the interior state is u_L on an upper face
+                const int dir = face >> 1;
 #pragma unroll
-                for (int c = 0; c < M; ++c) {
-                    uL[j][c] = upper ? ui[c] : ue[c];
-                    uR[j][c] = upper ? ue[c] : ui[c];
-                }
-                int dir = face >> 1;
-                S.al[lc][fp] = fmaxf(speed_dir_f<PHYS, DIM>(P, uL[j], dir), speed_dir_f<PHYS, DIM>(P, uR[j], dir));
-            } else if (fp < NTR) {
-                S.al[lc][fp] = 0.0f;
+                for (int c = 0; c < M; ++c) du[j][c] = upper ? ue[c] - ui[c] : ui[c] - ue[c];
+                const float si = flux_speed_dir_f<PHYS, DIM>(P, ui, dir, fin[j]);
+                const float se = flux_speed_dir_f<PHYS, DIM>(P, ue, dir, fex[j]);
+                sp[j] = fmaxf(0.0f, fmaxf(si, se));
+            } else {
+                sp[j] = 0.0f;
             }
         }
-        __syncthreads();
+        // alpha of each face: the largest radius over its points
+        float alf[FPT];
+        if constexpr (kFaceLanes) {  // a face's points sit on NF consecutive lanes: no barrier
+#pragma unroll
+            for (int j = 0; j < FPT; ++j) {
+                alf[j] = sp[j];
+#pragma unroll
+                for (int o = 1; o < NF; o <<= 1) alf[j] = fmaxf(alf[j], __shfl_xor_sync(0xffffffffu, alf[j], o));
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < FPT; ++j) {
+                const int fp = node + j * NN;
+                if (fp < NTR) S.al[lc][fp] = sp[j];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < FPT; ++j) {
+                const int fp = node + j * NN;
+                alf[j] = 0.0f;
+                if (fp < NTR) {
+                    const int face = fp / NF;
+#pragma unroll
+                    for (int q = 0; q < NF; ++q) alf[j] = fmaxf(alf[j], S.al[lc][face * NF + q]);
+                }
+            }
+        }
 #pragma unroll
         for (int j = 0; j < FPT; ++j) {
             int fp = node + j * NN;
             if (fp < NTR && active) {
-                int face = fp / NF;
-                int dir = face >> 1;
-                float alpha = 0.0f;
-#pragma unroll
-                for (int q = 0; q < NF; ++q) alpha = fmaxf(alpha, S.al[lc][face * NF + q]);
-                float fL[M], fR[M];
-                flux_dir_f<PHYS, DIM>(P, uL[j], dir, fL);
-                flux_dir_f<PHYS, DIM>(P, uR[j], dir, fR);
-                bool upper = face & 1;
+                const float alpha = alf[j];
 #pragma unroll
                 for (int c = 0; c < M; ++c) {
-                    float fhat = 0.5f * (fL[c] + fR[c]) - 0.5f * alpha * (uR[j][c] - uL[j][c]);
-                    float fint = upper ? fL[c] : fR[c];
-                    dcf[j][c] = fmaf(bi, fhat - fint, dcf[j][c]);
+                    float fhat = 0.5f * (fin[j][c] + fex[j][c]) - 0.5f * alpha * du[j][c];
+                    dcf[j][c] = fmaf(bi, fhat - fin[j][c], dcf[j][c]);
                     fhs[j][c] = fmaf(bi, fhat, fhs[j][c]);
                 }
             }
         }
-        __syncthreads();
+        if constexpr (!kFaceLanes) __syncthreads();  // S.al is rewritten by the next stage
     }
 #pragma unroll
     for (int j = 0; j < FPT; ++j) {
@@ -1289,6 +1403,13 @@ __global__ void __launch_bounds__(C::NT) k_scan_x(Params P, MixBufs X) {
                                                  C::NCB * C::NN, p, s);
 #pragma unroll
                 for (int c = 0; c < M; ++c) v32[c] = S.ubf[lc][c] + (s[c] - S.mean[lc][c]);
+            }
+            if constexpr (PHYS == PH_EULER) {
+                if (rho_ill(v32[0], S.ubf[lc][0], v32[0] - S.ubf[lc][0])) {  // near vacuum: FP64
+                    if (!margins) eval64_x(S, lc, p, ub, v, v32);
+#pragma unroll
+                    for (int c = 0; c < M; ++c) v32[c] = (float)v[c];
+                }
             }
             float r = speed_dir_f<PHYS, DIM>(P, v32, 0) * (0.5f * rhx);
             if constexpr (DIM == 2) r = fmaf(speed_dir_f<PHYS, DIM>(P, v32, 1), 0.5f * rhy, r);

@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(tc::NT, 1) k_inner_tc(Params P, MixBufs X) {
                     // FP64 theta for the cells the screen could not clear
                     double mn = INFINITY;
                     if (unsafe) {
-#pragma unroll 1
+#pragma unroll
                         for (int j = 0; j < QS; ++j) {
                             const double v0 = ubd[0] + (double)(sk[0][j] - mean[0]);
                             mn = (v0 == v0) ? fmin(mn, v0) : -INFINITY;
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(tc::NT, 1) k_inner_tc(Params P, MixBufs X) {
                     if (th1 < 1.0) th1 *= kMargin;
                     double mre = INFINITY;
                     if (unsafe) {
-#pragma unroll 1
+#pragma unroll
                         for (int j = 0; j < QS; ++j) {
                             double v[M];
 #pragma unroll
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(tc::NT, 1) k_inner_tc(Params P, MixBufs X) {
                         s1 = limited ? (float)tfin : 1.0f;
                         int viol = 0;
                         if (limited) {
-#pragma unroll 1
+#pragma unroll
                             for (int j = 0; j < QS; ++j) {
                                 double v[M];
 #pragma unroll
@@ -510,9 +510,14 @@ __global__ void __launch_bounds__(tc::NT, 1) k_inner_tc(Params P, MixBufs X) {
                 }
             }
 #pragma unroll
-            for (int c = 0; c < M; ++c)
+            for (int q = 0; q < QN; ++q) {
+                const float d0 = tr[0][q];  // the density deviation at the face point
 #pragma unroll
-                for (int q = 0; q < QN; ++q) tr[c][q] += ubf[c];
+                for (int c = 0; c < M; ++c) tr[c][q] += ubf[c];
+                // face points are S_K points (density >= eps in the FP64 evaluation after
+                // limiting): near vacuum take the density rounded from FP64, not the FP32 sum
+                if (rho_ill(tr[0][q], ubf[0], d0)) tr[0][q] = (float)(S.ubd[0][lc] + (double)d0);
+            }
             // traced stages: traces and averages for the final stage
             if (P.slot[i] >= 0 && active) {
 #pragma unroll
@@ -531,6 +536,9 @@ __global__ void __launch_bounds__(tc::NT, 1) k_inner_tc(Params P, MixBufs X) {
                     float u[M], gx[M], gy[M];
 #pragma unroll
                     for (int c = 0; c < M; ++c) u[c] = ubf[c] + dvc[c][q];
+                    // near vacuum: the density rounded from its FP64 value (its sign and digits
+                    // right, so 1 / rho is that of the FP64 evaluation), as for the traces
+                    if (rho_ill(u[0], ubf[0], dvc[0][q])) u[0] = (float)(S.ubd[0][lc] + (double)dvc[0][q]);
                     flux_xy_f<PHYS>(P, u, gx, gy);
 #pragma unroll
                     for (int c = 0; c < M; ++c) {

@@ -22,6 +22,8 @@ enum Mode {
     MODE_OP_G = 1,   // inner kernel writes G(u) instead of the stage accumulation
     MODE_OP_F = 2,   // final kernel adds the face correction only (no limiter, no checks)
     MODE_RATE = 3,   // scan kernels: the trial-step rate only (no bound margins)
+    MODE_LIMIT_CHECK = 4,  // limiter kernel: also test the averages and count limited cells
+    MODE_LIMIT_FINAL = 5,  // as MODE_LIMIT_CHECK, and post the trial-step rate of the result
 };
 
 __host__ __device__ constexpr int ncomp(int phys, int dim) { return phys == PH_EULER ? dim + 2 : 1; }

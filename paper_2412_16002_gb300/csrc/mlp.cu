@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(TM, 1) k_mlp_forward_tc(const float *__restric
                                                           float *__restrict__ prob) {
     extern __shared__ __align__(1024) unsigned char smt[];
     __shared__ float sb1[NH], sb2[NH], sw3[NH];
-    __shared__ __align__(8) unsigned long long s_mbar, s_xbar;
+    __shared__ __align__(8) unsigned long long s_mbar, s_mbar2, s_xbar;
     __shared__ uint32_t s_tmem;
     __shared__ int s_fault;
     const int t = threadIdx.x, warp = t >> 5;
@@ -197,12 +197,13 @@ __global__ void __launch_bounds__(TM, 1) k_mlp_forward_tc(const float *__restric
         sw3[t] = theta[OW3 + t];
     }
     const float b3 = theta[OB3];
-    const uint32_t mbar = smem_addr(&s_mbar), xbar = smem_addr(&s_xbar);
+    const uint32_t mbar = smem_addr(&s_mbar), mbar2 = smem_addr(&s_mbar2), xbar = smem_addr(&s_xbar);
     const uint32_t a_stage = smem_addr(smt + OFF_XS);
     const int ntiles = (n + TM - 1) / TM;
     auto tile_rows = [&](int tl) { return n - tl * TM < TM ? n - tl * TM : TM; };
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar2) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(xbar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fault = 0;
@@ -226,24 +227,24 @@ __global__ void __launch_bounds__(TM, 1) k_mlp_forward_tc(const float *__restric
     const uint32_t a_w1[2] = {smem_addr(smt + OFF_W1H), smem_addr(smt + OFF_W1L)};
     const uint32_t a_w2[2] = {smem_addr(smt + OFF_W2H), smem_addr(smt + OFF_W2L)};
     constexpr uint32_t LBO_A = (TM / 8) * 128, LBO_B = (NH / 8) * 128, SBO = 128;
-    uint32_t phase = 0, xphase = 0;
+    uint32_t phase1 = 0, phase2 = 0, xphase = 0;
     bool inflight = (int)blockIdx.x < ntiles;  // a bulk copy this thread has not seen complete
 
+    // Software pipeline over the CTA's tiles: the next tile's layer-1 MMAs are issued right
+    // after this tile's layer-2 MMAs, so they run while the threads wait for layer 2 and
+    // form this tile's outputs.  Layer 1 accumulates in columns [0, NH), layer 2 in
+    // [NH, 2 NH); mbar (layer 1) and s_mbar2 (layer 2) complete each tile's groups.
     float x[NIN];
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int r = tile * TM + t;
-        // this tile's features, staged by the bulk copy
+    // stage tile `tl`'s features (staged by the bulk copy) into the layer-1 A tile and issue
+    // its MMAs, then the copy of the tile after it; false if the copy's wait ran out
+    auto start_tile = [&](int tl) -> bool {
         const bool okx = wait_mma(xbar, xphase);
         if (okx) {  // otherwise the copy may still land: drained below at the same phase
             xphase ^= 1u;
             inflight = false;
         }
-        if (__syncthreads_or(!okx)) {
-            if (t == 0) s_fault = 1;
-            break;
-        }
-        stage_row(smt + OFF_XS, tile_rows(tile), t, x);
-        // layer-1 A tile: this cell's features, split
+        if (__syncthreads_or(!okx)) return false;
+        stage_row(smt + OFF_XS, tile_rows(tl), t, x);
 #pragma unroll
         for (int k = 0; k < K1; ++k) {
             float hi = 0.0f, lo = 0.0f;
@@ -265,15 +266,25 @@ __global__ void __launch_bounds__(TM, 1) k_mlp_forward_tc(const float *__restric
             }
             mma_commit(mbar);
         }
-        // the next tile's features while the tensor cores work (every thread has read
-        // the staging buffer and fenced the async proxy before the barrier above)
-        const int nxt = tile + gridDim.x;
+        // the copy of the tile after it (every thread has read the staging buffer and fenced
+        // the async proxy before the barrier above)
+        const int nxt = tl + gridDim.x;
         if (nxt < ntiles) {
             if (t == 0) bulk_load(a_stage, X + (size_t)nxt * TM * NIN, (uint32_t)(tile_rows(nxt) * NIN * 4), xbar);
             inflight = true;
         }
-        bool ok = wait_mma(mbar, phase);
-        phase ^= 1u;
+        return true;
+    };
+
+    bool go = (int)blockIdx.x < ntiles;
+    if (go && !start_tile(blockIdx.x)) {
+        if (t == 0) s_fault = 1;
+        go = false;
+    }
+    for (int tile = blockIdx.x; go && tile < ntiles; tile += gridDim.x) {
+        const int r = tile * TM + t;
+        bool ok = wait_mma(mbar, phase1);
+        phase1 ^= 1u;
         tc_after_sync();
         // layer 1 epilogue: bias, ReLU, split into the layer-2 A tile
         if (ok) {
@@ -306,10 +317,17 @@ __global__ void __launch_bounds__(TM, 1) k_mlp_forward_tc(const float *__restric
                 mma_tf32(tmem + NH, smem_desc(a_h[0] + oa, LBO_A, SBO), smem_desc(a_w2[1] + ob, LBO_B, SBO), 1);
                 mma_tf32(tmem + NH, smem_desc(a_h[1] + oa, LBO_A, SBO), smem_desc(a_w2[0] + ob, LBO_B, SBO), 1);
             }
-            mma_commit(mbar);
+            mma_commit(mbar2);
         }
-        ok = wait_mma(mbar, phase);
-        phase ^= 1u;
+        // the next tile's layer 1 while layer 2 of this one runs (its A tile is free: this
+        // tile's layer-1 MMAs completed above)
+        const int nxt = tile + gridDim.x;
+        if (nxt < ntiles && !start_tile(nxt)) {
+            if (t == 0) s_fault = 1;
+            break;
+        }
+        ok = wait_mma(mbar2, phase2);
+        phase2 ^= 1u;
         tc_after_sync();
         // layer 2 epilogue and the output unit
         float z = b3;

@@ -106,6 +106,21 @@ class Ensemble:
         assert _is_torch(params) and params.is_cuda and params.element_size() == 4 and params.numel() == 7105
         self._chk(self.lib.crkdg_ensemble_set_mlp(self.e, C.c_void_p(params.data_ptr())))
 
+    def set_harvest(self, on=True):
+        self._chk(self.lib.crkdg_ensemble_set_harvest(self.e, 1 if on else 0))
+
+    def last_features(self, i, out):
+        """Problem i's features of the last step ([cells, 44] float32 CUDA tensor `out`)."""
+        assert _is_torch(out) and out.is_cuda and out.element_size() == 4 and out.is_contiguous()
+        self._chk(self.lib.crkdg_ensemble_last_features(self.e, i, C.c_void_p(out.data_ptr()), 1))
+        return out
+
+    def troubled_flags(self, i, out):
+        """Problem i's troubled-cell flags of the last step ([cells] int32 CUDA tensor `out`)."""
+        assert _is_torch(out) and out.is_cuda and out.element_size() == 4 and out.is_contiguous()
+        self._chk(self.lib.crkdg_ensemble_troubled_flags(self.e, i, C.c_void_p(out.data_ptr()), 1))
+        return out
+
     def set_profiling(self, on=True):
         self._chk(self.lib.crkdg_ensemble_set_profiling(self.e, 1 if on else 0))
 

@@ -69,6 +69,38 @@ def harvest(seeds, n=256, k=2, steps=60, every=4, tvb_M=10.0, cfl=None, device="
     return torch.cat(X), torch.cat(Y)
 
 
+def harvest_ensemble(seeds, n=256, k=2, steps=60, every=4, tvb_M=10.0, device="cuda"):
+    """As harvest, from one ensemble run of the seeded Riemann problems (all n x n, degree k,
+    plain TVB indicator, each problem at its own trial step): every `every`-th of `steps`
+    ensemble steps contributes every cell of every problem.  The ensemble reproduces each
+    problem's single-handle run bit for bit, so the labelled set is the same as harvest's."""
+    import torch
+
+    from .ensemble import Ensemble, riemann_problem
+
+    probs = [riemann_problem(s, n, k) for s in seeds]
+    for p in probs:
+        p["t_end"] = 1e30
+    ens = Ensemble(probs, indicator="tvb", tvb_M=tvb_M)
+    for i, s in enumerate(seeds):
+        ens.set_state(i, inputs.riemann_quadrants(s, n, k).state)
+    ens.set_harvest(True)
+    per_problem = [[] for _ in seeds]
+    flags = torch.empty(n * n, dtype=torch.int32, device=device)
+    for s in range(steps):
+        ens.step()
+        if (s + 1) % every == 0:
+            for i in range(len(seeds)):
+                feat = torch.empty((n * n, NIN), dtype=torch.float32, device=device)
+                ens.last_features(i, feat)
+                ens.troubled_flags(i, flags)
+                per_problem[i].append((feat, flags.to(torch.float32)))
+    ens.close()
+    X = [f for rows in per_problem for f, _ in rows]  # problem by problem, as harvest orders them
+    Y = [y for rows in per_problem for _, y in rows]
+    return torch.cat(X), torch.cat(Y)
+
+
 def loss_and_grad(lib, theta, X, Y, grad=None, loss=None):
     import torch
 

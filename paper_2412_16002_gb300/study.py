@@ -169,7 +169,7 @@ def main():
     build()
     torch.cuda.init()
     t0 = time.perf_counter()
-    X, Y = ind.harvest(range(1000, 1004), n=256, k=2, steps=800, every=200, tvb_M=args.tvb_M)
+    X, Y = ind.harvest_ensemble(list(range(1000, 1004)), n=256, k=2, steps=800, every=200, tvb_M=args.tvb_M)
     theta, hist = ind.train(X, Y, epochs=8)
     conf = ind.confusion(theta, X, Y)
     train = {"cells": int(Y.numel()), "loss": hist[-1], "agreement": conf["accuracy"],

@@ -98,3 +98,17 @@ def test_ensemble_learned_indicator_and_autotune():
 
     theta = init_params(3)
     _run_and_compare(_riemann(SPECS), 5, indicator="mlp", mlp=theta, autotune=True)
+
+
+def test_ensemble_harvest_equals_single_problem_harvest():
+    """The indicator's training set from one ensemble run (features of the unlimited final
+    stage and the plain TVB labels, every problem, every few steps) equals the single-handle
+    harvest of the same seeds bit for bit."""
+    from paper_2412_16002_gb300 import indicator as ind
+
+    seeds, n, steps, every = [11, 12, 13], 24, 12, 4
+    Xe, Ye = ind.harvest_ensemble(seeds, n=n, k=2, steps=steps, every=every)
+    Xs, Ys = ind.harvest(seeds, n=n, k=2, steps=steps, every=every)
+    assert Xe.shape == Xs.shape == (len(seeds) * (steps // every) * n * n, 44)
+    assert torch.equal(Xe, Xs) and torch.equal(Ye, Ys)
+    assert float(Ye.sum()) > 0
