@@ -151,8 +151,10 @@ void crkdg_options_default(crkdg_options *opt);
 
 /* Create a solver.  k: polynomial degree 1..3; m must match the flux kind and
  * dim (see the state layout above).  opt may be NULL (defaults).  On success
- * *out receives a handle.  Errors: CRKDG_E_ARG, CRKDG_E_UNSUPPORTED,
- * CRKDG_E_OOM, CRKDG_E_CUDA (no handle is returned). */
+ * *out receives a handle.  Errors: CRKDG_E_ARG (also for meshes of more than
+ * 2e9 cells, or whose cells times face points per cell, 2 d (k+1)^(d-1), reach
+ * 2^32 - 1), CRKDG_E_UNSUPPORTED, CRKDG_E_OOM, CRKDG_E_CUDA (no handle is
+ * returned). */
 crkdg_status crkdg_create(const crkdg_mesh *mesh, int k, int m, const crkdg_flux *flux,
                           const crkdg_bounds *bounds, const crkdg_options *opt, crkdg_t *out);
 

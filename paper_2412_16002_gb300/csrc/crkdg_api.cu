@@ -556,6 +556,8 @@ crkdg_status crkdg_create(const crkdg_mesh *mesh, int k, int m, const crkdg_flux
     if (mesh->nx < 1 || ny < 1) return CRKDG_E_ARG;
     if ((double)mesh->nx * ny * m * 64.0 > 9.0e15) return CRKDG_E_ARG;
     if ((double)mesh->nx * ny > 2.0e9) return CRKDG_E_ARG;
+    // the split kernels address a component's face points with 32-bit offsets
+    if ((double)mesh->nx * ny * 2 * mesh->dim * (mesh->dim == 2 ? k + 1 : 1) >= 4294967295.0) return CRKDG_E_ARG;
     if (!(mesh->x1 > mesh->x0) || (mesh->dim == 2 && !(mesh->y1 > mesh->y0))) return CRKDG_E_ARG;
     int nsides = 2 * mesh->dim;
     for (int s = 0; s < nsides; ++s)

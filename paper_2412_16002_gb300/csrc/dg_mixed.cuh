@@ -918,22 +918,44 @@ __global__ void __launch_bounds__(C::NT, split_final_min_blocks<C>()) k_final_x(
     constexpr bool kFaceLanes = NTR == NN && (NF & (NF - 1)) == 0 && NF > 1 && 32 % NN == 0;
     const Bufs B = scal_of<C>(X);
     init_kappa<C>(P, S);
-    double ub0[M];
-    float dvs[M];
-    {
-        MixBufs Y = X;
-        Y.dv = X.dv_s;
-        load_x<C>(P, Y, cell, node, active, ub0, dvs);
+    // u^n's averages: thread `node` of a cell updates components node, node + NN, ... (below M)
+    constexpr int CT = (M + NN - 1) / NN;
+    double ub0[CT];
+#pragma unroll
+    for (int t = 0; t < CT; ++t) {
+        const int c = node + t * NN;
+        ub0[t] = (c < M && active) ? X.ub[(size_t)c * P.ncell + cell] : 0.0;
     }
+    float dvs[M];  // u^n's deviations plus dt sum_{i<s} b_i G(u^(i)) (written by the inner kernel)
+#pragma unroll
+    for (int c = 0; c < M; ++c) dvs[c] = active ? X.dv_s[((size_t)c * P.ncell + cell) * NN + node] : 0.0f;
     float dcf[FPT][M], fhs[FPT][M];
 #pragma unroll
     for (int j = 0; j < FPT; ++j)
 #pragma unroll
         for (int c = 0; c < M; ++c) dcf[j][c] = fhs[j][c] = 0.0f;
 
+    // the trace offsets of this thread's face points and of their partners in the neighbours
+    // (-1: a boundary face), the same in every traced stage
+    // (element offsets within a component's block, 32-bit: the host keeps ncell * NTR below
+    // 2^32 - 1, the marker of a boundary face)
+    const size_t cstr = (size_t)P.ncell * NTR;  // component stride of a trace slot
+    unsigned toff[FPT], noff[FPT];
+#pragma unroll
+    for (int j = 0; j < FPT; ++j) {
+        const int fp = node + j * NN;
+        toff[j] = (unsigned)cell * NTR + fp;
+        noff[j] = 0xffffffffu;
+        if (fp < NTR && active) {
+            const int face = fp / NF, pos = fp - face * NF;
+            const int nb = neighbour(P, cell, face);
+            if (nb >= 0) noff[j] = (unsigned)nb * NTR + (face ^ 1) * NF + pos;
+        }
+    }
+
     for (int i = 0; i < P.s; ++i) {
         if (P.slot[i] < 0) continue;
-        const float *tr = X.tr + (size_t)P.slot[i] * M * P.ncell * NTR;
+        const float *tr = X.tr + (size_t)P.slot[i] * M * cstr;
         const float bi = P.f.b[i];
         // per face point: the interior and exterior normal fluxes and the jump u_R - u_L
         float fin[FPT][M], fex[FPT][M], du[FPT][M], sp[FPT];
@@ -941,15 +963,13 @@ __global__ void __launch_bounds__(C::NT, split_final_min_blocks<C>()) k_final_x(
         for (int j = 0; j < FPT; ++j) {
             int fp = node + j * NN;
             if (fp < NTR && active) {
-                int face = fp / NF, pos = fp - face * NF;
+                int face = fp / NF;
                 float ui[M], ue[M];
 #pragma unroll
-                for (int c = 0; c < M; ++c) ui[c] = tr[((size_t)c * P.ncell + cell) * NTR + fp];
-                int nb = neighbour(P, cell, face);
-                if (nb >= 0) {
-                    int ofp = (face ^ 1) * NF + pos;
+                for (int c = 0; c < M; ++c) ui[c] = tr[c * cstr + toff[j]];
+                if (noff[j] != 0xffffffffu) {
 #pragma unroll
-                    for (int c = 0; c < M; ++c) ue[c] = tr[((size_t)c * P.ncell + nb) * NTR + ofp];
+                    for (int c = 0; c < M; ++c) ue[c] = tr[c * cstr + noff[j]];
                 } else {
                     float av[M];
 #pragma unroll
@@ -1068,16 +1088,20 @@ __global__ void __launch_bounds__(C::NT, split_final_min_blocks<C>()) k_final_x(
         S.term[c][lc][part] = g;
     }
     __syncthreads();
-    for (int c = node; c < M; c += NN) {
-        float m = 0.0f;
-        for (int q = 0; q < NN; ++q) m += S.w[c][lc][q];
-        S.mean[lc][c] = m;
-        double g = S.term[c][lc][0];
 #pragma unroll
-        for (int part = 1; part < PARTS; ++part) g += S.term[c][lc][part];
-        double v = fma(P.dt, g, ub0[c]);
-        S.ubd[lc][c] = v;
-        S.ubf[lc][c] = (float)v;
+    for (int t = 0; t < CT; ++t) {
+        const int c = node + t * NN;
+        if (c < M) {
+            float m = 0.0f;
+            for (int q = 0; q < NN; ++q) m += S.w[c][lc][q];
+            S.mean[lc][c] = m;
+            double g = S.term[c][lc][0];
+#pragma unroll
+            for (int part = 1; part < PARTS; ++part) g += S.term[c][lc][part];
+            double v = fma(P.dt, g, ub0[t]);
+            S.ubd[lc][c] = v;
+            S.ubf[lc][c] = (float)v;
+        }
     }
     __syncthreads();
     float dvn[M];
@@ -1100,9 +1124,6 @@ __global__ void __launch_bounds__(C::NT, split_final_min_blocks<C>()) k_final_x(
     }
     float pts[C::PPT][M];
     limit_x(P, B, S, lc, node, own, S.ubd[lc], dvn, true, true, pts);
-    double ubn[M];
-#pragma unroll
-    for (int c = 0; c < M; ++c) ubn[c] = S.ubd[lc][c];
     float amax = 0.0f;
 #pragma unroll
     for (int j = 0; j < C::PPT; ++j) {
@@ -1118,7 +1139,7 @@ __global__ void __launch_bounds__(C::NT, split_final_min_blocks<C>()) k_final_x(
     // the rate is FP32-evaluated: widen by 2^-20 before it bounds the FP64 step
     if ((threadIdx.x & 31) == 0 && amax > 0.0f) atomicMax(X.a0, dbits((double)amax * (1.0 + 9.5367431640625e-07)));
     if (active) {
-        for (int c = node; c < M; c += NN) X.ub_n[(size_t)c * P.ncell + cell] = ubn[c];
+        for (int c = node; c < M; c += NN) X.ub_n[(size_t)c * P.ncell + cell] = S.ubd[lc][c];
 #pragma unroll
         for (int c = 0; c < M; ++c) X.dv_n[((size_t)c * P.ncell + cell) * NN + node] = dvn[c];
     }

@@ -60,12 +60,22 @@ __device__ __forceinline__ int core_off(int row, int k, int rows) {
     return (((k >> 2) * (rows >> 3) + (row >> 3)) << 7) + ((row & 7) << 4) + ((k & 3) << 2);
 }
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// x rounded to TF32 (10 mantissa bits), to nearest with ties away from zero: half a TF32
+// unit added to the magnitude bits (a carry into the exponent is the correct rounding up),
+// then the 13 low bits cleared.  Two integer operations; equal to cvt.rna.tf32.f32 for every
+// finite or infinite x.
 __device__ __forceinline__ float tf32r(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
+// x = hi + lo with hi its TF32 rounding; lo = x - hi is exact in FP32 and goes to the tensor
+// cores as it is: they read its leading TF32 bits, so hi + lo as read is x to within 2^-21 |x|
+// (|lo| <= 2^-11 |x|, and lo loses below 2^-10 |lo|), the A side of the three-product split.
 __device__ __forceinline__ void split(float x, float &hi, float &lo) {
+    hi = tf32r(x);
+    lo = x - hi;
+}
+// the same with lo rounded to TF32 as well (2^-22 |x|), for the maps, built once per CTA
+__device__ __forceinline__ void split_r(float x, float &hi, float &lo) {
     hi = tf32r(x);
     lo = tf32r(x - hi);
 }
@@ -247,7 +257,7 @@ __device__ inline void tc_build_maps(const Params &P, tc::Smem &S) {
         const int o = e / KE, q = e % KE;
         const float v = (float)map_E(T, o, q);
         float hi, lo;
-        split(v, hi, lo);
+        split_r(v, hi, lo);
         const int off = core_off(o, q, NE) >> 2;
         S.be[0][off] = hi;
         S.be[1][off] = lo;
@@ -264,7 +274,7 @@ __device__ inline void tc_build_maps(const Params &P, tc::Smem &S) {
             v = (float)(((face & 1) ? -0.5 : 0.5) * T.w1[pos] * (face < 2 ? P.rhx : P.rhy));
         }
         float hi, lo;
-        split((float)v, hi, lo);
+        split_r((float)v, hi, lo);
         const int off = core_off(o, k, NG) >> 2;
         S.bg[0][off] = hi;
         S.bg[1][off] = lo;
@@ -509,14 +519,29 @@ __global__ void __launch_bounds__(tc::NT, 1) k_inner_tc(Params P, MixBufs X) {
                     }
                 }
             }
+            // near vacuum (rho_ill) a density is taken rounded from its FP64 value, not the FP32
+            // sum: at the face points (S_K points, so >= eps in the FP64 evaluation after
+            // limiting) and at the nodes, so 1 / rho is that of the FP64 evaluation.  The test is
+            // FP32; the FP64 repair runs behind a warp vote, so it costs nothing where no lane
+            // needs it (the FP64 units are a small fraction of the FP32 ones).
+            float rn[QN], td[QN];  // node densities; the face points' density deviations
+            int ill = 0;
 #pragma unroll
             for (int q = 0; q < QN; ++q) {
-                const float d0 = tr[0][q];  // the density deviation at the face point
+                td[q] = tr[0][q];
 #pragma unroll
                 for (int c = 0; c < M; ++c) tr[c][q] += ubf[c];
-                // face points are S_K points (density >= eps in the FP64 evaluation after
-                // limiting): near vacuum take the density rounded from FP64, not the FP32 sum
-                if (rho_ill(tr[0][q], ubf[0], d0)) tr[0][q] = (float)(S.ubd[0][lc] + (double)d0);
+                if (rho_ill(tr[0][q], ubf[0], td[q])) ill |= 1 << q;
+                rn[q] = ubf[0] + dvc[0][q];
+                if (rho_ill(rn[q], ubf[0], dvc[0][q])) ill |= 16 << q;
+            }
+            if (__any_sync(0xffffffffu, ill != 0)) {
+                const double u0 = S.ubd[0][lc];
+#pragma unroll
+                for (int q = 0; q < QN; ++q) {
+                    if (ill & (1 << q)) tr[0][q] = (float)(u0 + (double)td[q]);
+                    if (ill & (16 << q)) rn[q] = (float)(u0 + (double)dvc[0][q]);
+                }
             }
             // traced stages: traces and averages for the final stage
             if (P.slot[i] >= 0 && active) {
@@ -535,10 +560,8 @@ __global__ void __launch_bounds__(tc::NT, 1) k_inner_tc(Params P, MixBufs X) {
                 for (int q = 0; q < QN; ++q) {
                     float u[M], gx[M], gy[M];
 #pragma unroll
-                    for (int c = 0; c < M; ++c) u[c] = ubf[c] + dvc[c][q];
-                    // near vacuum: the density rounded from its FP64 value (its sign and digits
-                    // right, so 1 / rho is that of the FP64 evaluation), as for the traces
-                    if (rho_ill(u[0], ubf[0], dvc[0][q])) u[0] = (float)(S.ubd[0][lc] + (double)dvc[0][q]);
+                    for (int c = 1; c < M; ++c) u[c] = ubf[c] + dvc[c][q];
+                    u[0] = rn[q];
                     flux_xy_f<PHYS>(P, u, gx, gy);
 #pragma unroll
                     for (int c = 0; c < M; ++c) {

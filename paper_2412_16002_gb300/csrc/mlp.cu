@@ -58,10 +58,10 @@ __device__ __forceinline__ int core_off(int row, int k, int rows) {
     return (((k >> 2) * (rows >> 3) + (row >> 3)) << 7) + ((row & 7) << 4) + ((k & 3) << 2);
 }
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// x rounded to TF32, to nearest with ties away from zero (the rounding of cvt.rna.tf32.f32 for
+// every finite or infinite x): half a TF32 unit added to the magnitude bits, 13 low bits cleared
 __device__ __forceinline__ float tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 // x -> (hi, lo) for the three-product split
 __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
