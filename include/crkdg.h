@@ -163,10 +163,16 @@ crkdg_status crkdg_destroy(crkdg_t h);
 
 /* Copy count doubles of nodal state in (host or device pointer) and apply the
  * scaling limiter once, so that u^n lies in B on every S_K (the hypothesis of
- * Theorem 3.5).  count must equal the state size. */
+ * Theorem 3.5).  count must equal the state size.  The split-precision path
+ * reads a device buffer, or page-locked host memory (cudaHostAlloc,
+ * cudaHostRegister), in place with the kernel that splits it; pageable host
+ * memory is staged by a copy.  The buffer is not read after the call returns. */
 crkdg_status crkdg_set_state(crkdg_t h, const double *nodal, size_t count, int on_device);
 
-/* Copy the current nodal state out (host or device pointer). */
+/* Copy the current nodal state out (host or device pointer).  The
+ * split-precision path writes a device buffer or page-locked host memory in
+ * place with the kernel that merges the state; the call returns when the
+ * state is there. */
 crkdg_status crkdg_get_state(crkdg_t h, double *nodal, size_t count, int on_device);
 
 /* Trial step of eq. (numerical_experiment:CFL), *dt = cfl * dx / a0, written for

@@ -727,28 +727,48 @@ crkdg_status crkdg_kernel_times(crkdg_t h, double ms[3], long long launches[3]) 
 
 const char *crkdg_last_error(crkdg_t h) { return h ? h->err.c_str() : "invalid handle"; }
 
+// The device address under which a kernel can read or write the caller's buffer in place: a
+// device pointer itself, or page-locked host memory mapped into the device's address space
+// (a split-precision state is split or merged over the host link by the kernel, with no staging
+// copy).  nullptr for pageable host memory, which is staged by cudaMemcpyAsync.
+static void *direct_ptr(const void *p, int on_device) {
+    if (on_device) return const_cast<void *>(p);
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // not a CUDA-known pointer: clear the error, stage it
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 crkdg_status crkdg_set_state(crkdg_t h, const double *nodal, size_t count, int on_device) {
     if (!h) return CRKDG_E_ARG;
     if (!nodal || count != h->nstate) return fail(h, CRKDG_E_ARG, "set_state: count must equal the state size");
     try {
-        CK(h, cudaMemcpyAsync(h->unew, nodal, count * sizeof(double),
-                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+        const double *src = h->mixed ? static_cast<const double *>(direct_ptr(nodal, on_device)) : nullptr;
+        if (!src) {
+            CK(h, cudaMemcpyAsync(h->unew, nodal, count * sizeof(double),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+            src = h->unew;
+        }
         Params P = base_params(h);
         CK(h, reset_scalars(h) == CRKDG_OK ? cudaSuccess : cudaErrorUnknown);
         if (h->mixed) {
             MixBufs X = base_xbufs(h);
-            X.nod_in = h->unew;
+            X.nod_in = src;
             X.ub_n = h->xub[h->xcur];
             X.dv_n = h->xdv[h->xcur];
             CK(h, launch_x(h, KX_SPLIT, P, X));
             X = base_xbufs(h);
             X.dv_n = h->xdv[h->xcur];
+            P.mode = MODE_RATE;  // the limiter also posts the trial-step rate of the limited state
             CK(h, launch_x(h, KX_LIMIT, P, X));
             crkdg_status s = queue_mass(h, nullptr, h->xub[h->xcur]);
             if (s == CRKDG_OK) s = read_scalars(h);
             if (s) return s;
             take_mass(h);
-            h->a0_valid = false;
+            h->a0 = from_bits(h->hs->a0);
+            h->a0_valid = true;
             return CRKDG_OK;
         }
         // FP64: the limiter also posts the trial-step rate of the limited state, so
@@ -773,13 +793,16 @@ crkdg_status crkdg_set_state(crkdg_t h, const double *nodal, size_t count, int o
 crkdg_status crkdg_get_state(crkdg_t h, double *nodal, size_t count, int on_device) {
     if (!h) return CRKDG_E_ARG;
     if (!nodal || count != h->nstate) return fail(h, CRKDG_E_ARG, "get_state: count must equal the state size");
+    double *dst = nullptr;
     if (h->mixed) {
+        dst = static_cast<double *>(direct_ptr(nodal, on_device));
         MixBufs X = base_xbufs(h);
-        X.nod_out = h->u;
+        X.nod_out = dst ? dst : h->u;
         CK(h, launch_x(h, KX_MERGE, base_params(h), X));
     }
-    CK(h, cudaMemcpyAsync(nodal, h->u, count * sizeof(double),
-                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+    if (!dst)
+        CK(h, cudaMemcpyAsync(nodal, h->u, count * sizeof(double),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
     CK(h, cudaStreamSynchronize(h->st));
     return CRKDG_OK;
 }

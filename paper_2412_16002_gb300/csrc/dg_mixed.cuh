@@ -1349,6 +1349,37 @@ __global__ void __launch_bounds__(C::NT) k_split_x(Params P, MixBufs X) {
     }
 }
 
+// Trial-step rate at S_K point p of the published split state (deviations and their mean in
+// S.u / S.mean, FP32 averages in S.ubf, FP64 averages ub): sum_d radius_d / (2 h_d) of the
+// FP32 value, and near vacuum of the FP64 evaluation rounded to FP32.
+template <class C>
+__device__ __forceinline__ float rate_point_x(const Params &P, SmemX<C> &S, int lc, int p, const double *ub) {
+    constexpr int DIM = C::D, PHYS = C::PH, M = C::M;
+    float s[M], v32[M];
+    sk_eval_f<C::D, C::NP, M, C::NN>(&S.u[0][lc][0], vec4<C>() ? &S.uT[0][lc][0] : nullptr, C::NCB * C::NN, p, s);
+#pragma unroll
+    for (int c = 0; c < M; ++c) v32[c] = S.ubf[lc][c] + (s[c] - S.mean[lc][c]);
+    if constexpr (PHYS == PH_EULER) {
+        if (rho_ill(v32[0], S.ubf[lc][0], v32[0] - S.ubf[lc][0])) {
+            double v[M];
+            eval64_x(S, lc, p, ub, v, v32);
+#pragma unroll
+            for (int c = 0; c < M; ++c) v32[c] = (float)v[c];
+        }
+    }
+    float r = speed_dir_f<PHYS, DIM>(P, v32, 0) * (0.5f * P.f.rhx);
+    if constexpr (DIM == 2) r = fmaf(speed_dir_f<PHYS, DIM>(P, v32, 1), 0.5f * P.f.rhy, r);
+    return r;
+}
+
+// The largest rate of a block's warps into X.a0, widened by 2^-20 (the rate is FP32-evaluated)
+// before it bounds the FP64 step.
+__device__ __forceinline__ void post_rate_x(const MixBufs &X, float amax) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if ((threadIdx.x & 31) == 0 && amax > 0.0f) atomicMax(X.a0, dbits((double)amax * (1.0 + 9.5367431640625e-07)));
+}
+
 // (ubar, dev) -> FP64 nodal values ubar + (dev - dbar).
 template <class C>
 __global__ void __launch_bounds__(C::NT) k_merge_x(Params P, MixBufs X) {
@@ -1387,6 +1418,16 @@ __global__ void __launch_bounds__(C::NT) k_limit_x(Params P, MixBufs X) {
     }
     __syncthreads();
     limit_x(P, B, S, lc, node, own, S.ubd[lc], dv, false, false, pts);
+    if (P.mode == MODE_RATE) {  // the trial-step rate of the limited state (k_scan_x's rate pass):
+                                // the limiter left the final deviations published
+        float amax = 0.0f;
+#pragma unroll
+        for (int j = 0; j < C::PPT; ++j) {
+            const int p = node + j * NN;
+            if (p < C::NSK && own) amax = fmaxf(amax, rate_point_x<C>(P, S, lc, p, S.ubd[lc]));
+        }
+        post_rate_x(X, amax);
+    }
     if (active)
 #pragma unroll
         for (int c = 0; c < M; ++c) X.dv_n[((size_t)c * P.ncell + cell) * NN + node] = dv[c];
@@ -1414,20 +1455,15 @@ __global__ void __launch_bounds__(C::NT) k_scan_x(Params P, MixBufs X) {
     for (int j = 0; j < C::PPT; ++j) {
         int p = node + j * NN;
         if (p < C::NSK && own) {
+            if (!margins) {
+                amax = fmaxf(amax, rate_point_x<C>(P, S, lc, p, ub));
+                continue;
+            }
             double v[M];
             float v32[M];
-            if (margins) {
-                eval64_x(S, lc, p, ub, v, v32);
-            } else {  // the FP32 value alone (eval64_x's v32)
-                float s[M];
-                sk_eval_f<C::D, C::NP, M, C::NN>(&S.u[0][lc][0], vec4<C>() ? &S.uT[0][lc][0] : nullptr,
-                                                 C::NCB * C::NN, p, s);
-#pragma unroll
-                for (int c = 0; c < M; ++c) v32[c] = S.ubf[lc][c] + (s[c] - S.mean[lc][c]);
-            }
+            eval64_x(S, lc, p, ub, v, v32);
             if constexpr (PHYS == PH_EULER) {
                 if (rho_ill(v32[0], S.ubf[lc][0], v32[0] - S.ubf[lc][0])) {  // near vacuum: FP64
-                    if (!margins) eval64_x(S, lc, p, ub, v, v32);
 #pragma unroll
                     for (int c = 0; c < M; ++c) v32[c] = (float)v[c];
                 }
@@ -1435,7 +1471,6 @@ __global__ void __launch_bounds__(C::NT) k_scan_x(Params P, MixBufs X) {
             float r = speed_dir_f<PHYS, DIM>(P, v32, 0) * (0.5f * rhx);
             if constexpr (DIM == 2) r = fmaf(speed_dir_f<PHYS, DIM>(P, v32, 1), 0.5f * rhy, r);
             amax = fmaxf(amax, r);
-            if (!margins) continue;
             double a0m, a1m;
             if constexpr (PHYS == PH_EULER) {
                 a0m = v[0] - P.eps;

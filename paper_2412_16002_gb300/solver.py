@@ -118,17 +118,19 @@ class Solver:
 
     # ---- state ---------------------------------------------------------------
     def set_state(self, x):
-        """x: numpy array (host) or torch CUDA tensor (device), float64, state layout."""
+        """x: numpy array (host), or torch tensor (a CUDA tensor, or a CPU one, e.g. page-locked),
+        float64, state layout."""
         if _is_torch(x):
-            assert x.is_cuda and x.dtype.is_floating_point and x.element_size() == 8 and x.is_contiguous()
-            self._chk(self.lib.crkdg_set_state(self.h, C.c_void_p(x.data_ptr()), x.numel(), 1))
+            assert x.dtype.is_floating_point and x.element_size() == 8 and x.is_contiguous()
+            self._chk(self.lib.crkdg_set_state(self.h, C.c_void_p(x.data_ptr()), x.numel(), 1 if x.is_cuda else 0))
         else:
             a = np.ascontiguousarray(x, dtype=np.float64)
             self._chk(self.lib.crkdg_set_state(self.h, C.c_void_p(a.ctypes.data), a.size, 0))
 
     def get_state(self, out=None):
         if out is not None and _is_torch(out):
-            self._chk(self.lib.crkdg_get_state(self.h, C.c_void_p(out.data_ptr()), out.numel(), 1))
+            assert out.dtype.is_floating_point and out.element_size() == 8 and out.is_contiguous()
+            self._chk(self.lib.crkdg_get_state(self.h, C.c_void_p(out.data_ptr()), out.numel(), 1 if out.is_cuda else 0))
             return out
         a = np.empty(self.size, dtype=np.float64) if out is None else out
         self._chk(self.lib.crkdg_get_state(self.h, C.c_void_p(a.ctypes.data), a.size, 0))

@@ -362,3 +362,30 @@ def test_mixed_full_size_sampled_cells(name):
             scale = max(np.abs(ref[c]).max(), np.abs(wl.state[c]).max() * 1e-3)
             assert np.abs(got[c] - ref[c]).max() <= 2e-5 * scale, (cx, cy, c)
             assert abs((W * got[c]).sum() - (W * ref[c]).sum()) <= 1e-6 * scale, (cx, cy, c)
+
+
+@pytest.mark.parametrize("dim,k", [(1, 2), (2, 3)])
+def test_mixed_state_in_and_out_of_page_locked_host_memory(dim, k):
+    """The split-precision path splits a page-locked host buffer in place (its kernel reads the
+    host memory) and merges into one: the same state, bit for bit, as through a device buffer and
+    through a pageable (staged) host buffer."""
+    from paper_2412_16002_gb300.solver import Solver
+
+    nx, ny = (37, 1) if dim == 1 else (13, 11)
+    U = inputs.random_euler(dim, nx, ny, k, seed=12, osc=0.8)
+    flat = torch.from_numpy(U.reshape(-1).copy())
+    pinned = flat.pin_memory()
+    outs = []
+    for src in (pinned, flat.cuda(), U):
+        g = Solver(dim, nx, ny, k, (0.0, 1.0, 0.0, 1.0), "euler", precision="mixed")
+        g.set_state(src)
+        g.step(g.max_dt(0.1), "heun3")
+        o_pin = torch.empty_like(flat).pin_memory()
+        o_dev = torch.empty_like(flat, device="cuda")
+        g.get_state(o_pin)
+        g.get_state(o_dev)
+        o_host = g.get_state().reshape(-1)
+        assert np.array_equal(o_pin.numpy(), o_dev.cpu().numpy())
+        assert np.array_equal(o_pin.numpy(), o_host)
+        outs.append(o_pin.numpy().copy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
