@@ -224,3 +224,56 @@ def test_riemann_1024_learned_indicator_to_t02(precision):
     rec = _run_gpu(g, wl, 0.2, closed=False)
     rec.update(config="riemann_1024_q2_mlp", precision=precision, t_end=0.2, training=train)
     _record(rec)
+
+
+def test_ensemble_64_full_size_sampled_members_bitwise():
+    """The benchmark's 64-problem ensemble (256^2-1536^2, Q^2 and Q^3, 6.5e7 cells, learned
+    indicator, autotuned tiles) for 3 steps: every member still running with no failure, and
+    a sample of members (the two smallest of each degree) bit-identical to the same problem
+    stepped alone by crkdg_step at the same trial steps, with equal restarts and flag counts."""
+    import bench
+    from paper_2412_16002_gb300.ensemble import Ensemble, riemann_ensemble_specs, riemann_problem
+    from paper_2412_16002_gb300.solver import Solver
+
+    specs = riemann_ensemble_specs(64, seed=0)
+    theta, _ = bench.trained_indicator()
+    probs = [riemann_problem(s, n, k) for s, n, k in specs]
+    ens = Ensemble(probs, indicator="mlp")
+    ens.set_mlp(theta)
+    for i, (s, n, k) in enumerate(specs):
+        x = inputs.riemann_quadrants_device(s, n, k)
+        ens.set_state(i, x)
+        del x
+    ens.autotune(reps=1)
+    sample = []
+    for deg in (2, 3):
+        members = sorted((n, i) for i, (_, n, k) in enumerate(specs) if k == deg)
+        sample += [i for _, i in members[:2]]
+    singles = {}
+    for i in sample:
+        s, n, k = specs[i]
+        g = Solver.from_workload(inputs.riemann_quadrants(s, n, k), indicator="mlp")
+        g.set_mlp(theta)
+        g.set_state(inputs.riemann_quadrants_device(s, n, k))
+        singles[i] = g
+    times = {i: 0.0 for i in sample}
+    t0 = time.perf_counter()
+    for _ in range(3):
+        assert ens.step() == 64
+        for i, g in singles.items():
+            p = probs[i]
+            info = g.step(min(g.max_dt(p["cfl"]), p["t_end"] - times[i]), p["tableau"])
+            times[i] += info["dt_taken"]
+            e = ens.info(i)
+            assert e["t"] == times[i]
+            assert e["last_restarts"] == info["restarts"]
+            assert e["troubled"] == info["troubled"]
+            assert g.margins().min() >= 0.0
+    for i in range(64):
+        e = ens.info(i)
+        assert e["status"] == 0 and e["steps"] == 3 and e["t"] > 0.0
+    for i, g in singles.items():
+        assert np.array_equal(ens.get_state(i), g.get_state()), i
+    _record(dict(config="ensemble_64_riemann_mlp", steps=3, sampled=sample, seconds=time.perf_counter() - t0,
+                 restarts=sum(ens.info(i)["restarts"] for i in range(64)),
+                 troubled=sum(ens.info(i)["troubled"] for i in range(64))))
