@@ -56,11 +56,15 @@ WORKLOADS = {
     "ensemble_64_riemann_mlp": dict(kind="ensemble", count=64, indicator="mlp"),
     # the standard RKDG (F in every stage), for comparison with the compact scheme
     "sedov_2048_q3_standard": dict(kind="sedov", nx=2048, k=3, scheme="standard"),
+    # the same configuration timed on a developed blast (dense shell of radius 0.3 around the
+    # corner, hot low-density interior, flowing radially) instead of the initial data
+    "sedov_shell_2048_q3_mixed": dict(kind="sedov_shell", nx=2048, k=3, precision="mixed"),
+    "sedov_shell_2048_q3_fp64": dict(kind="sedov_shell", nx=2048, k=3),
     "riemann_1024_q2_standard": dict(kind="riemann", nx=1024, k=2, scheme="standard"),
 }
 DEFAULT = "sedov_2048_q3_mixed"
 # timed steps when --steps is not given
-DEFAULT_STEPS = {"euler1d": 2000, "burgers": 2000, "sedov": 50, "riemann": 100, "ensemble": 5}
+DEFAULT_STEPS = {"euler1d": 2000, "burgers": 2000, "sedov": 50, "sedov_shell": 50, "riemann": 100, "ensemble": 5}
 
 
 def launches_per_attempt(precision, indicator):
@@ -89,8 +93,13 @@ def make_workload(name, seed=0, nx=None):
         return inputs.burgers_sine(w["nx"], w["k"])
     if w["kind"] == "sedov":
         return inputs.sedov(w["nx"], w["k"])
+    if w["kind"] == "sedov_shell":
+        return inputs.sedov_shell(w["nx"], w["k"])
     return inputs.riemann_quadrants(seed, w["nx"], w["k"])
 
+
+INITIAL_STATE = {"sedov_shell": "a developed Sedov-type blast: dense shell of radius 0.3 around the corner, "
+                                "hot low-density interior, radial flow, cold ambient state (p = 1e-13) outside"}
 
 TAB_S = {"midpoint2": 2, "heun3": 3, "rk4": 4}
 TAB_NSLOT = {"midpoint2": 1, "heun3": 2, "rk4": 4}
@@ -333,7 +342,7 @@ def workload_config(name, wl, world):
             "scheme": WORKLOADS[name].get("scheme", "compact"),
             "indicator": WORKLOADS[name].get("indicator", "off"), "cells": wl.cells, "k": wl.k, "m": wl.m,
             "dofs_per_cell": wl.dofs_per_cell, "tableau": wl.tableau, "stages": TAB_S[wl.tableau],
-            "cfl": wl.cfl, "initial_state": "the workload's initial data at t = 0",
+            "cfl": wl.cfl, "initial_state": INITIAL_STATE.get(WORKLOADS[name]["kind"], "the workload's initial data at t = 0"),
             "l2": "GPU arm: L2 flushed (256 MB write) between timed steps" if wl.dim == 2 else
                   "GPU arm: state L2-resident by design in the device-resident loop; L2 flushed before the timed launch",
             "parallelism": f"replicas{world}"}
