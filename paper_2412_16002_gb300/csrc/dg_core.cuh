@@ -1028,8 +1028,18 @@ __device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int b
     store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
 }
 
+// Resident blocks per SM the FP64 final kernel's register budget is sized for: two of the
+// 2D Q^2 blocks (288 threads).  Unbounded, the owned-box test of the domain decomposition took
+// it from 96 to 126 registers, one resident block, and the 1024^2 Q^2 launch from 4.78 to
+// 6.33 ms.
+template <class C>
+constexpr int fp64_final_min_blocks() {
+    return C::NT > 128 ? 2 : 1;
+}
+
 template <int DIM, int N, int PHYS, bool STORED>
-__global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_final(Params P, Bufs B) {
+__global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT, fp64_final_min_blocks<Cfg<DIM, N, PHYS>>())
+    k_final(Params P, Bufs B) {
     final_body<DIM, N, PHYS, STORED>(P, B, blockIdx.x);
 }
 
