@@ -61,6 +61,7 @@ enum { CRKDG_FLUX_ADVECTION = 0, CRKDG_FLUX_BURGERS = 1, CRKDG_FLUX_EULER = 2 };
 enum { CRKDG_PREC_FP64 = 0, CRKDG_PREC_MIXED = 1 };
 enum { CRKDG_IND_OFF = 0, CRKDG_IND_TVB = 1, CRKDG_IND_MLP = 2 };
 enum { CRKDG_SCHEME_COMPACT = 0, CRKDG_SCHEME_STANDARD = 1 };
+enum { CRKDG_THETA2_RATIO = 0, CRKDG_THETA2_EXACT = 1 };
 
 /* Mesh: the domain [x0,x1] (x [y0,y1] in 2D) cut into nx (x ny) equal cells.
  * bc[s] for the sides s = 0 left, 1 right, 2 bottom, 3 top; a periodic side
@@ -130,6 +131,16 @@ typedef struct {
                            its neighbour exchange) in every stage, the same scaling limiter
                            and restart rule; for comparison with the compact scheme.  FP64
                            precision, no indicator (CRKDG_E_UNSUPPORTED otherwise). */
+    int theta2;         /* theta_2 of the Euler scaling limiter.  CRKDG_THETA2_RATIO (default):
+                           the concavity ratio of eq. (Euler-limiter2), (rho e(ubar) - eps) /
+                           (rho e(ubar) - min_q rho e(u_q)).  CRKDG_THETA2_EXACT: for every S_K
+                           point q with rho e(u_q) < eps the t in (0, 1) where
+                           rho e(ubar + t (u_q - ubar)) = eps, a root of a quadratic in t (rho,
+                           m, E are linear in t), and theta_2 = min_q t_q: the least scaling
+                           that restores the bound (the per-point solve of the positivity-limiter
+                           works the text after eq. Euler-limiter2 refers to).  The
+                           same safety margin and verification follow.  FP64 precision
+                           (CRKDG_E_UNSUPPORTED otherwise). */
 } crkdg_options;
 
 typedef struct {

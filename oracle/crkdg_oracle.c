@@ -193,6 +193,7 @@ void orc_set_options(orc_problem *P, int limiter_on, int max_halvings) {
 }
 
 void orc_set_scheme(orc_problem *P, int standard) { P->standard = standard ? 1 : 0; }
+void orc_set_theta2(orc_problem *P, int exact) { P->theta2_exact = exact ? 1 : 0; }
 
 void orc_set_indicator(orc_problem *P, int on, double tvb_M) {
     P->indicator = on;
@@ -540,6 +541,46 @@ static double safe_ratio(double num, double den) {
     return t;
 }
 
+/* The exact theta_2 of one S_K point: along u(t) = ubar + t (u - ubar), rho, m and E are
+ * linear in t, so with rho(t) > 0
+ *   rho e(u(t)) >= eps  <=>  h(t) = (E(t) - eps) rho(t) - |m(t)|^2 / 2 >= 0,
+ * h(t) = a t^2 + b t + c.  h(0) = rho_bar (rho e(ubar) - eps) > 0 for an admissible average
+ * and h(1) < 0 at a violating point, so h has exactly one root in (0, 1): the answer.  The
+ * roots are taken in the cancellation-free form q = -(b + sign(b) sqrt(b^2 - 4ac)) / 2,
+ * roots q / a and c / q.  Returns 1 when the point does not violate (h(1) >= 0). */
+static double theta2_point(const orc_problem *P, const double *ubar, const double *u) {
+    int dim = P->dim;
+    double eps = P->eps;
+    double dr = u[0] - ubar[0], dE = u[dim + 1] - ubar[dim + 1];
+    double mm = 0.0, md = 0.0, dd = 0.0;
+    for (int d = 1; d <= dim; ++d) {
+        double dm = u[d] - ubar[d];
+        mm += ubar[d] * ubar[d];
+        md += ubar[d] * dm;
+        dd += dm * dm;
+    }
+    double c = (ubar[dim + 1] - eps) * ubar[0] - 0.5 * mm;
+    double b = (ubar[dim + 1] - eps) * dr + dE * ubar[0] - md;
+    double a = dE * dr - 0.5 * dd;
+    if (!(c > 0.0)) return 0.0;     /* the average itself is not strictly inside */
+    if (a + b + c >= 0.0) return 1.0; /* h(1) >= 0: no violation at this point */
+    double disc = b * b - 4.0 * a * c;
+    if (disc < 0.0) disc = 0.0;
+    double q = -0.5 * (b + (b >= 0.0 ? sqrt(disc) : -sqrt(disc)));
+    double best = 0.0;
+    int found = 0;
+    double r[2];
+    int nr = 0;
+    if (a != 0.0) r[nr++] = q / a;
+    if (q != 0.0) r[nr++] = c / q;
+    for (int i = 0; i < nr; ++i)
+        if (r[i] > 0.0 && r[i] < 1.0 && (!found || r[i] < best)) {
+            best = r[i];
+            found = 1;
+        }
+    return found ? best : 0.0;
+}
+
 long long orc_limit(const orc_problem *P, double *c, double *theta_out) {
     double xs[ORC_MAXP], ys[ORC_MAXP];
     int np = sk_points(P, xs, ys);
@@ -603,7 +644,23 @@ long long orc_limit(const orc_problem *P, double *c, double *theta_out) {
                 if (!(re >= remin)) remin = re; /* NaN propagates as a violation */
             }
             double th2 = 1.0;
-            if (!(remin >= eps)) th2 = safe_ratio(reb - eps, reb - remin) * margin_factor;
+            if (!(remin >= eps)) {
+                if (P->theta2_exact) {
+                    /* the smallest per-point solution over the violating points */
+                    double tmin = 1.0;
+                    for (int p = 0; p < np; ++p) {
+                        double u[ORC_MAXM];
+                        orc_point_state(P, c, cell, xs[p], ys[p], u);
+                        double re = rho_e(P, u);
+                        if (re >= eps) continue;
+                        double tq = re == re ? theta2_point(P, ubar, u) : 0.0;
+                        if (tq < tmin) tmin = tq;
+                    }
+                    th2 = tmin * margin_factor;
+                } else {
+                    th2 = safe_ratio(reb - eps, reb - remin) * margin_factor;
+                }
+            }
             if (th1 < 1.0 || th2 < 1.0) {
                 /* verify rho >= eps and rho e >= eps on S_K; shrink the final scaling */
                 double tha = th2;

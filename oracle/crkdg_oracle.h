@@ -45,6 +45,7 @@ typedef struct orc_problem {
     int limiter_on;          /* 1: scaling limiter after every stage */
     int indicator;           /* 1: TVB troubled-cell indicator + minmod shock limiter after the final stage */
     int standard;            /* 1: standard RKDG (eq. rkdg): F in the inner stages as well */
+    int theta2_exact;        /* 1: theta_2 from the exact per-point solve (see orc_set_theta2) */
     double tvb_M;            /* TVB constant of the indicator */
     int max_halvings;
     orc_exact_fn exact;
@@ -75,6 +76,13 @@ void orc_set_options(orc_problem *P, int limiter_on, int max_halvings);
 /* scheme: 0 the compact RKDG (Scheme 1L: G in the inner stages, F in the final one), 1 the
  * standard RKDG in Butcher form (eq. rkdg: F in every stage), with the same limiter */
 void orc_set_scheme(orc_problem *P, int standard);
+/* theta_2 of the Euler limiter: 0 the concavity ratio of eq. (Euler-limiter2), 1 the exact
+ * per-point solve of the positivity-limiter works the text after that equation refers to
+ * (the paper prints only the ratio): for every S_K point q where
+ * rho e(u_q) < eps, the t in (0, 1) with rho e(ubar + t (u_q - ubar)) = eps, a root of a
+ * quadratic (rho, m and E are linear in t); theta_2 = min_q t_q (the same safety margin
+ * and verification as the ratio) */
+void orc_set_theta2(orc_problem *P, int exact);
 size_t orc_state_size(const orc_problem *P); /* doubles: ncell*m*n^dim */
 
 /* nodal (Gauss points, layout [m][ny][nx][n_y][n_x]) <-> modal */

@@ -80,6 +80,7 @@ def _load():
     lib.orc_set_exact.argtypes = [V, _EXACT_FN, V]
     lib.orc_set_options.argtypes = [V, C.c_int, C.c_int]
     lib.orc_set_scheme.argtypes = [V, C.c_int]
+    lib.orc_set_theta2.argtypes = [V, C.c_int]
     lib.orc_state_size.argtypes = [V]
     lib.orc_state_size.restype = C.c_size_t
     lib.orc_nodal_to_modal.argtypes = [V, _dp, _dp]
@@ -156,7 +157,7 @@ class Oracle:
     def __init__(self, dim, nx, ny, k, domain, flux, gamma=1.4, velocity=(1.0, 0.0),
                  bounds=(0.0, 1.0), eps=1e-13, bc=("periodic",) * 4, bc_state=None,
                  exact=None, limiter=True, max_halvings=20, indicator=False, tvb_M=10.0,
-                 scheme="compact"):
+                 scheme="compact", theta2="ratio"):
         lib = _load()
         self.lib = lib
         x0, x1, y0, y1 = (tuple(domain) + (0.0, 1.0))[:4]
@@ -191,6 +192,7 @@ class Oracle:
         lib.orc_set_options(self.h, 1 if limiter else 0, max_halvings)
         lib.orc_set_indicator(self.h, 1 if indicator else 0, tvb_M)
         lib.orc_set_scheme(self.h, 1 if scheme == "standard" else 0)
+        lib.orc_set_theta2(self.h, 1 if theta2 == "exact" else 0)
         self.c = np.zeros(self.N)
 
     def __del__(self):

@@ -18,6 +18,7 @@ FLUX = {"advection": 0, "burgers": 1, "euler": 2}
 PREC = {"fp64": 0, "mixed": 1}
 INDICATOR = {"off": 0, "tvb": 1, "mlp": 2}
 SCHEME = {"compact": 0, "standard": 1}
+THETA2 = {"ratio": 0, "exact": 1}
 OPS = {"G": 0, "F": 1, "limit": 2}
 
 
@@ -40,7 +41,8 @@ class Tableau(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("max_halvings", C.c_int), ("indicator", C.c_int),
-                ("tvb_M", C.c_double), ("cuda_stream", C.c_void_p), ("scheme", C.c_int)]
+                ("tvb_M", C.c_double), ("cuda_stream", C.c_void_p), ("scheme", C.c_int),
+                ("theta2", C.c_int)]
 
 
 class StepInfo(C.Structure):

@@ -278,6 +278,7 @@ Params base_params(const crkdg_ctx *h) {
     }
     P.own_on = h->own_on ? 1 : 0;
     for (int i = 0; i < 4; ++i) P.own[i] = h->own[i];
+    P.theta2_exact = h->opt.theta2 == CRKDG_THETA2_EXACT ? 1 : 0;
     for (int i = 0; i < MAXS; ++i) P.slot[i] = -1;
     return P;
 }
@@ -540,6 +541,7 @@ void crkdg_options_default(crkdg_options *opt) {
     opt->tvb_M = 10.0;
     opt->cuda_stream = nullptr;
     opt->scheme = CRKDG_SCHEME_COMPACT;
+    opt->theta2 = CRKDG_THETA2_RATIO;
 }
 
 crkdg_status crkdg_create(const crkdg_mesh *mesh, int k, int m, const crkdg_flux *flux,
@@ -575,6 +577,8 @@ crkdg_status crkdg_create(const crkdg_mesh *mesh, int k, int m, const crkdg_flux
     if (o.indicator != CRKDG_IND_OFF && flux->kind != CRKDG_FLUX_EULER) return CRKDG_E_UNSUPPORTED;
     if (o.indicator == CRKDG_IND_MLP && mesh->dim != 2) return CRKDG_E_UNSUPPORTED;
     if (o.scheme != CRKDG_SCHEME_COMPACT && o.scheme != CRKDG_SCHEME_STANDARD) return CRKDG_E_ARG;
+    if (o.theta2 != CRKDG_THETA2_RATIO && o.theta2 != CRKDG_THETA2_EXACT) return CRKDG_E_ARG;
+    if (o.theta2 == CRKDG_THETA2_EXACT && o.precision != CRKDG_PREC_FP64) return CRKDG_E_UNSUPPORTED;
     if (o.scheme == CRKDG_SCHEME_STANDARD && (o.precision != CRKDG_PREC_FP64 || o.indicator != CRKDG_IND_OFF))
         return CRKDG_E_UNSUPPORTED;
 

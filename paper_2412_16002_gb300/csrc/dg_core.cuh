@@ -242,6 +242,44 @@ __device__ __forceinline__ double rho_e(const double *u) {
     return u[DIM + 1] - (0.5 * kin) * recip_nr(u[0]);
 }
 
+// The exact theta_2 of one S_K point (the alternative to eq. Euler-limiter2's concavity ratio):
+// along u(t) = ub + t (u - ub) the density, momentum and energy are linear in t, so with
+// rho(t) > 0, rho e(u(t)) >= eps <=> h(t) = (E(t) - eps) rho(t) - |m(t)|^2 / 2 >= 0, a quadratic
+// a t^2 + b t + c.  h(0) = rho_bar (rho e(ub) - eps) > 0 for an admissible average and h(1) < 0
+// at a violating point: one root in (0, 1), taken in the cancellation-free form
+// q = -(b + sign(b) sqrt(b^2 - 4ac)) / 2, roots q / a and c / q.  1 when h(1) >= 0, 0 when the
+// average is not strictly inside.  FP64, IEEE division and square root (rare: limited cells).
+template <int DIM>
+__device__ double theta2_point(const double *ub, const double *u, double eps) {
+    const double dr = u[0] - ub[0], dE = u[DIM + 1] - ub[DIM + 1];
+    double mm = 0.0, md = 0.0, dd = 0.0;
+#pragma unroll
+    for (int d = 1; d <= DIM; ++d) {
+        const double dm = u[d] - ub[d];
+        mm += ub[d] * ub[d];
+        md += ub[d] * dm;
+        dd += dm * dm;
+    }
+    const double c = (ub[DIM + 1] - eps) * ub[0] - 0.5 * mm;
+    const double b = (ub[DIM + 1] - eps) * dr + dE * ub[0] - md;
+    const double a = dE * dr - 0.5 * dd;
+    if (!(c > 0.0)) return 0.0;
+    if (a + b + c >= 0.0) return 1.0;
+    double disc = b * b - 4.0 * a * c;
+    if (disc < 0.0) disc = 0.0;
+    const double q = -0.5 * (b + (b >= 0.0 ? sqrt(disc) : -sqrt(disc)));
+    double best = 2.0;
+    if (a != 0.0) {
+        const double r = q / a;
+        if (r > 0.0 && r < 1.0 && r < best) best = r;
+    }
+    if (q != 0.0) {
+        const double r = c / q;
+        if (r > 0.0 && r < 1.0 && r < best) best = r;
+    }
+    return best <= 1.0 ? best : 0.0;
+}
+
 // averages in B (scalar) or B^eps (Euler, rho >= eps and rho e >= eps); NaN fails
 template <int PHYS, int DIM>
 __device__ __forceinline__ bool admissible(const Params &P, const double *ub) {
@@ -600,7 +638,7 @@ __device__ void limit_block(const Params &P, const Bufs &B, Smem<C> &S, int lc, 
     double th2 = 1.0;
     if constexpr (PHYS == PH_EULER) {
         // 5. rho e at S_K with the density already scaled by theta_1
-        unsigned long long km = kKeyPosInf;
+        unsigned long long km = kKeyPosInf, kt = ordbits(1.0);
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
             int p = node + j * NN;
@@ -611,15 +649,24 @@ __device__ void limit_block(const Params &P, const Bufs &B, Smem<C> &S, int lc, 
                 if (below_one(th1)) v[0] = th1 * (v[0] - ub[0]) + ub[0];
                 double re = rho_e<DIM>(v);
                 km = isnan_bits(re) ? kKeyNegInf : umin64(km, ordbits(re));  // NaN counts as a violation
+                // the exact solve: the smallest per-point theta over the violating points
+                if (P.theta2_exact && !ge_pos_bits(re, P.eps))
+                    kt = umin64(kt, ordbits(isnan_bits(re) ? 0.0 : theta2_point<DIM>(ub, v, P.eps)));
             }
         }
         S.red[lc][node][1] = km;
+        S.red[lc][node][0] = kt;
         __syncthreads();
         if (node == 0) {
-            unsigned long long kmn = kKeyPosInf;
-            for (int q = 0; q < NN; ++q) kmn = umin64(kmn, S.red[lc][q][1]);
+            unsigned long long kmn = kKeyPosInf, ktn = ordbits(1.0);
+            for (int q = 0; q < NN; ++q) {
+                kmn = umin64(kmn, S.red[lc][q][1]);
+                ktn = umin64(ktn, S.red[lc][q][0]);
+            }
             const double mn = ordbits_inv(kmn);
-            S.th[lc][1] = ge_pos_bits(mn, P.eps) ? 1.0 : ratio01(reb - P.eps, reb - mn) * kMargin;
+            S.th[lc][1] = ge_pos_bits(mn, P.eps) ? 1.0
+                          : P.theta2_exact        ? ordbits_inv(ktn) * kMargin
+                                                  : ratio01(reb - P.eps, reb - mn) * kMargin;
         }
         __syncthreads();
         th2 = S.th[lc][1];

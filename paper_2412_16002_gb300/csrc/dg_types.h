@@ -105,6 +105,9 @@ struct Params {
     // are still computed, so that the owned cells' final stage reads their traces.
     int own_on;
     int own[4];
+    // theta_2 of the Euler limiter: 0 the concavity ratio of eq. (Euler-limiter2), 1 the exact
+    // per-point solve (theta2_point)
+    int theta2_exact;
 };
 
 // Cells outside the owned box are halo cells (never when own_on is 0).

@@ -844,3 +844,99 @@ def test_standard_rkdg_conservation_and_rate():
         errs.append(o.l2_error(0.1))
     rate = math.log(errs[0] / errs[1]) / math.log(2)
     assert 2.6 < rate < 3.5, (errs, rate)
+
+
+# ---- exact theta_2 (the per-point solve offered beside eq. Euler-limiter2's concavity ratio)
+
+MARGIN = 1.0 - 2.0 ** -40
+
+
+def _momentum_slope_state(dim, k, s):
+    """rho = 1, E = 0.5 everywhere, m_x = s * xi (xi the cell's local x coordinate), m_y = 0:
+    rho e = 0.5 - s^2 xi^2 / 2 is smallest at the Gauss--Lobatto end points xi = +-1."""
+    n = k + 1
+    xg, _ = np.polynomial.legendre.leggauss(n)
+    if dim == 1:
+        U = np.zeros((3, 3, n))
+        U[0] = 1.0
+        U[1] = s * xg[None, :]
+        U[2] = 0.5
+    else:
+        U = np.zeros((4, 3, 3, n, n))
+        U[0] = 1.0
+        U[1] = s * xg[None, None, None, :]
+        U[3] = 0.5
+    return U
+
+
+@pytest.mark.parametrize("dim,k", [(1, 1), (1, 2), (2, 1), (2, 3)])
+def test_theta2_exact_closed_form(dim, k):
+    """The exact theta_2 solves rho e(ubar + t (u_q - ubar)) = eps: with only the momentum
+    varying, 0.5 - t^2 s^2 / 2 = eps, t = sqrt(1 - 2 eps) / s; the concavity ratio gives
+    (0.5 - eps) / (0.5 - (0.5 - s^2 / 2)) instead.  eps = 0.1, s = 1: sqrt(0.8) against 0.8."""
+    eps, s = 0.1, 1.0
+    U = _momentum_slope_state(dim, k, s)
+    nx, ny = (3, 1) if dim == 1 else (3, 3)
+    thetas = {}
+    for mode in ("ratio", "exact"):
+        o = Oracle(dim, nx, ny, k, (0.0, 1.0, 0.0, 1.0), "euler", eps=eps, theta2=mode)
+        o.set_state(U, limit=False)
+        nl, th = o.limit()
+        assert nl == nx * ny
+        thetas[mode] = th
+        # bounds hold at every S_K point after limiting, and the averages are kept
+        assert o.min_margins()[1] >= 0.0
+        assert np.allclose(o.averages()[..., 0], 1.0, rtol=0, atol=1e-15)
+    assert np.allclose(thetas["ratio"], 0.8 * MARGIN, rtol=1e-14, atol=0)
+    assert np.allclose(thetas["exact"], math.sqrt(1.0 - 2.0 * eps) / s * MARGIN, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("dim,k", [(1, 2), (2, 2), (2, 3)])
+def test_theta2_exact_is_the_least_scaling(dim, k):
+    """On oscillating states: per cell the exact theta is at least the concavity ratio's (rho e is
+    concave along the scaling path, so the ratio is a lower bound), the bounds hold after
+    limiting, and at a cell limited by theta_2 the smallest rho e over S_K sits on eps (up to
+    the 2^-40 safety margin) -- no further scaling than the bound needs."""
+    nx, ny = (17, 1) if dim == 1 else (9, 7)
+    U = inputs.random_euler(dim, nx, ny, k, seed=31, osc=1.3)
+    eps = 1e-3
+    res = {}
+    for mode in ("ratio", "exact"):
+        o = Oracle(dim, nx, ny, k, (0.0, 1.0, 0.0, 1.0), "euler", eps=eps, theta2=mode)
+        o.set_state(U, limit=False)
+        c0 = o.c.copy()
+        nl, th = o.limit()
+        assert o.min_margins()[0] >= 0.0 and o.min_margins()[1] >= 0.0
+        res[mode] = (th, o, c0)
+    th_r, th_e = res["ratio"][0], res["exact"][0]
+    limited = th_r < 1.0
+    assert limited.sum() >= 3
+    assert np.all(th_e >= th_r)
+    assert np.any(th_e > th_r * (1 + 1e-6))
+    # the binding point of a limited cell: with the exact solve the smallest rho e over S_K
+    # sits on eps (up to what the 2^-40 safety margin moves it: tiny against the ratio's gap)
+    L = (k + 4) // 2  # ceil((k + 3) / 2) Gauss--Lobatto points
+    xl, _ = np.polynomial.legendre.leggauss(k + 1)
+    xgl = np.asarray(gauss_lobatto(L)[0])
+    pts = [(a, 0.0) for a in xgl] if dim == 1 else \
+        [(a, b) for b in xl for a in xgl] + [(b, a) for b in xl for a in xgl]
+
+    def gap(o, cell):
+        re = []
+        for x, y in pts:
+            u = o.point_state(int(cell), x, y)
+            re.append(u[dim + 1] - 0.5 * sum(u[1 + d] ** 2 for d in range(dim)) / u[0])
+        return min(re) - eps
+
+    o_r, o_e = res["ratio"][1], res["exact"][1]
+    ub = o_e.averages(res["exact"][2]).reshape(o_e.m, -1)
+    rhoe_bar = ub[dim + 1] - 0.5 * sum(ub[1 + d] ** 2 for d in range(dim)) / ub[0]
+    inside = (ub[0] > eps) & (rhoe_bar > eps)  # the limiter's hypothesis: an admissible average
+    tight = 0
+    for cell in np.nonzero(limited & inside)[0]:
+        ge, gr = gap(o_e, cell), gap(o_r, cell)
+        assert ge >= 0.0 and gr >= 0.0
+        if gr > 1e-6:  # theta_2 bound the ratio's scaling
+            assert ge <= 1e-4 * gr
+            tight += 1
+    assert tight >= 1
