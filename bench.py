@@ -68,10 +68,12 @@ DEFAULT_STEPS = {"euler1d": 2000, "burgers": 2000, "sedov": 50, "sedov_shell": 5
 
 
 def launches_per_attempt(precision, indicator):
-    """Kernels one step attempt launches: the inner and final stages, then the indicator:
-    the troubled-cell pass, after (learned) the feature kernel and the network's forward
-    pass, on the split path also the merge to FP64 nodal values the feature kernel reads."""
-    n = 2
+    """Kernels one step attempt launches: the inner and final stages; the indicator: the
+    troubled-cell pass, after (learned) the feature kernel and the network's forward pass, on
+    the split path also the merge to FP64 nodal values the feature kernel reads; then the
+    component totals of the new state for the step's conservation drift (two reduction
+    kernels, after the FP64 path's cell-average kernel)."""
+    n = 2 + (2 if precision == "mixed" else 3)
     if indicator == "tvb":
         n += 1
     elif indicator == "mlp":
@@ -494,7 +496,7 @@ def run_decomposed(args, wl, name):
                          "note": "rank 0's dominant kernel over its local cells (owned block and halo ring)"},
             "e2e": {"value": e2e_value, "unit": "cell-DOF-stage/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes},
-            "gpu_launches": int(kn["inner"]) * 2 * world,
+            "gpu_launches": int(kn["inner"]) * launches_per_attempt(precision, "off") * world,
             "clocks": clocks,
         }
         print(json.dumps(line))
