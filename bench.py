@@ -8,8 +8,9 @@ dt control).  One bench step = one cRKDG time step of the workload.
 Default workload (N=1): the largest single-GPU configuration, the 2D Euler
 (gamma 1.4) Sedov-type blast on [0,1.1]^2, 2048 x 2048 cells, Q^3, four-stage
 fourth-order cRKDG (CFL 0.103), split precision: FP64 cell averages, limiter
-decisions, conservation sums and time step; FP32 operators.  Other
-configurations: --workload.
+decisions, conservation sums and time step; FP32-level operators, the inner stages'
+maps as three-product TF32 tensor-core GEMMs.  Other configurations: --workload
+(e.g. sedov_shell_2048_q3_mixed times the same configuration on a developed blast).
 
 Arms:
   --impl gb300      (default) the CUDA library through its C ABI.
