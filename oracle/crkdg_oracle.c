@@ -194,6 +194,44 @@ void orc_set_options(orc_problem *P, int limiter_on, int max_halvings) {
 
 void orc_set_scheme(orc_problem *P, int standard) { P->standard = standard ? 1 : 0; }
 void orc_set_theta2(orc_problem *P, int exact) { P->theta2_exact = exact ? 1 : 0; }
+void orc_set_source(orc_problem *P, int source) { P->source = source; }
+
+/* Scenario I (Example 4.2): S = d_t U + d_x F + d_y G by the chain rule from the primitive
+ * fields q in {rho, wx, wy, e} and their partial derivatives in t, x and y. */
+void orc_scenario1_source(double gamma, double x, double y, double t, double *S) {
+    const double tp = 2.0 * 3.14159265358979323846, a = exp(-t);
+    const double s1 = sin(tp * (x + y)), c1 = cos(tp * (x + y));
+    const double sx = sin(tp * x), cx = cos(tp * x), sy = sin(tp * y), cy = cos(tp * y);
+    /* primitive fields and their derivatives (index 0: value, 1: d_t, 2: d_x, 3: d_y) */
+    double r[4], u[4], v[4], e[4];
+    r[0] = a * s1 + 2.0;        r[1] = -a * s1;                r[2] = a * tp * c1;        r[3] = a * tp * c1;
+    u[0] = a * cx * sy + 2.0;   u[1] = -a * cx * sy;           u[2] = -a * tp * sx * sy;  u[3] = a * tp * cx * cy;
+    v[0] = a * sx * cy + 2.0;   v[1] = -a * sx * cy;           v[2] = a * tp * cx * cy;   v[3] = -a * tp * sx * sy;
+    e[0] = 0.5 * a * c1 + 1.0;  e[1] = -0.5 * a * c1;          e[2] = -0.5 * a * tp * s1; e[3] = -0.5 * a * tp * s1;
+    /* derived quantities and their derivatives, d = 1, 2, 3 */
+    double p[4], E[4], K[4];
+    for (int d = 0; d < 4; ++d) {
+        if (d == 0) {
+            K[0] = 0.5 * (u[0] * u[0] + v[0] * v[0]);
+            p[0] = (gamma - 1.0) * r[0] * e[0];
+            E[0] = r[0] * e[0] + r[0] * K[0];
+        } else {
+            K[d] = u[0] * u[d] + v[0] * v[d];
+            p[d] = (gamma - 1.0) * (r[d] * e[0] + r[0] * e[d]);
+            E[d] = r[d] * e[0] + r[0] * e[d] + r[d] * K[0] + r[0] * K[d];
+        }
+    }
+    /* S_rho = rho_t + (rho u)_x + (rho v)_y */
+    S[0] = r[1] + (r[2] * u[0] + r[0] * u[2]) + (r[3] * v[0] + r[0] * v[3]);
+    /* S_mx = (rho u)_t + (rho u^2 + p)_x + (rho u v)_y */
+    S[1] = (r[1] * u[0] + r[0] * u[1]) + (r[2] * u[0] * u[0] + 2.0 * r[0] * u[0] * u[2] + p[2]) +
+           (r[3] * u[0] * v[0] + r[0] * u[3] * v[0] + r[0] * u[0] * v[3]);
+    /* S_my = (rho v)_t + (rho u v)_x + (rho v^2 + p)_y */
+    S[2] = (r[1] * v[0] + r[0] * v[1]) + (r[2] * u[0] * v[0] + r[0] * u[2] * v[0] + r[0] * u[0] * v[2]) +
+           (r[3] * v[0] * v[0] + 2.0 * r[0] * v[0] * v[3] + p[3]);
+    /* S_E = E_t + ((E + p) u)_x + ((E + p) v)_y */
+    S[3] = E[1] + ((E[2] + p[2]) * u[0] + (E[0] + p[0]) * u[2]) + ((E[3] + p[3]) * v[0] + (E[0] + p[0]) * v[3]);
+}
 
 void orc_set_indicator(orc_problem *P, int on, double tvb_M) {
     P->indicator = on;
@@ -483,6 +521,22 @@ void orc_apply(const orc_problem *P, int op, const double *in, double *out, doub
                         for (int c = 0; c < m; ++c) rhs[c * P->nmodes + j * n + i] -= len * fnu[q][c] * v;
                     }
             }
+        }
+        /* the source (scenario I): + int_K S v, (k+1)-point Gauss rule, at the stage time t */
+        if (P->source == 1 && dim == 2) {
+            for (int r = 0; r < n; ++r)
+                for (int q = 0; q < n; ++q) {
+                    double xi = P->xg[q], eta = P->xg[r];
+                    double x = P->x0 + (cx + 0.5 * (xi + 1.0)) * hx, y = P->y0 + (cy + 0.5 * (eta + 1.0)) * hy;
+                    double src[ORC_MAXM];
+                    orc_scenario1_source(P->gamma, x, y, t, src);
+                    double jac = hx * hy / 4.0 * P->wg[q] * P->wg[r];
+                    for (int j = 0; j < n; ++j)
+                        for (int i = 0; i < n; ++i) {
+                            double v = orc_legendre(i, xi) * orc_legendre(j, eta);
+                            for (int c = 0; c < m; ++c) rhs[c * P->nmodes + j * n + i] += jac * src[c] * v;
+                        }
+                }
         }
         /* divide by the (diagonal, exact) mass matrix */
         for (int j = 0; j < nyq; ++j)

@@ -46,6 +46,7 @@ typedef struct orc_problem {
     int indicator;           /* 1: TVB troubled-cell indicator + minmod shock limiter after the final stage */
     int standard;            /* 1: standard RKDG (eq. rkdg): F in the inner stages as well */
     int theta2_exact;        /* 1: theta_2 from the exact per-point solve (see orc_set_theta2) */
+    int source;              /* 1: the manufactured source of scenario I (see orc_set_source) */
     double tvb_M;            /* TVB constant of the indicator */
     int max_halvings;
     orc_exact_fn exact;
@@ -83,6 +84,14 @@ void orc_set_scheme(orc_problem *P, int standard);
  * quadratic (rho, m and E are linear in t); theta_2 = min_q t_q (the same safety margin
  * and verification as the ratio) */
 void orc_set_theta2(orc_problem *P, int exact);
+/* source: 0 none; 1 the source of Example 4.2's scenario I (2D Euler), S = d_t U + d_x F(U) +
+ * d_y G(U) of the manufactured solution rho = exp(-t) sin 2pi(x+y) + 2,
+ * w = (exp(-t) cos 2pi x sin 2pi y + 2, exp(-t) sin 2pi x cos 2pi y + 2),
+ * e = exp(-t) cos 2pi(x+y) / 2 + 1 (e the specific internal energy), added to G and F as its L2
+ * projection (the (k+1)-point Gauss rule) at the stage time */
+void orc_set_source(orc_problem *P, int source);
+/* the source of scenario I at (x, y, t), m = 4 components */
+void orc_scenario1_source(double gamma, double x, double y, double t, double *S);
 size_t orc_state_size(const orc_problem *P); /* doubles: ncell*m*n^dim */
 
 /* nodal (Gauss points, layout [m][ny][nx][n_y][n_x]) <-> modal */
