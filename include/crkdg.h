@@ -62,6 +62,7 @@ enum { CRKDG_PREC_FP64 = 0, CRKDG_PREC_MIXED = 1 };
 enum { CRKDG_IND_OFF = 0, CRKDG_IND_TVB = 1, CRKDG_IND_MLP = 2 };
 enum { CRKDG_SCHEME_COMPACT = 0, CRKDG_SCHEME_STANDARD = 1 };
 enum { CRKDG_THETA2_RATIO = 0, CRKDG_THETA2_EXACT = 1 };
+enum { CRKDG_SOURCE_NONE = 0, CRKDG_SOURCE_SCENARIO1 = 1 };
 
 /* Mesh: the domain [x0,x1] (x [y0,y1] in 2D) cut into nx (x ny) equal cells.
  * bc[s] for the sides s = 0 left, 1 right, 2 bottom, 3 top; a periodic side
@@ -141,6 +142,15 @@ typedef struct {
                            works the text after eq. Euler-limiter2 refers to).  The
                            same safety margin and verification follow.  FP64 precision
                            (CRKDG_E_UNSUPPORTED otherwise). */
+    int source;         /* CRKDG_SOURCE_NONE (default), or CRKDG_SOURCE_SCENARIO1: the source of
+                           the manufactured solution of Example 4.2's scenario I (Sec. 4.2),
+                           S = d_t U + d_x F(U) + d_y G(U) for rho = e^-t sin 2pi(x+y) + 2,
+                           w = (e^-t cos 2pi x sin 2pi y + 2, e^-t sin 2pi x cos 2pi y + 2),
+                           e = e^-t cos 2pi(x+y)/2 + 1 (e the specific internal energy), added
+                           to the DG operator at every stage at the stage time t + c_i dt
+                           (c_i = sum_j a_ij; t: crkdg_set_time, advanced by each accepted
+                           step).  For accuracy tests (Table 2): 2D Euler, FP64, the compact
+                           scheme, no indicator (CRKDG_E_UNSUPPORTED otherwise). */
 } crkdg_options;
 
 typedef struct {
@@ -185,6 +195,12 @@ crkdg_status crkdg_set_state(crkdg_t h, const double *nodal, size_t count, int o
  * place with the kernel that merges the state; the call returns when the
  * state is there. */
 crkdg_status crkdg_get_state(crkdg_t h, double *nodal, size_t count, int on_device);
+
+/* The time of the current state: 0 for a new handle, set by crkdg_set_time (or by the t of
+ * crkdg_advance / crkdg_advance_fixed), increased by the dt of every accepted step.  Only a
+ * time-dependent source (crkdg_options.source) reads it. */
+crkdg_status crkdg_set_time(crkdg_t h, double t);
+crkdg_status crkdg_get_time(crkdg_t h, double *t);
 
 /* Trial step of eq. (numerical_experiment:CFL), *dt = cfl * dx / a0, written for
  * Cartesian meshes as *dt = cfl / max_{S_K} sum_d lambda_d / h_d, where

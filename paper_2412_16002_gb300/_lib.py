@@ -19,6 +19,7 @@ PREC = {"fp64": 0, "mixed": 1}
 INDICATOR = {"off": 0, "tvb": 1, "mlp": 2}
 SCHEME = {"compact": 0, "standard": 1}
 THETA2 = {"ratio": 0, "exact": 1}
+SOURCE = {None: 0, "scenario1": 1}
 OPS = {"G": 0, "F": 1, "limit": 2}
 
 
@@ -42,7 +43,7 @@ class Tableau(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("max_halvings", C.c_int), ("indicator", C.c_int),
                 ("tvb_M", C.c_double), ("cuda_stream", C.c_void_p), ("scheme", C.c_int),
-                ("theta2", C.c_int)]
+                ("theta2", C.c_int), ("source", C.c_int)]
 
 
 class StepInfo(C.Structure):
@@ -79,6 +80,8 @@ SYMBOLS = {
     "crkdg_set_state": (C.c_int, [_H, C.c_void_p, C.c_size_t, C.c_int]),
     "crkdg_get_state": (C.c_int, [_H, C.c_void_p, C.c_size_t, C.c_int]),
     "crkdg_max_dt": (C.c_int, [_H, C.c_double, _dp]),
+    "crkdg_set_time": (C.c_int, [_H, C.c_double]),
+    "crkdg_get_time": (C.c_int, [_H, _dp]),
     "crkdg_step": (C.c_int, [_H, C.c_double, C.POINTER(Tableau), C.POINTER(StepInfo)]),
     "crkdg_advance": (C.c_int, [_H, C.c_int, C.c_double, C.c_double, C.POINTER(Tableau), _dp,
                                 C.POINTER(C.c_int), C.POINTER(C.c_int)]),

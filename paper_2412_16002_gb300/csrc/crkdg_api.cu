@@ -203,6 +203,7 @@ struct crkdg_ctx {
     DevScal *hs = nullptr;      // pinned readback
     DevScal *hinit = nullptr;   // pinned initial values
     bool a0_valid = false;
+    double t = 0.0;  // time of the current state (stage times of a time-dependent source)
     double a0 = 0.0;
     bool prof = false;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -279,6 +280,10 @@ Params base_params(const crkdg_ctx *h) {
     P.own_on = h->own_on ? 1 : 0;
     for (int i = 0; i < 4; ++i) P.own[i] = h->own[i];
     P.theta2_exact = h->opt.theta2 == CRKDG_THETA2_EXACT ? 1 : 0;
+    P.source = h->opt.source == CRKDG_SOURCE_SCENARIO1 ? 1 : 0;
+    P.t0 = h->t;
+    P.x0 = h->mesh.x0;
+    P.y0 = h->mesh.y0;
     for (int i = 0; i < MAXS; ++i) P.slot[i] = -1;
     return P;
 }
@@ -542,6 +547,7 @@ void crkdg_options_default(crkdg_options *opt) {
     opt->cuda_stream = nullptr;
     opt->scheme = CRKDG_SCHEME_COMPACT;
     opt->theta2 = CRKDG_THETA2_RATIO;
+    opt->source = CRKDG_SOURCE_NONE;
 }
 
 crkdg_status crkdg_create(const crkdg_mesh *mesh, int k, int m, const crkdg_flux *flux,
@@ -579,6 +585,11 @@ crkdg_status crkdg_create(const crkdg_mesh *mesh, int k, int m, const crkdg_flux
     if (o.scheme != CRKDG_SCHEME_COMPACT && o.scheme != CRKDG_SCHEME_STANDARD) return CRKDG_E_ARG;
     if (o.theta2 != CRKDG_THETA2_RATIO && o.theta2 != CRKDG_THETA2_EXACT) return CRKDG_E_ARG;
     if (o.theta2 == CRKDG_THETA2_EXACT && o.precision != CRKDG_PREC_FP64) return CRKDG_E_UNSUPPORTED;
+    if (o.source != CRKDG_SOURCE_NONE && o.source != CRKDG_SOURCE_SCENARIO1) return CRKDG_E_ARG;
+    if (o.source == CRKDG_SOURCE_SCENARIO1 &&
+        (mesh->dim != 2 || flux->kind != CRKDG_FLUX_EULER || o.precision != CRKDG_PREC_FP64 ||
+         o.scheme != CRKDG_SCHEME_COMPACT || o.indicator != CRKDG_IND_OFF))
+        return CRKDG_E_UNSUPPORTED;
     if (o.scheme == CRKDG_SCHEME_STANDARD && (o.precision != CRKDG_PREC_FP64 || o.indicator != CRKDG_IND_OFF))
         return CRKDG_E_UNSUPPORTED;
 
@@ -808,6 +819,18 @@ crkdg_status crkdg_get_state(crkdg_t h, double *nodal, size_t count, int on_devi
         CK(h, cudaMemcpyAsync(nodal, h->u, count * sizeof(double),
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
     CK(h, cudaStreamSynchronize(h->st));
+    return CRKDG_OK;
+}
+
+crkdg_status crkdg_set_time(crkdg_t h, double t) {
+    if (!h || !isfinite(t)) return CRKDG_E_ARG;
+    h->t = t;
+    return CRKDG_OK;
+}
+
+crkdg_status crkdg_get_time(crkdg_t h, double *t) {
+    if (!h || !t) return CRKDG_E_ARG;
+    *t = h->t;
     return CRKDG_OK;
 }
 
@@ -1057,6 +1080,7 @@ crkdg_status attempt_once(crkdg_t h, Params &P, double dt, bool want_mass) {
 
 // Accept the attempt in h->hs: the new state becomes u^n.
 void accept_attempt(crkdg_t h, double dt, int restarts, crkdg_step_info *info) {
+    h->t += dt;
     if (h->mixed) {
         h->xcur = 1 - h->xcur;
     } else {
@@ -1186,6 +1210,7 @@ static crkdg_status advance_1d(crkdg_t h, int nsteps, double cfl, double dt_fixe
     }
     if (c->steps > 0) h->mass_valid = false;  // the loop keeps no component totals
     *t = c->t_out;
+    h->t = *t;
     if (steps_done) *steps_done = c->steps;
     if (restarts) *restarts = c->restarts;
     if (c->steps > 0 && c->rate_out >= 0.0) {
@@ -1202,6 +1227,7 @@ crkdg_status crkdg_advance(crkdg_t h, int nsteps, double cfl, double t_end, cons
                            double *t, int *steps_done, int *restarts) {
     if (!h || !t) return CRKDG_E_ARG;
     if (!(cfl > 0.0)) return fail(h, CRKDG_E_ARG, "advance: cfl must be > 0");
+    h->t = *t;  // the caller's time is the state's
     if (h->dim == 1 && !h->mixed && h->opt.indicator == CRKDG_IND_OFF && !h->own_on &&
         h->opt.scheme == CRKDG_SCHEME_COMPACT) {
         try {
@@ -1234,6 +1260,7 @@ crkdg_status crkdg_advance_fixed(crkdg_t h, int nsteps, double dt, double t_end,
                                  double *t, int *steps_done, int *restarts) {
     if (!h || !t) return CRKDG_E_ARG;
     if (!(dt > 0.0) || !isfinite(dt)) return fail(h, CRKDG_E_ARG, "advance_fixed: dt must be finite and > 0");
+    h->t = *t;  // the caller's time is the state's
     if (h->dim == 1 && !h->mixed && h->opt.indicator == CRKDG_IND_OFF && !h->own_on &&
         h->opt.scheme == CRKDG_SCHEME_COMPACT) {
         try {

@@ -841,6 +841,68 @@ __device__ __forceinline__ void store_node(const Params &P, double *dst, int cel
 //   u^(i) = u^n + dt sum_{j<i} a_ij G(u~^(j)),  u~^(i) = L(u^(i))   (eq. rkdg-lim)
 // and the accumulation u* = u^n + dt sum_i b_i G(u~^(i)); the traces of every
 // u~^(i) with b_i != 0 go to B.tr for the final kernel.
+// The source of Example 4.2's scenario I, S = d_t U + div F(U) of the manufactured solution
+// rho = e^-t sin 2pi(x+y) + 2, w = (e^-t cos 2pi x sin 2pi y + 2, e^-t sin 2pi x cos 2pi y + 2),
+// e = e^-t cos 2pi(x+y) / 2 + 1, at (x, y, t).  Each primitive q is held with its t-, x- and
+// y-derivatives (q[0..3]); products by the product rule, then the four balance laws.
+__device__ inline void scenario1_source(double gamma, double x, double y, double t, double *S) {
+    const double w = 6.283185307179586, a = exp(-t);
+    double sxy, cxy, sx, cx, sy, cy;
+    sincos(w * (x + y), &sxy, &cxy);
+    sincos(w * x, &sx, &cx);
+    sincos(w * y, &sy, &cy);
+    const double rho[4] = {a * sxy + 2.0, -a * sxy, w * a * cxy, w * a * cxy};
+    const double vx[4] = {a * cx * sy + 2.0, -a * cx * sy, -w * a * sx * sy, w * a * cx * cy};
+    const double vy[4] = {a * sx * cy + 2.0, -a * sx * cy, w * a * cx * cy, -w * a * sx * sy};
+    const double ei[4] = {0.5 * a * cxy + 1.0, -0.5 * a * cxy, -0.5 * w * a * sxy, -0.5 * w * a * sxy};
+    auto prod = [](const double *f, const double *g, double *h) {  // h = f g with its derivatives
+        h[0] = f[0] * g[0];
+#pragma unroll
+        for (int d = 1; d < 4; ++d) h[d] = f[d] * g[0] + f[0] * g[d];
+    };
+    double mx[4], my[4], re[4], mxx[4], mxy[4], myy[4], kx[4], ky[4];
+    prod(rho, vx, mx);   // rho w_x
+    prod(rho, vy, my);   // rho w_y
+    prod(rho, ei, re);   // rho e
+    prod(mx, vx, mxx);   // rho w_x^2
+    prod(mx, vy, mxy);   // rho w_x w_y
+    prod(my, vy, myy);   // rho w_y^2
+    double E[4], H[4], p[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        p[d] = (gamma - 1.0) * re[d];
+        E[d] = re[d] + 0.5 * (mxx[d] + myy[d]);
+        H[d] = E[d] + p[d];  // E + p
+    }
+    prod(H, vx, kx);  // (E + p) w_x
+    prod(H, vy, ky);  // (E + p) w_y
+    // index 1: d/dt, 2: d/dx, 3: d/dy
+    S[0] = rho[1] + mx[2] + my[3];
+    S[1] = mx[1] + mxx[2] + p[2] + mxy[3];
+    S[2] = my[1] + mxy[2] + myy[3] + p[3];
+    S[3] = E[1] + kx[2] + ky[3];
+}
+
+// G += S at this thread's node for stage i (time t0 + c_i dt, c_i the row sum of A): the
+// collocated source is its projection by the (k+1)-point Gauss rule.
+template <int DIM, int N, int PHYS>
+__device__ __forceinline__ void add_source(const Params &P, int cell, int node, int stage, double *g) {
+    if constexpr (DIM == 2 && PHYS == PH_EULER) {
+        const NodalTables &T = c_tab[N - 2];
+        double c = 0.0;
+        for (int j = 0; j < stage; ++j) c += P.A[stage][j];
+        const int cx = cell % P.nx, cy = cell / P.nx;
+        const int a = node % N, b = node / N;
+        const double hx = 2.0 / P.rhx, hy = 2.0 / P.rhy;
+        const double x = P.x0 + (cx + 0.5 * (T.xg[a] + 1.0)) * hx;
+        const double y = P.y0 + (cy + 0.5 * (T.xg[b] + 1.0)) * hy;
+        double src[4];
+        scenario1_source(P.gamma, x, y, P.t0 + c * P.dt, src);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) g[k] += src[k];
+    }
+}
+
 template <int DIM, int N, int PHYS>
 __device__ __forceinline__ void inner_body(const Params &P, const Bufs &B, int blk) {
     using C = Cfg<DIM, N, PHYS>;
@@ -872,6 +934,7 @@ __device__ __forceinline__ void inner_body(const Params &P, const Bufs &B, int b
         double trs[FPT][M];
         const bool keep_faces = P.slot[i] >= 0 && B.tfs != nullptr;
         eval_G(P, S, lc, node, cur, gh[i], trs, keep_faces);
+        if (P.source && active) add_source<DIM, N, PHYS>(P, cell, node, i, gh[i]);
         if (P.slot[i] >= 0) {  // cell average of the traced stage value (outflow exterior state)
             const NodalTables &T = c_tab[N - 2];
             cell_averages<C>(S.u[lc], node, [&](int c, double s) {

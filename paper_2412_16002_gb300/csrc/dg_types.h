@@ -108,6 +108,10 @@ struct Params {
     // theta_2 of the Euler limiter: 0 the concavity ratio of eq. (Euler-limiter2), 1 the exact
     // per-point solve (theta2_point)
     int theta2_exact;
+    // the manufactured source of Example 4.2's scenario I (2D Euler) added to G at the nodes:
+    // 0 off, 1 on; t0 the time of u^n (stage i at t0 + c_i dt), x0, y0 the mesh's lower corner
+    int source;
+    double t0, x0, y0;
 };
 
 // Cells outside the owned box are halo cells (never when own_on is 0).

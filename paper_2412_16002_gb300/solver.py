@@ -57,7 +57,8 @@ class Solver:
 
     def __init__(self, dim, nx, ny, k, domain, flux, gamma=1.4, velocity=(1.0, 0.0), bounds=(0.0, 1.0),
                  eps=1e-13, bc=("periodic",) * 4, bc_state=None, stream=None, max_halvings=20,
-                 precision="fp64", indicator="off", tvb_M=10.0, scheme="compact", theta2="ratio"):
+                 precision="fp64", indicator="off", tvb_M=10.0, scheme="compact", theta2="ratio",
+                 source=None):
         self.lib = L.load()
         mesh = L.Mesh()
         mesh.dim, mesh.nx, mesh.ny = dim, nx, ny if dim == 2 else 1
@@ -78,6 +79,7 @@ class Solver:
         opt.tvb_M = tvb_M
         opt.scheme = L.SCHEME[scheme]
         opt.theta2 = L.THETA2[theta2]
+        opt.source = L.SOURCE[source]
         if stream is not None:
             opt.cuda_stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
         self.m = dim + 2 if flux == "euler" else 1
@@ -138,6 +140,14 @@ class Solver:
         return a.reshape(self.nodal_shape())
 
     # ---- stepping ------------------------------------------------------------
+    def set_time(self, t):
+        self._chk(self.lib.crkdg_set_time(self.h, C.c_double(t)))
+
+    def time(self):
+        t = C.c_double()
+        self._chk(self.lib.crkdg_get_time(self.h, C.byref(t)))
+        return t.value
+
     def max_dt(self, cfl):
         dt = C.c_double()
         self._chk(self.lib.crkdg_max_dt(self.h, cfl, C.byref(dt)))
