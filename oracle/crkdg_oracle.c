@@ -195,6 +195,7 @@ void orc_set_options(orc_problem *P, int limiter_on, int max_halvings) {
 void orc_set_scheme(orc_problem *P, int standard) { P->standard = standard ? 1 : 0; }
 void orc_set_theta2(orc_problem *P, int exact) { P->theta2_exact = exact ? 1 : 0; }
 void orc_set_source(orc_problem *P, int source) { P->source = source; }
+void orc_set_basis(orc_problem *P, int pk) { P->pk = pk ? 1 : 0; }
 
 /* Scenario I (Example 4.2): S = d_t U + d_x F + d_y G by the chain rule from the primitive
  * fields q in {rho, wx, wy, e} and their partial derivatives in t, x and y. */
@@ -251,6 +252,19 @@ static double *cell_coef_w(const orc_problem *P, double *c, int cell, int comp) 
 /* nodal <-> modal                                                           */
 /* ------------------------------------------------------------------------ */
 
+/* P^k: zero the modes L_i(x) L_j(y) with i + j > k of every cell and component */
+static void drop_high_modes(const orc_problem *P, double *modal) {
+    if (!P->pk || P->dim != 2) return;
+    int n = P->n;
+    for (int comp = 0; comp < P->m; ++comp)
+        for (int cell = 0; cell < P->ncell; ++cell) {
+            double *c = cell_coef_w(P, modal, cell, comp);
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < n; ++i)
+                    if (i + j > P->k) c[j * n + i] = 0.0;
+        }
+}
+
 void orc_nodal_to_modal(const orc_problem *P, const double *nodal, double *modal) {
     /* L2 projection by the (k+1)-point Gauss rule, exact for Q^k */
     int n = P->n, nyn = P->dim == 2 ? n : 1;
@@ -271,6 +285,7 @@ void orc_nodal_to_modal(const orc_problem *P, const double *nodal, double *modal
                     c[j * n + i] = s / norm;
                 }
         }
+    drop_high_modes(P, modal);  /* P^k: the L2 projection keeps the retained modes */
 }
 
 static double eval_modal(const orc_problem *P, const double *c, double xi, double eta) {
@@ -548,6 +563,7 @@ void orc_apply(const orc_problem *P, int op, const double *in, double *out, doub
             }
     }
     free(rhs);
+    drop_high_modes(P, out);  /* P^k: only the retained modes are test functions */
 }
 
 /* ------------------------------------------------------------------------ */

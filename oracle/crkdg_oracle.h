@@ -47,6 +47,7 @@ typedef struct orc_problem {
     int standard;            /* 1: standard RKDG (eq. rkdg): F in the inner stages as well */
     int theta2_exact;        /* 1: theta_2 from the exact per-point solve (see orc_set_theta2) */
     int source;              /* 1: the manufactured source of scenario I (see orc_set_source) */
+    int pk;                  /* 1: the total-degree space P^k in 2D (see orc_set_basis) */
     double tvb_M;            /* TVB constant of the indicator */
     int max_halvings;
     orc_exact_fn exact;
@@ -90,6 +91,12 @@ void orc_set_theta2(orc_problem *P, int exact);
  * e = exp(-t) cos 2pi(x+y) / 2 + 1 (e the specific internal energy), added to G and F as its L2
  * projection (the (k+1)-point Gauss rule) at the stage time */
 void orc_set_source(orc_problem *P, int source);
+/* basis: 0 the tensor space Q^k; 1 the total-degree space P^k (2D; in 1D the two coincide):
+ * the modal tensor Legendre basis restricted to the modes L_i(x) L_j(y) with i + j <= k, which
+ * are L2-orthogonal, so the Galerkin equations of P^k are those of Q^k tested against the
+ * retained modes only: every operator output, state projection and stage value keeps the
+ * modes i + j <= k and has the others zero (Sec. 4.2 tests both spaces) */
+void orc_set_basis(orc_problem *P, int pk);
 /* the source of scenario I at (x, y, t), m = 4 components */
 void orc_scenario1_source(double gamma, double x, double y, double t, double *S);
 size_t orc_state_size(const orc_problem *P); /* doubles: ncell*m*n^dim */

@@ -82,6 +82,7 @@ def _load():
     lib.orc_set_scheme.argtypes = [V, C.c_int]
     lib.orc_set_theta2.argtypes = [V, C.c_int]
     lib.orc_set_source.argtypes = [V, C.c_int]
+    lib.orc_set_basis.argtypes = [V, C.c_int]
     lib.orc_scenario1_source.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double)]
     lib.orc_state_size.argtypes = [V]
     lib.orc_state_size.restype = C.c_size_t
@@ -159,7 +160,7 @@ class Oracle:
     def __init__(self, dim, nx, ny, k, domain, flux, gamma=1.4, velocity=(1.0, 0.0),
                  bounds=(0.0, 1.0), eps=1e-13, bc=("periodic",) * 4, bc_state=None,
                  exact=None, limiter=True, max_halvings=20, indicator=False, tvb_M=10.0,
-                 scheme="compact", theta2="ratio", source=None):
+                 scheme="compact", theta2="ratio", source=None, basis="Q"):
         lib = _load()
         self.lib = lib
         x0, x1, y0, y1 = (tuple(domain) + (0.0, 1.0))[:4]
@@ -196,6 +197,7 @@ class Oracle:
         lib.orc_set_scheme(self.h, 1 if scheme == "standard" else 0)
         lib.orc_set_theta2(self.h, 1 if theta2 == "exact" else 0)
         lib.orc_set_source(self.h, 1 if source == "scenario1" else 0)
+        lib.orc_set_basis(self.h, 1 if basis == "P" else 0)
         self.c = np.zeros(self.N)
 
     def __del__(self):

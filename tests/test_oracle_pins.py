@@ -1027,3 +1027,48 @@ def test_scenario1_without_source_is_not_exact():
         o.run(0.1024, 0.0, HEUN3, fixed_dt=dt)
         errs[src] = o.l2_error(0.1024)
     assert errs[None] > 20 * errs["scenario1"]
+
+
+# ---- total-degree P^k bases (2D)
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_table3_pk_column_reproduced(k):
+    """Table 3's P^k column (Example 4.2, scenario II, the modal Legendre basis restricted to
+    i + j <= k, exact boundary data on [0, 1]^2): the oracle reproduces the printed errors within
+    10% and the rates within 0.15 on the first two levels (k = 1 with the midpoint scheme, eq.
+    cRKDG2).  The same runs in Q^k give different errors (the spaces differ)."""
+    rows = [r for r in _golden("table3_euler_scenario2_pk.txt") if int(r[0]) == k][:2]
+    tab = {1: MIDPOINT2, 2: HEUN3, 3: RK4}[k]
+    errs = {}
+    for basis in ("P", "Q"):
+        errs[basis] = []
+        for r in rows:
+            nx, dt = int(r[1]), float(r[2])
+            o = Oracle(2, nx, nx, k, (0, 1, 0, 1), "euler", eps=1e-8, bc=("exact",) * 4, exact=_scenario2, basis=basis)
+            X, Y = inputs.node_coords(2, nx, nx, k, (0, 1, 0, 1))
+            o.set_state(np.array(np.vectorize(lambda x, y, c: _scenario2(x, y, 0.0)[c])(
+                X[None], Y[None], np.arange(4)[:, None, None, None, None])))
+            o.run(0.1024, 0.0, tab, fixed_dt=dt)
+            errs[basis].append(o.l2_error(0.1024))
+    for e, r in zip(errs["P"], rows):
+        assert abs(e / float(r[3]) - 1.0) < 0.10, (k, r, e)
+    rate = math.log(errs["P"][0] / errs["P"][1]) / math.log(2)
+    assert abs(rate - float(rows[1][4])) < 0.15, rate
+    assert all(abs(p / q - 1.0) > 0.2 for p, q in zip(errs["P"], errs["Q"]))
+
+
+def test_pk_projection_keeps_pk_and_averages():
+    """The P^k state of a Q^k nodal field keeps the modes i + j <= k exactly (a P^k field is
+    unchanged), drops the others, and keeps the cell averages."""
+    k, n = 3, 5
+    X, Y = inputs.node_coords(2, n, n, k, (0, 1, 0, 1))
+    U = np.stack([2 + X + X * Y + X ** 2 * Y, 1 + X ** 3, 1 + Y ** 2 * X, 3 + X * Y]) * 1.0
+    q = Oracle(2, n, n, k, (0, 1, 0, 1), "euler", eps=1e-8)
+    p = Oracle(2, n, n, k, (0, 1, 0, 1), "euler", eps=1e-8, basis="P")
+    cq, cp = q.to_modal(U), p.to_modal(U)
+    # components 1..3 have total degree <= 3: unchanged; the averages are kept in any case
+    assert np.allclose(p.to_nodal(cp)[1:], U[1:], atol=1e-13)
+    assert np.allclose(p.averages(cp), q.averages(cq), atol=1e-14)
+    V = np.stack([2 + X ** 2 * Y ** 2, 1 + 0 * X, 1 + 0 * X, 3 + X ** 3 * Y])  # degrees 4 and 4
+    assert not np.allclose(p.to_nodal(p.to_modal(V))[0], V[0], rtol=0.0, atol=1e-7)
+    assert np.allclose(p.averages(p.to_modal(V)), q.averages(q.to_modal(V)), atol=1e-14)
