@@ -63,6 +63,7 @@ enum { CRKDG_IND_OFF = 0, CRKDG_IND_TVB = 1, CRKDG_IND_MLP = 2 };
 enum { CRKDG_SCHEME_COMPACT = 0, CRKDG_SCHEME_STANDARD = 1 };
 enum { CRKDG_THETA2_RATIO = 0, CRKDG_THETA2_EXACT = 1 };
 enum { CRKDG_SOURCE_NONE = 0, CRKDG_SOURCE_SCENARIO1 = 1 };
+enum { CRKDG_BASIS_Q = 0, CRKDG_BASIS_P = 1 };
 
 /* Mesh: the domain [x0,x1] (x [y0,y1] in 2D) cut into nx (x ny) equal cells.
  * bc[s] for the sides s = 0 left, 1 right, 2 bottom, 3 top; a periodic side
@@ -151,6 +152,15 @@ typedef struct {
                            (c_i = sum_j a_ij; t: crkdg_set_time, advanced by each accepted
                            step).  For accuracy tests (Table 2): 2D Euler, FP64, the compact
                            scheme, no indicator (CRKDG_E_UNSUPPORTED otherwise). */
+    int basis;          /* the DG space: CRKDG_BASIS_Q (default), the tensor-product Q^k, or
+                           CRKDG_BASIS_P, the total-degree P^k (Sec. 4.2 reports both).  The
+                           state keeps the nodal layout at the (k+1)^2 Gauss points and lies in
+                           P^k: every stage value, u* and u^{n+1} (and the state crkdg_set_state
+                           receives) is L2-projected onto P^k before the limiter; the Legendre
+                           modes L_i(x) L_j(y) being orthogonal, that is the P^k Galerkin
+                           scheme with the same quadrature.  In 1D the spaces coincide.  2D:
+                           FP64, the compact scheme, no indicator (CRKDG_E_UNSUPPORTED
+                           otherwise). */
 } crkdg_options;
 
 typedef struct {

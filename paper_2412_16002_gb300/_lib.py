@@ -20,6 +20,7 @@ INDICATOR = {"off": 0, "tvb": 1, "mlp": 2}
 SCHEME = {"compact": 0, "standard": 1}
 THETA2 = {"ratio": 0, "exact": 1}
 SOURCE = {None: 0, "scenario1": 1}
+BASIS = {"Q": 0, "P": 1}
 OPS = {"G": 0, "F": 1, "limit": 2}
 
 
@@ -43,7 +44,7 @@ class Tableau(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("max_halvings", C.c_int), ("indicator", C.c_int),
                 ("tvb_M", C.c_double), ("cuda_stream", C.c_void_p), ("scheme", C.c_int),
-                ("theta2", C.c_int), ("source", C.c_int)]
+                ("theta2", C.c_int), ("source", C.c_int), ("basis", C.c_int)]
 
 
 class StepInfo(C.Structure):

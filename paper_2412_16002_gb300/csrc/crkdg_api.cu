@@ -168,6 +168,31 @@ void build_tables(NodalTables *tab) {
             T.w1f[a] = (float)T.w1[a];
         }
         for (int q = 0; q < MAXN * MAXN; ++q) T.w2f[q] = (float)T.w2[q];
+        {  // P^k projection: modes L_i(x) L_j(y), i + j <= n - 1, Legendre by the recurrence
+            auto leg = [](int i, double x) {
+                double p0 = 1.0, p1 = x;
+                if (i == 0) return p0;
+                for (int l = 1; l < i; ++l) {
+                    const double p2 = ((2.0 * l + 1.0) * x * p1 - l * p0) / (l + 1.0);
+                    p0 = p1;
+                    p1 = p2;
+                }
+                return p1;
+            };
+            const int k = n - 1;
+            for (int node = 0; node < n * n; ++node) {
+                const int a = node % n, b = node / n;
+                for (int q = 0; q < n * n; ++q) {
+                    const int qa = q % n, qb = q / n;
+                    double v = 0.0;
+                    for (int j = 0; j <= k; ++j)
+                        for (int i = 0; i + j <= k; ++i)
+                            v += leg(i, T.xg[a]) * leg(j, T.xg[b]) * (0.5 * (2 * i + 1)) * (0.5 * (2 * j + 1)) *
+                                 T.wg[qa] * T.wg[qb] * leg(i, T.xg[qa]) * leg(j, T.xg[qb]);
+                    T.pk[node][q] = v;
+                }
+            }
+        }
         for (int q = 0; q < n * n; ++q) {
             const int qa = q % n, qb = q / n;
             T.mom2[q] = (3.0 * T.w1[qa]) * T.w1[qb];
@@ -284,6 +309,7 @@ Params base_params(const crkdg_ctx *h) {
     P.t0 = h->t;
     P.x0 = h->mesh.x0;
     P.y0 = h->mesh.y0;
+    P.pk = (h->opt.basis == CRKDG_BASIS_P && h->dim == 2) ? 1 : 0;
     for (int i = 0; i < MAXS; ++i) P.slot[i] = -1;
     return P;
 }
@@ -548,6 +574,7 @@ void crkdg_options_default(crkdg_options *opt) {
     opt->scheme = CRKDG_SCHEME_COMPACT;
     opt->theta2 = CRKDG_THETA2_RATIO;
     opt->source = CRKDG_SOURCE_NONE;
+    opt->basis = CRKDG_BASIS_Q;
 }
 
 crkdg_status crkdg_create(const crkdg_mesh *mesh, int k, int m, const crkdg_flux *flux,
@@ -586,6 +613,10 @@ crkdg_status crkdg_create(const crkdg_mesh *mesh, int k, int m, const crkdg_flux
     if (o.theta2 != CRKDG_THETA2_RATIO && o.theta2 != CRKDG_THETA2_EXACT) return CRKDG_E_ARG;
     if (o.theta2 == CRKDG_THETA2_EXACT && o.precision != CRKDG_PREC_FP64) return CRKDG_E_UNSUPPORTED;
     if (o.source != CRKDG_SOURCE_NONE && o.source != CRKDG_SOURCE_SCENARIO1) return CRKDG_E_ARG;
+    if (o.basis != CRKDG_BASIS_Q && o.basis != CRKDG_BASIS_P) return CRKDG_E_ARG;
+    if (o.basis == CRKDG_BASIS_P && mesh->dim == 2 &&
+        (o.precision != CRKDG_PREC_FP64 || o.scheme != CRKDG_SCHEME_COMPACT || o.indicator != CRKDG_IND_OFF))
+        return CRKDG_E_UNSUPPORTED;
     if (o.source == CRKDG_SOURCE_SCENARIO1 &&
         (mesh->dim != 2 || flux->kind != CRKDG_FLUX_EULER || o.precision != CRKDG_PREC_FP64 ||
          o.scheme != CRKDG_SCHEME_COMPACT || o.indicator != CRKDG_IND_OFF))

@@ -841,6 +841,28 @@ __device__ __forceinline__ void store_node(const Params &P, double *dst, int cel
 //   u^(i) = u^n + dt sum_{j<i} a_ij G(u~^(j)),  u~^(i) = L(u^(i))   (eq. rkdg-lim)
 // and the accumulation u* = u^n + dt sum_i b_i G(u~^(i)); the traces of every
 // u~^(i) with b_i != 0 go to B.tr for the final kernel.
+// The L2 projection of this thread's node values onto the total-degree space P^k (2D; a block
+// collective): v at node = sum_q pk[node][q] v_q per component, through S.u.
+template <class C>
+__device__ __forceinline__ void project_pk(Smem<C> &S, int lc, int node, double *v) {
+    if constexpr (C::D == 2) {
+        constexpr int M = C::M, NN = C::NN;
+        const NodalTables &T = c_tab[C::NP - 2];
+        __syncthreads();  // earlier readers of S.u are done
+#pragma unroll
+        for (int c = 0; c < M; ++c) S.u[lc][c][node] = v[c];
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            double s = 0.0;
+#pragma unroll
+            for (int q = 0; q < NN; ++q) s = fma(T.pk[node][q], S.u[lc][c][q], s);
+            v[c] = s;
+        }
+        __syncthreads();  // S.u is free again
+    }
+}
+
 // The source of Example 4.2's scenario I, S = d_t U + div F(U) of the manufactured solution
 // rho = e^-t sin 2pi(x+y) + 2, w = (e^-t cos 2pi x sin 2pi y + 2, e^-t sin 2pi x cos 2pi y + 2),
 // e = e^-t cos 2pi(x+y) / 2 + 1, at (x, y, t).  Each primitive q is held with its t-, x- and
@@ -928,6 +950,7 @@ __device__ __forceinline__ void inner_body(const Params &P, const Bufs &B, int b
                     if (nonzero_bits(P.A[i][j])) v = fma(P.dt * P.A[i][j], gh[j][c], v);
                 cur[c] = v;
             }
+            if (P.pk) project_pk<C>(S, lc, node, cur);
             double pts[C::PPT][M];
             limit_block(P, B, S, lc, node, own, cur, pts, true, true, false);
         }
@@ -967,6 +990,7 @@ __device__ __forceinline__ void inner_body(const Params &P, const Bufs &B, int b
             }
         }
     }
+    if (P.pk) project_pk<C>(S, lc, node, acc);
     store_node<DIM, N, PHYS>(P, B.ustar, cell, node, active, acc);
 }
 
@@ -1105,6 +1129,7 @@ __device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int b
         }
         u[c] = fma(P.dt, corr, u[c]);
     }
+    if (P.pk) project_pk<C>(S, lc, node, u);
     if (P.mode == MODE_OP_F) {
         store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
         return;
@@ -1139,12 +1164,12 @@ __device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int b
 }
 
 // Resident blocks per SM the FP64 final kernel's register budget is sized for: two of the
-// 2D Q^2 blocks (288 threads).  Unbounded, the owned-box test of the domain decomposition took
-// it from 96 to 126 registers, one resident block, and the 1024^2 Q^2 launch from 4.78 to
-// 6.33 ms.
+// 2D Q^2 blocks (288 threads), five of the 128-thread ones.  Unbounded, the owned-box test of
+// the domain decomposition took the Q^2 kernel from 96 to 126 registers, one resident block,
+// and the 1024^2 Q^2 launch from 4.78 to 6.33 ms.
 template <class C>
 constexpr int fp64_final_min_blocks() {
-    return C::NT > 128 ? 2 : 1;
+    return C::NT > 128 ? 2 : 5;
 }
 
 template <int DIM, int N, int PHYS, bool STORED>
@@ -1169,6 +1194,7 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_limit(Params P, Bufs 
     const bool check = P.mode == MODE_LIMIT_CHECK || P.mode == MODE_LIMIT_FINAL;  // standard RKDG stages
     double u[C::M], pts[C::PPT][C::M];
     load_node<DIM, N, PHYS>(P, B.un, cell, node, active, u);
+    if (P.pk) project_pk<C>(S, lc, node, u);  // a state set in P^k: its L2 projection first
     limit_block(P, B, S, lc, node, own, u, pts, check, check, rate);
     if (rate) {
         double amax = 0.0;

@@ -58,6 +58,10 @@ struct NodalTables {
     // FP32 copies for the split-precision path
     float Dhatf[MAXN][MAXN], lmf[MAXN], lpf[MAXN], liftmf[MAXN], liftpf[MAXN], Iglf[MAXN][MAXN];
     float w1f[MAXN], w2f[MAXN * MAXN];
+    // the L2 projection of Q^k nodal values onto the total-degree space P^k (2D): node b*n+a
+    // from node q, sum over the Legendre modes i + j <= k of L_i(x_a) L_j(x_b) times the
+    // Gauss-rule coefficient of that mode at node q
+    double pk[MAXN * MAXN][MAXN * MAXN];
 };
 
 // FP32 copies of the parameters for the split-precision kernels, rounded once by
@@ -112,6 +116,8 @@ struct Params {
     // 0 off, 1 on; t0 the time of u^n (stage i at t0 + c_i dt), x0, y0 the mesh's lower corner
     int source;
     double t0, x0, y0;
+    // 1: the total-degree space P^k (2D): stage values, u* and u^{n+1} projected (NodalTables::pk)
+    int pk;
 };
 
 // Cells outside the owned box are halo cells (never when own_on is 0).

@@ -58,7 +58,7 @@ class Solver:
     def __init__(self, dim, nx, ny, k, domain, flux, gamma=1.4, velocity=(1.0, 0.0), bounds=(0.0, 1.0),
                  eps=1e-13, bc=("periodic",) * 4, bc_state=None, stream=None, max_halvings=20,
                  precision="fp64", indicator="off", tvb_M=10.0, scheme="compact", theta2="ratio",
-                 source=None):
+                 source=None, basis="Q"):
         self.lib = L.load()
         mesh = L.Mesh()
         mesh.dim, mesh.nx, mesh.ny = dim, nx, ny if dim == 2 else 1
@@ -80,6 +80,7 @@ class Solver:
         opt.scheme = L.SCHEME[scheme]
         opt.theta2 = L.THETA2[theta2]
         opt.source = L.SOURCE[source]
+        opt.basis = L.BASIS[basis]
         if stream is not None:
             opt.cuda_stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
         self.m = dim + 2 if flux == "euler" else 1
