@@ -180,7 +180,10 @@ orc_problem *orc_create(int dim, int nx, int ny, int k, double x0, double x1, do
     return P;
 }
 
-void orc_destroy(orc_problem *P) { free(P); }
+void orc_destroy(orc_problem *P) {
+    if (P) free(P->geo);
+    free(P);
+}
 
 void orc_set_exact(orc_problem *P, orc_exact_fn fn, void *ctx) {
     P->exact = fn;
@@ -196,6 +199,55 @@ void orc_set_scheme(orc_problem *P, int standard) { P->standard = standard ? 1 :
 void orc_set_theta2(orc_problem *P, int exact) { P->theta2_exact = exact ? 1 : 0; }
 void orc_set_source(orc_problem *P, int source) { P->source = source; }
 void orc_set_basis(orc_problem *P, int pk) { P->pk = pk ? 1 : 0; }
+
+/* boundary kind of side s of a cell (ORC_GEO_MESH without a geometry) */
+static int geo_kind(const orc_problem *P, int cell, int s) {
+    return P->geo ? (int)((P->geo[cell] >> (4 * s)) & 15u) : ORC_GEO_MESH;
+}
+
+int orc_is_solid(const orc_problem *P, int cell) {
+    return P->geo && (P->geo[cell] & ORC_GEO_SOLID) ? 1 : 0;
+}
+
+int orc_set_geometry(orc_problem *P, const unsigned *geo, const double *state_a,
+                     const double *state_b, double shock_x0, double shock_speed) {
+    if (!geo) {
+        free(P->geo);
+        P->geo = NULL;
+        return 0;
+    }
+    if (P->dim != 2) return -1;
+    for (int cell = 0; cell < P->ncell; ++cell) {
+        unsigned g = geo[cell];
+        if (g & ~(ORC_GEO_SOLID | 0xFFFFu)) return -1;
+        if (g & ORC_GEO_SOLID) continue;
+        int cx = cell % P->nx, cy = cell / P->nx;
+        for (int s = 0; s < 4; ++s) {
+            int kind = (int)((g >> (4 * s)) & 15u);
+            if (kind > ORC_GEO_SHOCK) return -1;
+            if (kind != ORC_GEO_MESH) continue;
+            /* the mesh neighbour (periodic wrap included) must be a fluid cell */
+            int nb;
+            if (s == 0) nb = cx > 0 ? cell - 1 : (P->bc[0] == ORC_BC_PERIODIC ? cell + P->nx - 1 : -1);
+            else if (s == 1) nb = cx < P->nx - 1 ? cell + 1 : (P->bc[1] == ORC_BC_PERIODIC ? cell - P->nx + 1 : -1);
+            else if (s == 2) nb = cy > 0 ? cell - P->nx : (P->bc[2] == ORC_BC_PERIODIC ? cell + (P->ny - 1) * P->nx : -1);
+            else nb = cy < P->ny - 1 ? cell + P->nx : (P->bc[3] == ORC_BC_PERIODIC ? cell - (P->ny - 1) * P->nx : -1);
+            if (nb >= 0 && (geo[nb] & ORC_GEO_SOLID)) return -1;
+        }
+    }
+    unsigned *copy = (unsigned *)malloc(sizeof(unsigned) * P->ncell);
+    if (!copy) return -1;
+    memcpy(copy, geo, sizeof(unsigned) * P->ncell);
+    free(P->geo);
+    P->geo = copy;
+    for (int comp = 0; comp < ORC_MAXM; ++comp) {
+        P->geo_state[0][comp] = comp < P->m && state_a ? state_a[comp] : 0.0;
+        P->geo_state[1][comp] = comp < P->m && state_b ? state_b[comp] : 0.0;
+    }
+    P->shock_x0 = shock_x0;
+    P->shock_speed = shock_speed;
+    return 0;
+}
 
 /* Scenario I (Example 4.2): S = d_t U + d_x F + d_y G by the chain rule from the primitive
  * fields q in {rho, wx, wy, e} and their partial derivatives in t, x and y. */
@@ -387,6 +439,7 @@ double orc_speed(const orc_problem *P, const double *u, int dir) {
 
 /* neighbour across side s (0 L, 1 R, 2 B, 3 T) or -1 if the side is a boundary */
 static int neighbour(const orc_problem *P, int cell, int s) {
+    if (geo_kind(P, cell, s) != ORC_GEO_MESH) return -1; /* a boundary of the domain's geometry */
     int cx = cell % P->nx, cy = cell / P->nx;
     int nx = P->nx, ny = P->ny;
     switch (s) {
@@ -405,13 +458,30 @@ static int neighbour(const orc_problem *P, int cell, int s) {
     }
 }
 
-/* Exterior state on boundary side s: uin is the interior trace, avg the cell average of
- * the same polynomial.  Outflow takes the cell average (the Lax--Friedrichs flux keeps
- * its dissipation on outflow faces; a constant state is kept exactly). */
-static void exterior_state(const orc_problem *P, int s, const double *uin, const double *avg, double x,
-                           double y, double t, double *uex) {
+/* Exterior state on boundary side s of a cell whose side has the geometry kind `kind`
+ * (ORC_GEO_MESH: the rectangle side's condition bc[s]): uin is the interior trace, avg the
+ * cell average of the same polynomial, (x, y) the face point, t the stage time.  Outflow
+ * takes the cell average (the Lax--Friedrichs flux keeps its dissipation on outflow faces;
+ * a constant state is kept exactly). */
+static void exterior_state(const orc_problem *P, int kind, int s, const double *uin, const double *avg,
+                           double x, double y, double t, double *uex) {
     int m = P->m;
-    switch (P->bc[s]) {
+    int bc = P->bc[s];
+    switch (kind) {
+    case ORC_GEO_WALL: bc = ORC_BC_REFLECT; break;
+    case ORC_GEO_OUTFLOW: bc = ORC_BC_OUTFLOW; break;
+    case ORC_GEO_STATE_A:
+    case ORC_GEO_STATE_B:
+    case ORC_GEO_SHOCK: {
+        /* behind the shock (x < its position at time t) state_a, ahead of it state_b */
+        int which = kind == ORC_GEO_STATE_A ? 0 : kind == ORC_GEO_STATE_B ? 1
+                    : (x < P->shock_x0 + P->shock_speed * t ? 0 : 1);
+        for (int c = 0; c < m; ++c) uex[c] = P->geo_state[which][c];
+        return;
+    }
+    default: break;
+    }
+    switch (bc) {
     case ORC_BC_DIRICHLET:
         for (int c = 0; c < m; ++c) uex[c] = P->bc_state[s][c];
         break;
@@ -452,6 +522,10 @@ void orc_apply(const orc_problem *P, int op, const double *in, double *out, doub
     for (int cell = 0; cell < P->ncell; ++cell) {
         int cx = cell % P->nx, cy = cell / P->nx;
         memset(rhs, 0, sizeof(double) * m * P->nmodes);
+        if (orc_is_solid(P, cell)) { /* outside the domain: no operator */
+            for (int c = 0; c < m; ++c) memset(cell_coef_w(P, out, cell, c), 0, sizeof(double) * P->nmodes);
+            continue;
+        }
         /* volume term: int_K f(u) : grad v */
         for (int r = 0; r < nyq; ++r)
             for (int q = 0; q < n; ++q) {
@@ -506,7 +580,7 @@ void orc_apply(const orc_problem *P, int op, const double *in, double *out, doub
                         double y = P->y0 + (cy + 0.5 * (eta + 1.0)) * hy;
                         double av[ORC_MAXM];
                         for (int c = 0; c < m; ++c) av[c] = cell_coef(P, in, cell, c)[0];
-                        exterior_state(P, s, ui, av, x, y, t, ue);
+                        exterior_state(P, geo_kind(P, cell, s), s, ui, av, x, y, t, ue);
                     }
                     for (int c = 0; c < m; ++c) {
                         uL[q][c] = (s % 2) ? ui[c] : ue[c];
@@ -659,6 +733,10 @@ long long orc_limit(const orc_problem *P, double *c, double *theta_out) {
     double *trial = (double *)malloc(sizeof(double) * orc_state_size(P));
     memcpy(trial, c, sizeof(double) * orc_state_size(P));
     for (int cell = 0; cell < P->ncell; ++cell) {
+        if (orc_is_solid(P, cell)) { /* outside the domain */
+            if (theta_out) theta_out[cell] = 1.0;
+            continue;
+        }
         double theta_rep = 1.0;
         if (P->flux != ORC_FLUX_EULER) {
             double ub = cell_coef(P, c, cell, 0)[0];
@@ -760,6 +838,7 @@ long long orc_limit(const orc_problem *P, double *c, double *theta_out) {
 int orc_averages_admissible(const orc_problem *P, const double *c) {
     int m = P->m;
     for (int cell = 0; cell < P->ncell; ++cell) {
+        if (orc_is_solid(P, cell)) continue;
         double ub[ORC_MAXM];
         for (int comp = 0; comp < m; ++comp) ub[comp] = cell_coef(P, c, cell, comp)[0];
         if (P->flux == ORC_FLUX_EULER) {
@@ -777,7 +856,7 @@ void orc_min_margins(const orc_problem *P, const double *c, double *margins2) {
     int np = sk_points(P, xs, ys);
     double m0 = INFINITY, m1 = INFINITY;
     for (int cell = 0; cell < P->ncell; ++cell)
-        for (int p = 0; p < np; ++p) {
+        for (int p = 0; p < np && !orc_is_solid(P, cell); ++p) {
             double u[ORC_MAXM];
             orc_point_state(P, c, cell, xs[p], ys[p], u);
             double a, b;
@@ -800,7 +879,7 @@ double orc_a0(const orc_problem *P, const double *c) {
     int np = sk_points(P, xs, ys);
     double a0 = 0.0;
     for (int cell = 0; cell < P->ncell; ++cell)
-        for (int p = 0; p < np; ++p) {
+        for (int p = 0; p < np && !orc_is_solid(P, cell); ++p) {
             double u[ORC_MAXM];
             orc_point_state(P, c, cell, xs[p], ys[p], u);
             for (int d = 0; d < P->dim; ++d) {
@@ -820,7 +899,7 @@ double orc_max_dt(const orc_problem *P, const double *c, double cfl) {
     int np = sk_points(P, xs, ys);
     double rate = 0.0;
     for (int cell = 0; cell < P->ncell; ++cell)
-        for (int p = 0; p < np; ++p) {
+        for (int p = 0; p < np && !orc_is_solid(P, cell); ++p) {
             double u[ORC_MAXM];
             orc_point_state(P, c, cell, xs[p], ys[p], u);
             double r = orc_speed(P, u, 0) / P->hx;
@@ -850,7 +929,7 @@ static void neighbour_average(const orc_problem *P, const double *c, int cell, i
     }
     double own[ORC_MAXM];
     for (int comp = 0; comp < m; ++comp) own[comp] = cell_coef(P, c, cell, comp)[0];
-    exterior_state(P, s, own, own, 0.0, 0.0, 0.0, ub);
+    exterior_state(P, geo_kind(P, cell, s), s, own, own, 0.0, 0.0, 0.0, ub);
 }
 
 long long orc_troubled_cells(const orc_problem *P, const double *c, int *flags) {
@@ -858,7 +937,7 @@ long long orc_troubled_cells(const orc_problem *P, const double *c, int *flags) 
     long long count = 0;
     for (int cell = 0; cell < P->ncell; ++cell) {
         int troubled = 0;
-        for (int dir = 0; dir < P->dim && !troubled; ++dir) {
+        for (int dir = 0; dir < P->dim && !troubled && !orc_is_solid(P, cell); ++dir) {
             double h = dir == 0 ? P->hx : P->hy;
             double ulo[ORC_MAXM], uhi[ORC_MAXM];
             neighbour_average(P, c, cell, 2 * dir, ulo);
@@ -1024,9 +1103,10 @@ int orc_step_stages(const orc_problem *P, const double *c, double dt, int s, con
 /* ------------------------------------------------------------------------ */
 
 double orc_total_mass(const orc_problem *P, const double *c, int comp) {
-    /* sum_K |K| ubar_K, summed in cell order */
+    /* sum_K |K| ubar_K over the domain's cells, summed in cell order */
     double s = 0.0;
-    for (int cell = 0; cell < P->ncell; ++cell) s += cell_coef(P, c, cell, comp)[0];
+    for (int cell = 0; cell < P->ncell; ++cell)
+        if (!orc_is_solid(P, cell)) s += cell_coef(P, c, cell, comp)[0];
     return s * P->hx * P->hy;
 }
 

@@ -48,6 +48,9 @@ typedef struct orc_problem {
     int theta2_exact;        /* 1: theta_2 from the exact per-point solve (see orc_set_theta2) */
     int source;              /* 1: the manufactured source of scenario I (see orc_set_source) */
     int pk;                  /* 1: the total-degree space P^k in 2D (see orc_set_basis) */
+    unsigned *geo;           /* non-rectangular domain (see orc_set_geometry) or NULL */
+    double geo_state[2][ORC_MAXM];
+    double shock_x0, shock_speed;
     double tvb_M;            /* TVB constant of the indicator */
     int max_halvings;
     orc_exact_fn exact;
@@ -98,6 +101,22 @@ void orc_set_source(orc_problem *P, int source);
  * modes i + j <= k and has the others zero (Sec. 4.2 tests both spaces) */
 void orc_set_basis(orc_problem *P, int pk);
 /* the source of scenario I at (x, y, t), m = 4 components */
+/* Non-rectangular domains (Examples 4.8 and 4.9): the domain is a union of mesh cells of the
+ * bounding rectangle.  geo[cell] holds, in bits 4s..4s+3, the boundary kind of side s
+ * (0 left, 1 right, 2 bottom, 3 top) and, in bit 16, whether the cell is solid.  Kinds:
+ * ORC_GEO_MESH the mesh rule (the neighbouring cell, or the rectangle side's condition),
+ * ORC_GEO_WALL reflective, ORC_GEO_OUTFLOW outflow, ORC_GEO_STATE_A / _B the fixed state
+ * state_a / state_b, ORC_GEO_SHOCK state_a at face points with x < shock_x0 + shock_speed t
+ * and state_b elsewhere (a planar shock's exact trace on a boundary).  Solid cells take no
+ * part: their operators are zero and they count in no test, rate or total.  Every side of a
+ * fluid cell that faces a solid cell must carry a kind other than ORC_GEO_MESH.  Returns 0,
+ * or -1 (geometry unchanged) on a bad word.  geo is copied; NULL removes the geometry. */
+enum { ORC_GEO_MESH = 0, ORC_GEO_WALL = 1, ORC_GEO_OUTFLOW = 2, ORC_GEO_STATE_A = 3,
+       ORC_GEO_STATE_B = 4, ORC_GEO_SHOCK = 5 };
+#define ORC_GEO_SOLID 0x10000u
+int orc_set_geometry(orc_problem *P, const unsigned *geo, const double *state_a,
+                     const double *state_b, double shock_x0, double shock_speed);
+int orc_is_solid(const orc_problem *P, int cell);
 void orc_scenario1_source(double gamma, double x, double y, double t, double *S);
 size_t orc_state_size(const orc_problem *P); /* doubles: ncell*m*n^dim */
 

@@ -83,6 +83,10 @@ def _load():
     lib.orc_set_theta2.argtypes = [V, C.c_int]
     lib.orc_set_source.argtypes = [V, C.c_int]
     lib.orc_set_basis.argtypes = [V, C.c_int]
+    lib.orc_set_geometry.argtypes = [V, C.POINTER(C.c_uint), _dp, _dp, C.c_double, C.c_double]
+    lib.orc_set_geometry.restype = C.c_int
+    lib.orc_is_solid.argtypes = [V, C.c_int]
+    lib.orc_is_solid.restype = C.c_int
     lib.orc_scenario1_source.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double)]
     lib.orc_state_size.argtypes = [V]
     lib.orc_state_size.restype = C.c_size_t
@@ -233,6 +237,28 @@ class Oracle:
 
     def get_state(self) -> np.ndarray:
         return self.to_nodal()
+
+    def set_geometry(self, geo, state_a=None, state_b=None, shock_x0=0.0, shock_speed=0.0):
+        """Non-rectangular domain (Examples 4.8, 4.9): per-cell words of boundary kinds and
+        the solid bit (see orc_set_geometry); None removes it.  Raises on a bad word."""
+        if geo is None:
+            self.lib.orc_set_geometry(self.h, None, None, None, 0.0, 0.0)
+            self._geo = None
+            return
+        g = np.ascontiguousarray(np.asarray(geo, dtype=np.uint32).reshape(-1))
+        if g.size != self.nx * self.ny:
+            raise ValueError("oracle: geometry needs one word per cell")
+        sa = np.zeros(4)
+        sb = np.zeros(4)
+        if state_a is not None:
+            sa[: len(state_a)] = state_a
+        if state_b is not None:
+            sb[: len(state_b)] = state_b
+        rc = self.lib.orc_set_geometry(self.h, g.ctypes.data_as(C.POINTER(C.c_uint)), _p(sa), _p(sb),
+                                       float(shock_x0), float(shock_speed))
+        if rc != 0:
+            raise ValueError("oracle: bad geometry word")
+        self._geo = g
 
     def averages(self, modal=None) -> np.ndarray:
         modal = self.c if modal is None else modal

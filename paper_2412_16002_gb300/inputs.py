@@ -16,6 +16,9 @@ Workloads (the paper's analytic initial data; there are no datasets):
   * ``riemann_quadrants`` seeded 2D four-quadrant Riemann problems on [0,1]^2
   * ``random_euler`` / ``random_scalar``  seeded admissible states with
                           zero-mean oscillations for operator and limiter parity
+  * ``shock_diffraction`` 2D Euler, Example 4.8: Mach 5.09 shock past a step corner
+  * ``double_mach``       2D Euler, Example 4.9: Mach 10 shock at 60 degrees reflecting
+                          off a wall and diffracting at its corner
 """
 from __future__ import annotations
 
@@ -75,6 +78,11 @@ class Workload:
     cfl: float = 0.1
     t_end: float = 0.0
     tableau: str = "heun3"
+    # non-rectangular domains: one geometry word per cell (GEO_* below) or None, the two
+    # fixed states the words refer to, and the moving shock line x_s(t) = shock[0] + shock[1] t
+    geo: np.ndarray | None = None
+    geo_states: tuple = ()
+    shock: tuple = (0.0, 0.0)
 
     @property
     def m(self):
@@ -258,3 +266,125 @@ def random_scalar(dim, nx, ny, k, seed, lo=-0.5, hi=1.5, osc=0.6):
         cells = (ny, nx)
     u = u + osc * half * _zero_mean(rng, cells, k, dim)
     return np.ascontiguousarray(u[None])
+
+
+# ----------------------------------------------------------------- non-rectangular domains
+# Geometry words (one uint32 per cell of the bounding rectangle): bits 4s..4s+3 hold the
+# boundary kind of side s (0 left, 1 right, 2 bottom, 3 top), bit 16 marks a solid cell.
+# Kinds: the mesh rule (neighbouring cell or the rectangle side's condition), reflective
+# wall, outflow, fixed state A, fixed state B, and the moving planar shock (state A behind
+# the line x < x_s(t), state B ahead of it).
+GEO_MESH, GEO_WALL, GEO_OUTFLOW, GEO_STATE_A, GEO_STATE_B, GEO_SHOCK = range(6)
+GEO_SOLID = 1 << 16
+
+
+def geo_word(left=GEO_MESH, right=GEO_MESH, bottom=GEO_MESH, top=GEO_MESH, solid=False):
+    return (left | right << 4 | bottom << 8 | top << 12) | (GEO_SOLID if solid else 0)
+
+
+def normal_shock(mach, rho1, p1, gamma=GAMMA):
+    """A shock of Mach number `mach` running into gas at rest (rho1, p1): the post-shock
+    density, normal velocity and pressure from the normal-shock (Rankine-Hugoniot) relations,
+    and the shock speed."""
+    c1 = math.sqrt(gamma * p1 / rho1)
+    s = mach * c1
+    m2 = mach * mach
+    rho2 = rho1 * (gamma + 1.0) * m2 / ((gamma - 1.0) * m2 + 2.0)
+    p2 = p1 * (1.0 + 2.0 * gamma / (gamma + 1.0) * (m2 - 1.0))
+    u2 = s * (1.0 - rho1 / rho2)
+    return rho2, u2, p2, s
+
+
+def _mark_solid_faces(geo, solid):
+    """Put a reflective wall on every side of a fluid cell that faces a solid cell (the
+    callers then overwrite the segments that carry other data)."""
+    ny, nx = solid.shape
+    fluid = ~solid
+    w = geo.reshape(ny, nx)
+    lft = np.zeros_like(solid)
+    lft[:, 1:] = solid[:, :-1]
+    rgt = np.zeros_like(solid)
+    rgt[:, :-1] = solid[:, 1:]
+    bot = np.zeros_like(solid)
+    bot[1:, :] = solid[:-1, :]
+    top = np.zeros_like(solid)
+    top[:-1, :] = solid[1:, :]
+    for mask, side in ((lft, 0), (rgt, 1), (bot, 2), (top, 3)):
+        sel = mask & fluid
+        w[sel] = (w[sel] & ~np.uint32(15 << (4 * side))) | np.uint32(GEO_WALL << (4 * side))
+    w[solid] |= np.uint32(GEO_SOLID)
+
+
+def shock_diffraction(cells_per_unit=64, k=2, cfl=None, t_end=2.3, gamma=GAMMA):
+    """Example 4.8: the union of [0,1]x[6,12] and [1,13]x[0,12] on the bounding rectangle
+    [0,13]x[0,12] (the solid step [0,1]x[0,6] masked); a right-moving Mach 5.09 shock at
+    x = 0.5 running into rho = 1.4, p = 1 at rest; inflow (the post-shock state) on the left,
+    outflow on the top, right and bottom, reflective walls y = 6 (x <= 1) and x = 1 (y <= 6).
+    Square cells of side 1 / cells_per_unit; solid cells hold the ambient state."""
+    nx, ny = 13 * cells_per_unit, 12 * cells_per_unit
+    dom = (0.0, 13.0, 0.0, 12.0)
+    h = 1.0 / cells_per_unit
+    rho2, u2, p2, _ = normal_shock(5.09, 1.4, 1.0, gamma)
+    post = prim_to_cons(np.array(rho2), (u2, 0.0), np.array(p2), gamma)
+    pre = prim_to_cons(np.array(1.4), (0.0, 0.0), np.array(1.0), gamma)
+    xc = (np.arange(nx) + 0.5) * h
+    yc = (np.arange(ny) + 0.5) * h
+    solid = (yc[:, None] < 6.0) & (xc[None, :] < 1.0)
+    geo = np.zeros(ny * nx, dtype=np.uint32)
+    _mark_solid_faces(geo, solid)
+    X, _ = node_coords(2, nx, ny, k, dom)
+    behind = X < 0.5
+    U = np.where(behind[None], post.reshape(4, 1, 1, 1, 1), pre.reshape(4, 1, 1, 1, 1))
+    U = np.ascontiguousarray(U * np.ones((4, ny, nx, k + 1, k + 1)))
+    U[:, solid] = pre.reshape(4, 1, 1, 1)
+    if cfl is None:
+        cfl = {1: 0.3, 2: 0.178, 3: 0.103}[k]
+    return Workload(f"shock_diffraction_q{k}", 2, nx, ny, k, dom, "euler",
+                    ("dirichlet", "outflow", "outflow", "outflow"), U, gamma=gamma, eps=1e-13,
+                    bc_state={0: post.tolist()}, cfl=cfl, t_end=t_end,
+                    tableau={1: "midpoint2", 2: "heun3", 3: "rk4"}[k], geo=geo,
+                    geo_states=(post.tolist(), pre.tolist()))
+
+
+def double_mach(cells_per_unit=360, k=3, cfl=None, t_end=0.2, gamma=GAMMA):
+    """Example 4.9: the union of [1,4]x[-1,0] and [0,4]x[0,1] on the bounding rectangle
+    [0,4]x[-1,1] (the solid block [0,1]x[-1,0] masked); a Mach 10 shock through (1/6, 0) at
+    60 degrees to the x-axis running into rho = 1.4, p = 1 at rest, post-shock state
+    rho = 8, w = (4.125 sqrt 3, -4.125), p = 116.5.  Inflow (post-shock) on the left, outflow
+    on the right and the bottom, the post-shock state on y = 0 for x < 1/6, reflective walls
+    y = 0 (1/6 <= x <= 1) and x = 1 (y <= 0), and on the top side the exact shock motion:
+    post-shock where x < 1/6 + (1 + 20 t)/sqrt 3.  Solid cells hold the ambient state."""
+    nx, ny = 4 * cells_per_unit, 2 * cells_per_unit
+    dom = (0.0, 4.0, -1.0, 1.0)
+    h = 1.0 / cells_per_unit
+    angle = math.pi / 3.0
+    rho2, u2, p2, s = normal_shock(10.0, 1.4, 1.0, gamma)
+    wx, wy = u2 * math.sin(angle), -u2 * math.cos(angle)  # along the shock's normal
+    post = prim_to_cons(np.array(rho2), (wx, wy), np.array(p2), gamma)
+    pre = prim_to_cons(np.array(1.4), (0.0, 0.0), np.array(1.0), gamma)
+    xc = (np.arange(nx) + 0.5) * h
+    yc = -1.0 + (np.arange(ny) + 0.5) * h
+    solid = (yc[:, None] < 0.0) & (xc[None, :] < 1.0)
+    geo = np.zeros(ny * nx, dtype=np.uint32)
+    _mark_solid_faces(geo, solid)
+    w = geo.reshape(ny, nx)
+    # y = 0, x < 1/6: the fixed post-shock state on the wall's leading part
+    row0 = cells_per_unit  # the first fluid row above y = 0
+    lead = xc < 1.0 / 6.0
+    w[row0, lead] = (w[row0, lead] & ~np.uint32(15 << 8)) | np.uint32(GEO_STATE_A << 8)
+    # the top side follows the shock: it meets y = 1 at x_s(t) = x_s0 + (s / sin 60) t
+    x_s0 = 1.0 / 6.0 + 1.0 / math.tan(angle)
+    speed = s / math.sin(angle)
+    w[ny - 1, :] = (w[ny - 1, :] & ~np.uint32(15 << 12)) | np.uint32(GEO_SHOCK << 12)
+    X, Y = node_coords(2, nx, ny, k, dom)
+    behind = X < 1.0 / 6.0 + Y / math.tan(angle)
+    U = np.where(behind[None], post.reshape(4, 1, 1, 1, 1), pre.reshape(4, 1, 1, 1, 1))
+    U = np.ascontiguousarray(U * np.ones((4, ny, nx, k + 1, k + 1)))
+    U[:, solid] = pre.reshape(4, 1, 1, 1)
+    if cfl is None:
+        cfl = {1: 0.3, 2: 0.178, 3: 0.103}[k]
+    return Workload(f"double_mach_q{k}", 2, nx, ny, k, dom, "euler",
+                    ("dirichlet", "outflow", "outflow", "outflow"), U, gamma=gamma, eps=1e-13,
+                    bc_state={0: post.tolist()}, cfl=cfl, t_end=t_end,
+                    tableau={1: "midpoint2", 2: "heun3", 3: "rk4"}[k], geo=geo,
+                    geo_states=(post.tolist(), pre.tolist()), shock=(x_s0, speed))
