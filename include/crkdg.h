@@ -208,7 +208,8 @@ crkdg_status crkdg_get_state(crkdg_t h, double *nodal, size_t count, int on_devi
 
 /* The time of the current state: 0 for a new handle, set by crkdg_set_time (or by the t of
  * crkdg_advance / crkdg_advance_fixed), increased by the dt of every accepted step.  Only a
- * time-dependent source (crkdg_options.source) reads it. */
+ * time-dependent source (crkdg_options.source) and the moving shock boundary of a
+ * non-rectangular domain (crkdg_set_geometry) read it. */
 crkdg_status crkdg_set_time(crkdg_t h, double t);
 crkdg_status crkdg_get_time(crkdg_t h, double *t);
 
@@ -351,6 +352,40 @@ size_t crkdg_state_size(crkdg_t h);
  * this loop on one handle. */
 crkdg_status crkdg_step_attempt(crkdg_t h, double dt, const crkdg_tableau *tab, int *violated);
 crkdg_status crkdg_step_accept(crkdg_t h, crkdg_step_info *info);
+
+/* ------------------------------------------------------------------------
+ * Non-rectangular domains (Sec. 4.4, Examples 4.8 and 4.9: the shock diffraction
+ * on [0,1]x[6,12] U [1,13]x[0,12] and the double Mach reflection on
+ * [1,4]x[-1,0] U [0,4]x[0,1]).  The domain is a union of the mesh's cells: the
+ * cells of the bounding rectangle outside it are solid.  geo holds one word per
+ * cell (host memory, cell order cy * nx + cx, copied into device memory owned
+ * by h): bits 4s..4s+3 the boundary kind of side s (0 left, 1 right, 2 bottom,
+ * 3 top), bit 16 (CRKDG_GEO_SOLID) a solid cell.  Kinds:
+ *   CRKDG_GEO_MESH     the mesh rule: the neighbouring cell, or on the
+ *                      rectangle's sides their crkdg_mesh condition;
+ *   CRKDG_GEO_WALL     reflective (the interior trace with the normal momentum
+ *                      negated);
+ *   CRKDG_GEO_OUTFLOW  outflow (the cell average of the same stage value);
+ *   CRKDG_GEO_STATE_A, CRKDG_GEO_STATE_B  the fixed state state_a / state_b
+ *                      (m doubles each, conservative; nullable: zeros);
+ *   CRKDG_GEO_SHOCK    a planar shock's exact trace: state_a at face points with
+ *                      x < shock_x0 + shock_speed t, state_b elsewhere, t the
+ *                      stage time t^n + c_i dt (crkdg_set_time; advanced by
+ *                      every accepted step), as on Example 4.9's top side.
+ * Solid cells keep their state (their operators are zero) and count in no
+ * admissibility test, limiter statistic, trial-step rate, bound margin or
+ * crkdg_total_mass; crkdg_step_info.mass_drift still divides by the totals
+ * over every cell.  Every side of a fluid cell that faces a solid cell through
+ * the mesh rule must carry another kind.  geo NULL removes the geometry.
+ * 2D, FP64, the compact scheme, no indicator, no subdomain
+ * (CRKDG_E_UNSUPPORTED otherwise); CRKDG_E_ARG for unknown bits or kinds, an
+ * open side facing a solid cell, or a non-finite shock line (the geometry is
+ * then unchanged). */
+enum { CRKDG_GEO_MESH = 0, CRKDG_GEO_WALL = 1, CRKDG_GEO_OUTFLOW = 2, CRKDG_GEO_STATE_A = 3,
+       CRKDG_GEO_STATE_B = 4, CRKDG_GEO_SHOCK = 5 };
+#define CRKDG_GEO_SOLID 0x10000u
+crkdg_status crkdg_set_geometry(crkdg_t h, const unsigned *geo, const double *state_a, const double *state_b,
+                                double shock_x0, double shock_speed);
 
 /* ------------------------------------------------------------------------
  * Subdomains of a block-decomposed mesh (multi-GPU; Sec. 1 and the Compactness

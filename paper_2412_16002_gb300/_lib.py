@@ -109,6 +109,7 @@ SYMBOLS = {
     "crkdg_step_attempt": (C.c_int, [_H, C.c_double, C.POINTER(Tableau), C.POINTER(C.c_int)]),
     "crkdg_step_accept": (C.c_int, [_H, C.POINTER(StepInfo)]),
     "crkdg_set_subdomain": (C.c_int, [_H, C.POINTER(Mesh), C.c_int, C.c_int, C.c_int, C.c_int]),
+    "crkdg_set_geometry": (C.c_int, [_H, C.POINTER(C.c_uint), _dp, _dp, C.c_double, C.c_double]),
     "crkdg_cells_bytes": (C.c_size_t, [_H, C.c_longlong]),
     "crkdg_pack_cells": (C.c_int, [_H, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_int]),
     "crkdg_unpack_cells": (C.c_int, [_H, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_int]),

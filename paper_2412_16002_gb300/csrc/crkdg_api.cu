@@ -7,6 +7,7 @@
 
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/crkdg.h"
 #include "dg_types.h"
@@ -263,6 +264,10 @@ struct crkdg_ctx {
     double *mass_part = nullptr;  // block sums of the component totals
     double mass_n[MAXM] = {};     // component totals of u^n (valid when mass_valid)
     bool mass_valid = false;
+    unsigned *geo = nullptr;          // geometry words of a non-rectangular domain (device)
+    std::vector<unsigned> geo_host;   // their host copy (solid cells of the totals)
+    double gstate[2][MAXM] = {};
+    double shock_x0 = 0.0, shock_speed = 0.0;
     std::string err;
 };
 
@@ -310,6 +315,11 @@ Params base_params(const crkdg_ctx *h) {
     P.x0 = h->mesh.x0;
     P.y0 = h->mesh.y0;
     P.pk = (h->opt.basis == CRKDG_BASIS_P && h->dim == 2) ? 1 : 0;
+    P.geo = h->geo;
+    for (int w = 0; w < 2; ++w)
+        for (int c = 0; c < MAXM; ++c) P.gstate[w][c] = h->gstate[w][c];
+    P.shock_x0 = h->shock_x0;
+    P.shock_speed = h->shock_speed;
     for (int i = 0; i < MAXS; ++i) P.slot[i] = -1;
     return P;
 }
@@ -707,6 +717,7 @@ crkdg_status crkdg_destroy(crkdg_t h) {
     cudaFree(h->u);
     cudaFree(h->unew);
     cudaFree(h->ustar);
+    cudaFree(h->geo);
     cudaFree(h->tr);
     cudaFree(h->aux);
     cudaFree(h->mass_part);
@@ -1469,12 +1480,71 @@ crkdg_status crkdg_total_mass(crkdg_t h, int comp, double *mass) {
             delete[] host;
             return s;
         }
-        double acc = 0.0;  // fixed cell order: deterministic
-        for (int c = 0; c < h->ncell; ++c) acc += host[(size_t)c * h->m + comp];
+        double acc = 0.0;  // fixed cell order: deterministic; cells of the domain only
+        const bool geo = !h->geo_host.empty();
+        for (int c = 0; c < h->ncell; ++c)
+            if (!geo || !(h->geo_host[c] & GEO_SOLID)) acc += host[(size_t)c * h->m + comp];
         delete[] host;
         double hx = (h->mesh.x1 - h->mesh.x0) / h->mesh.nx;
         double hy = h->dim == 2 ? (h->mesh.y1 - h->mesh.y0) / h->mesh.ny : 1.0;
         *mass = acc * hx * hy;
+        return CRKDG_OK;
+    } catch (...) {
+        return CRKDG_E_OOM;
+    }
+}
+
+// ---------------------------------------------------------------- non-rectangular domains
+
+crkdg_status crkdg_set_geometry(crkdg_t h, const unsigned *geo, const double *state_a, const double *state_b,
+                                double shock_x0, double shock_speed) {
+    if (!h) return CRKDG_E_ARG;
+    try {
+        if (!geo) {
+            if (h->geo) CK(h, cudaFree(h->geo));
+            h->geo = nullptr;
+            h->geo_host.clear();
+            h->a0_valid = false;
+            return CRKDG_OK;
+        }
+        if (h->dim != 2) return fail(h, CRKDG_E_UNSUPPORTED, "set_geometry: 2D meshes only");
+        if (h->mixed || h->opt.scheme != CRKDG_SCHEME_COMPACT || h->opt.indicator != CRKDG_IND_OFF || h->own_on)
+            return fail(h, CRKDG_E_UNSUPPORTED,
+                        "set_geometry: FP64, the compact scheme, no indicator, no subdomain");
+        if (!(isfinite(shock_x0) && isfinite(shock_speed)))
+            return fail(h, CRKDG_E_ARG, "set_geometry: the shock line must be finite");
+        const int nx = h->mesh.nx, ny = h->mesh.ny;
+        auto solid = [&](int cell) { return (geo[cell] & GEO_SOLID) != 0u; };
+        for (int cell = 0; cell < h->ncell; ++cell) {
+            const unsigned g = geo[cell];
+            if (g & ~(GEO_SOLID | 0xFFFFu)) return fail(h, CRKDG_E_ARG, "set_geometry: unknown bits in a word");
+            if (solid(cell)) continue;
+            const int cx = cell % nx, cy = cell / nx;
+            for (int s = 0; s < 4; ++s) {
+                const unsigned kind = (g >> (4 * s)) & 15u;
+                if (kind > GEO_SHOCK) return fail(h, CRKDG_E_ARG, "set_geometry: unknown boundary kind");
+                if (kind != GEO_MESH) continue;
+                int nb;
+                const int *bc = h->mesh.bc;
+                if (s == 0) nb = cx > 0 ? cell - 1 : (bc[0] == CRKDG_BC_PERIODIC ? cell + nx - 1 : -1);
+                else if (s == 1) nb = cx < nx - 1 ? cell + 1 : (bc[1] == CRKDG_BC_PERIODIC ? cell - nx + 1 : -1);
+                else if (s == 2) nb = cy > 0 ? cell - nx : (bc[2] == CRKDG_BC_PERIODIC ? cell + (ny - 1) * nx : -1);
+                else nb = cy < ny - 1 ? cell + nx : (bc[3] == CRKDG_BC_PERIODIC ? cell - (ny - 1) * nx : -1);
+                if (nb >= 0 && solid(nb))
+                    return fail(h, CRKDG_E_ARG, "set_geometry: a fluid side faces a solid cell without a boundary kind");
+            }
+        }
+        if (!h->geo) CK(h, cudaMalloc(&h->geo, sizeof(unsigned) * h->ncell));
+        CK(h, cudaMemcpyAsync(h->geo, geo, sizeof(unsigned) * h->ncell, cudaMemcpyHostToDevice, h->st));
+        CK(h, cudaStreamSynchronize(h->st));
+        h->geo_host.assign(geo, geo + h->ncell);
+        for (int c = 0; c < MAXM; ++c) {
+            h->gstate[0][c] = state_a && c < h->m ? state_a[c] : 0.0;
+            h->gstate[1][c] = state_b && c < h->m ? state_b[c] : 0.0;
+        }
+        h->shock_x0 = shock_x0;
+        h->shock_speed = shock_speed;
+        h->a0_valid = false;
         return CRKDG_OK;
     } catch (...) {
         return CRKDG_E_OOM;
@@ -1493,6 +1563,7 @@ crkdg_status crkdg_set_subdomain(crkdg_t h, const crkdg_mesh *global, int i0, in
         return fail(h, CRKDG_E_ARG, "set_subdomain: need 0 <= i0 < i1 <= nx and 0 <= j0 < j1 <= ny");
     if (h->opt.indicator != CRKDG_IND_OFF)
         return fail(h, CRKDG_E_UNSUPPORTED, "set_subdomain: the troubled-cell indicators need a second exchange");
+    if (h->geo) return fail(h, CRKDG_E_UNSUPPORTED, "set_subdomain: not with a non-rectangular domain");
     double rhx = 0.0, rhy = 0.0;
     if (global) {
         if (global->dim != h->dim || global->nx < 1 || (h->dim == 2 && global->ny < 1) ||

@@ -323,14 +323,50 @@ __device__ __forceinline__ void exterior_state(const Params &P, int side, const 
     }
 }
 
-// neighbour across side (0 L, 1 R, 2 B, 3 T), or -1 on a non-periodic boundary
+// neighbour across side (0 L, 1 R, 2 B, 3 T), or -1 on a non-periodic boundary or a side
+// that a non-rectangular domain's geometry word gives a boundary kind
 __device__ __forceinline__ int neighbour(const Params &P, int cell, int side) {
+    if (P.geo != nullptr && ((P.geo[cell] >> (4 * side)) & 15u) != GEO_MESH) return -1;
     int cx = cell % P.nx, cy = cell / P.nx;
     switch (side) {
     case 0: return cx > 0 ? cell - 1 : (P.bc[0] == BC_PERIODIC ? cell + P.nx - 1 : -1);
     case 1: return cx < P.nx - 1 ? cell + 1 : (P.bc[1] == BC_PERIODIC ? cell - P.nx + 1 : -1);
     case 2: return cy > 0 ? cell - P.nx : (P.bc[2] == BC_PERIODIC ? cell + (P.ny - 1) * P.nx : -1);
     default: return cy < P.ny - 1 ? cell + P.nx : (P.bc[3] == BC_PERIODIC ? cell - (P.ny - 1) * P.nx : -1);
+    }
+}
+
+// Exterior trace of a boundary face point of a non-rectangular domain (Examples 4.8, 4.9) in
+// the final stage: the side's kind in the cell's geometry word decides.  pos is the face
+// point's index along the face, stage the traced stage (its time t0 + c_i dt moves the
+// shock line); kind GEO_MESH falls back to the rectangle side's condition.
+template <int PHYS, int DIM, int N>
+__device__ __forceinline__ void geo_exterior(const Params &P, int cell, int side, int pos, int stage,
+                                             const double *ui, const double *avg, double *ue) {
+    constexpr int M = ncomp(PHYS, DIM);
+    const unsigned kind = (P.geo[cell] >> (4 * side)) & 15u;
+    if (kind == GEO_STATE_A || kind == GEO_STATE_B || kind == GEO_SHOCK) {
+        int which = kind == GEO_STATE_B ? 1 : 0;
+        if (kind == GEO_SHOCK) {
+            const NodalTables &T = c_tab[N - 2];
+            const int cx = cell % P.nx;
+            const double xi = side == 0 ? -1.0 : side == 1 ? 1.0 : T.xg[pos];
+            const double x = P.x0 + (cx + 0.5 * (xi + 1.0)) * (2.0 / P.rhx);
+            double ci = 0.0;
+            for (int j = 0; j < stage; ++j) ci += P.A[stage][j];
+            which = x < P.shock_x0 + P.shock_speed * (P.t0 + ci * P.dt) ? 0 : 1;
+        }
+#pragma unroll
+        for (int c = 0; c < M; ++c) ue[c] = P.gstate[which][c];
+    } else if (kind == GEO_WALL) {
+#pragma unroll
+        for (int c = 0; c < M; ++c) ue[c] = ui[c];
+        if constexpr (PHYS == PH_EULER) ue[1 + side / 2] = -ui[1 + side / 2];
+    } else if (kind == GEO_OUTFLOW) {
+#pragma unroll
+        for (int c = 0; c < M; ++c) ue[c] = avg[c];
+    } else {
+        exterior_state<PHYS, DIM>(P, side, ui, avg, ue);
     }
 }
 
@@ -933,7 +969,7 @@ __device__ __forceinline__ void inner_body(const Params &P, const Bufs &B, int b
     const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
     const int cell = blk * C::NCB + lc;
     const bool active = cell < P.ncell;
-    const bool own = active && owned(P, cell);  // counts in the flag and statistics
+    const bool own = active && owned(P, cell) && !solid_cell(P, cell);  // counts in the flag and statistics
     double un[M], cur[M], acc[M], gh[MAXS][M];
     load_node<DIM, N, PHYS>(P, B.un, cell, node, active, un);
 #pragma unroll
@@ -991,6 +1027,9 @@ __device__ __forceinline__ void inner_body(const Params &P, const Bufs &B, int b
         }
     }
     if (P.pk) project_pk<C>(S, lc, node, acc);
+    if (active && solid_cell(P, cell))  // outside the domain: G = 0, u* = u^n
+#pragma unroll
+        for (int c = 0; c < M; ++c) acc[c] = P.mode == MODE_OP_G ? 0.0 : un[c];
     store_node<DIM, N, PHYS>(P, B.ustar, cell, node, active, acc);
 }
 
@@ -1012,7 +1051,7 @@ __device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int b
     const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
     const int cell = blk * C::NCB + lc;
     const bool active = cell < P.ncell;
-    const bool own = active && owned(P, cell);  // counts in the flag, statistics and rate
+    const bool own = active && owned(P, cell) && !solid_cell(P, cell);  // counts in the flag, statistics and rate
     const int a = node % N, b = DIM == 2 ? node / N : 0;
     double u[M];
     load_node<DIM, N, PHYS>(P, B.ustar, cell, node, active, u);
@@ -1050,7 +1089,10 @@ __device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int b
                     double av[M];
 #pragma unroll
                     for (int c = 0; c < M; ++c) av[c] = B.tavg[((size_t)P.slot[i] * M + c) * P.ncell + cell];
-                    exterior_state<PHYS, DIM>(P, face, ui[j], av, ue[j]);
+                    if (P.geo != nullptr)
+                        geo_exterior<PHYS, DIM, N>(P, cell, face, pos, i, ui[j], av, ue[j]);
+                    else
+                        exterior_state<PHYS, DIM>(P, face, ui[j], av, ue[j]);
                 }
                 int dir = face >> 1;
                 double sI, sE;
@@ -1131,6 +1173,9 @@ __device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int b
     }
     if (P.pk) project_pk<C>(S, lc, node, u);
     if (P.mode == MODE_OP_F) {
+        if (active && solid_cell(P, cell))  // outside the domain: no operator
+#pragma unroll
+            for (int c = 0; c < M; ++c) u[c] = 0.0;
         store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
         return;
     }
@@ -1160,6 +1205,7 @@ __device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int b
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) abits = umax64(abits, __shfl_xor_sync(0xffffffffu, abits, o));
     if ((threadIdx.x & 31) == 0 && abits > 0ull) atomicMax(B.a0, abits);
+    if (active && solid_cell(P, cell)) load_node<DIM, N, PHYS>(P, B.un, cell, node, true, u);  // keeps u^n
     store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
 }
 
@@ -1189,7 +1235,7 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_limit(Params P, Bufs 
     const int lc = threadIdx.x / C::NN, node = threadIdx.x - lc * C::NN;
     const int cell = blockIdx.x * C::NCB + lc;
     const bool active = cell < P.ncell;
-    const bool own = active && owned(P, cell);
+    const bool own = active && owned(P, cell) && !solid_cell(P, cell);
     const bool rate = P.mode == MODE_RATE || P.mode == MODE_LIMIT_FINAL;
     const bool check = P.mode == MODE_LIMIT_CHECK || P.mode == MODE_LIMIT_FINAL;  // standard RKDG stages
     double u[C::M], pts[C::PPT][C::M];
@@ -1208,6 +1254,7 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_limit(Params P, Bufs 
         for (int o = 16; o > 0; o >>= 1) abits = umax64(abits, __shfl_xor_sync(0xffffffffu, abits, o));
         if ((threadIdx.x & 31) == 0 && abits > 0ull) atomicMax(B.a0, abits);
     }
+    if (active && solid_cell(P, cell)) load_node<DIM, N, PHYS>(P, B.un, cell, node, true, u);  // not limited
     store_node<DIM, N, PHYS>(P, B.unew, cell, node, active, u);
 }
 
@@ -1220,7 +1267,7 @@ __global__ void __launch_bounds__(Cfg<DIM, N, PHYS>::NT) k_scan(Params P, Bufs B
     const int lc = threadIdx.x / NN, node = threadIdx.x - lc * NN;
     const int cell = blockIdx.x * C::NCB + lc;
     const bool active = cell < P.ncell;
-    const bool own = active && owned(P, cell);
+    const bool own = active && owned(P, cell) && !solid_cell(P, cell);
     double u[M];
     load_node<DIM, N, PHYS>(P, B.un, cell, node, active, u);
 #pragma unroll

@@ -118,7 +118,24 @@ struct Params {
     double t0, x0, y0;
     // 1: the total-degree space P^k (2D): stage values, u* and u^{n+1} projected (NodalTables::pk)
     int pk;
+    // Non-rectangular domain (Examples 4.8 and 4.9) or null: one word per cell (device memory),
+    // bits 4s..4s+3 the boundary kind of side s (GEO_*), GEO_SOLID a cell outside the domain.
+    // Solid cells keep u^n (their operators are zero) and count in no test, statistic or rate.
+    const unsigned *geo;
+    double gstate[2][MAXM];          // the fixed states A and B of the GEO_STATE_* / GEO_SHOCK kinds
+    double shock_x0, shock_speed;    // GEO_SHOCK: state A where x < shock_x0 + shock_speed t
 };
+
+// Boundary kinds of a side in a geometry word: the mesh rule (the neighbouring cell, or the
+// rectangle side's condition), reflective wall, outflow, fixed state A, fixed state B, and a
+// planar shock's exact trace (state A behind x_s(t) = shock_x0 + shock_speed t, B ahead).
+enum GeoKind { GEO_MESH = 0, GEO_WALL = 1, GEO_OUTFLOW = 2, GEO_STATE_A = 3, GEO_STATE_B = 4, GEO_SHOCK = 5 };
+constexpr unsigned GEO_SOLID = 0x10000u;
+
+// A cell outside a non-rectangular domain (device side; never without a geometry).
+__device__ __forceinline__ bool solid_cell(const Params &P, int cell) {
+    return P.geo != nullptr && (P.geo[cell] & GEO_SOLID) != 0u;
+}
 
 // Cells outside the owned box are halo cells (never when own_on is 0).
 __host__ __device__ __forceinline__ bool owned(const Params &P, int cell) {

@@ -94,8 +94,26 @@ class Solver:
 
     @classmethod
     def from_workload(cls, wl, **kw):
-        return cls(wl.dim, wl.nx, wl.ny, wl.k, wl.domain, wl.flux, gamma=wl.gamma, velocity=wl.velocity,
-                   bounds=wl.bounds, eps=wl.eps, bc=wl.bc, bc_state=wl.bc_state, **kw)
+        s = cls(wl.dim, wl.nx, wl.ny, wl.k, wl.domain, wl.flux, gamma=wl.gamma, velocity=wl.velocity,
+                bounds=wl.bounds, eps=wl.eps, bc=wl.bc, bc_state=wl.bc_state, **kw)
+        if getattr(wl, "geo", None) is not None:
+            s.set_geometry(wl.geo, wl.geo_states[0], wl.geo_states[1], *wl.shock)
+        return s
+
+    def set_geometry(self, geo, state_a=None, state_b=None, shock_x0=0.0, shock_speed=0.0):
+        """Non-rectangular domain: one geometry word per cell (numpy uint32, see
+        crkdg_set_geometry), the fixed states A and B, and the moving shock line; None removes it."""
+        if geo is None:
+            self._chk(self.lib.crkdg_set_geometry(self.h, None, None, None, 0.0, 0.0))
+            return
+        g = np.ascontiguousarray(np.asarray(geo, dtype=np.uint32).reshape(-1))
+        if g.size != self.nx * self.ny:
+            raise ValueError("set_geometry: one word per cell")
+        sa = np.zeros(self.m) if state_a is None else np.ascontiguousarray(state_a, dtype=np.float64)
+        sb = np.zeros(self.m) if state_b is None else np.ascontiguousarray(state_b, dtype=np.float64)
+        self._chk(self.lib.crkdg_set_geometry(self.h, g.ctypes.data_as(C.POINTER(C.c_uint)),
+                                              sa.ctypes.data_as(L._dp), sb.ctypes.data_as(L._dp),
+                                              float(shock_x0), float(shock_speed)))
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:
