@@ -46,7 +46,12 @@ def _pair(wl):
 @pytest.mark.parametrize("k", [1, 2, 3])
 def test_geometry_operator_F(example, k):
     """F on a seeded oscillating state: walls, fixed states, inflow, outflow and (double Mach)
-    the shock line at t = 0.05, where it has left its initial cell on the top side."""
+    the shock line at t = 0.05, where it has left its initial cell on the top side.
+
+    Held to 1e-12 relative, or to 10 times the oracle's own response to a one-ulp relative
+    perturbation of its input where that is larger: on the 26 x 24 diffraction mesh the
+    seeded state has near-vacuum points whose Lax-Friedrichs viscosity amplifies rounding
+    (the oracle against itself: 2.5e-12 for Q^2, 1.4e-12 for Q^3)."""
     wl = _workload(example, k)
     g, o = _pair(wl)
     U = inputs.random_euler(2, wl.nx, wl.ny, k, seed=90 + k, osc=0.3)
@@ -56,8 +61,11 @@ def test_geometry_operator_F(example, k):
     out = torch.empty_like(x)
     g.apply("F", x, out)
     ref = o.to_nodal(o.apply("F", o.to_modal(U), t=t))
+    rng = np.random.default_rng(5)
+    envelope = max(rel_linf(o.to_nodal(o.apply("F", o.to_modal(U * (1.0 + 2.2e-16 * rng.standard_normal(U.shape))),
+                                               t=t)), ref, 4) for _ in range(3))
     got = out.cpu().numpy()
-    assert rel_linf(got, ref, 4) < 1e-12
+    assert rel_linf(got, ref, 4) < max(1e-12, 10.0 * envelope)
     solid = ((wl.geo & GEO_SOLID) != 0).reshape(wl.ny, wl.nx)
     assert not got.reshape(4, wl.ny, wl.nx, -1)[:, solid].any()  # no operator outside the domain
 
