@@ -3,7 +3,7 @@
 The shock diffraction and the double Mach reflection run on the bounding rectangle with the
 solid cells masked, walls on the sides facing them, an inflow side, a fixed state on part of
 a wall and the exact moving shock on a side.  Through the C ABI: the operator F at a stage
-time (rel L-inf 1e-12, as the rectangular operators), steps of both benchmarks (rel L-inf
+time (rel L-inf 1e-12, or the oracle's own rounding envelope where larger), steps of both benchmarks (rel L-inf
 1e-10, identical restarts, bounds exact at every step), solid cells untouched, and the
 argument checks of crkdg_set_geometry.
 """
