@@ -62,10 +62,15 @@ WORKLOADS = {
     "sedov_shell_2048_q3_mixed": dict(kind="sedov_shell", nx=2048, k=3, precision="mixed"),
     "sedov_shell_2048_q3_fp64": dict(kind="sedov_shell", nx=2048, k=3),
     "riemann_1024_q2_standard": dict(kind="riemann", nx=1024, k=2, scheme="standard"),
+    # the non-rectangular benchmarks at the paper's resolutions: the double Mach reflection
+    # (Example 4.9, Q^3, cells of side 1/360) and the shock diffraction (Example 4.8, Q^2, 1/64)
+    "double_mach_360_q3": dict(kind="double_mach", per_unit=360, k=3),
+    "shock_diffraction_64_q2": dict(kind="shock_diffraction", per_unit=64, k=2),
 }
 DEFAULT = "sedov_2048_q3_mixed"
 # timed steps when --steps is not given
-DEFAULT_STEPS = {"euler1d": 2000, "burgers": 2000, "sedov": 50, "sedov_shell": 50, "riemann": 100, "ensemble": 5}
+DEFAULT_STEPS = {"euler1d": 2000, "burgers": 2000, "sedov": 50, "sedov_shell": 50, "riemann": 100, "ensemble": 5,
+                 "double_mach": 50, "shock_diffraction": 50}
 
 
 def launches_per_attempt(precision, indicator):
@@ -98,7 +103,23 @@ def make_workload(name, seed=0, nx=None):
         return inputs.sedov(w["nx"], w["k"])
     if w["kind"] == "sedov_shell":
         return inputs.sedov_shell(w["nx"], w["k"])
+    if w["kind"] in ("double_mach", "shock_diffraction"):
+        # a sample of width nx takes cells of side 16 / nx (a 4-unit-wide rectangle 4 nx / 16
+        # cells wide for the double Mach reflection)
+        per_unit = max(2, nx // 16) if nx is not None else w["per_unit"]
+        make = inputs.double_mach if w["kind"] == "double_mach" else inputs.shock_diffraction
+        return make(cells_per_unit=per_unit, k=w["k"])
     return inputs.riemann_quadrants(seed, w["nx"], w["k"])
+
+
+def active_cells(wl):
+    """Cells of the domain: every cell of a rectangular mesh, the fluid cells of a
+    non-rectangular one (the solid cells carry no unknowns of the problem)."""
+    if getattr(wl, "geo", None) is None:
+        return wl.cells
+    from paper_2412_16002_gb300.inputs import GEO_SOLID
+
+    return int(((wl.geo & GEO_SOLID) == 0).sum())
 
 
 INITIAL_STATE = {"sedov_shell": "a developed Sedov-type blast: dense shell of radius 0.3 around the corner, "
@@ -281,6 +302,8 @@ def _oracle_worker(name, warmup, steps, budget_s, nx=None):
     o = Oracle(wl.dim, wl.nx, wl.ny, wl.k, wl.domain, wl.flux, gamma=wl.gamma, velocity=wl.velocity,
                bounds=wl.bounds, eps=wl.eps, bc=wl.bc, bc_state=wl.bc_state,
                scheme=WORKLOADS[name].get("scheme", "compact"))
+    if getattr(wl, "geo", None) is not None:
+        o.set_geometry(wl.geo, wl.geo_states[0], wl.geo_states[1], *wl.shock)
     o.set_state(wl.state)
     t = 0.0
     for _ in range(warmup):
@@ -295,7 +318,7 @@ def _oracle_worker(name, warmup, steps, budget_s, nx=None):
         t += info["dt_taken"]
         n += 1
     el = time.perf_counter() - t0
-    return n, el, wl.cells * wl.dofs_per_cell * TAB_S[wl.tableau]
+    return n, el, active_cells(wl) * wl.dofs_per_cell * TAB_S[wl.tableau]
 
 
 def oracle_throughput(name, procs, warmup=0, steps=None, budget_s=10.0, nx=None):
@@ -343,7 +366,7 @@ def workload_config(name, wl, world):
     """The config dict both arms print for a workload."""
     return {"workload": name, "precision": WORKLOADS[name].get("precision", "fp64"),
             "scheme": WORKLOADS[name].get("scheme", "compact"),
-            "indicator": WORKLOADS[name].get("indicator", "off"), "cells": wl.cells, "k": wl.k, "m": wl.m,
+            "indicator": WORKLOADS[name].get("indicator", "off"), "cells": active_cells(wl), "k": wl.k, "m": wl.m,
             "dofs_per_cell": wl.dofs_per_cell, "tableau": wl.tableau, "stages": TAB_S[wl.tableau],
             "cfl": wl.cfl, "initial_state": INITIAL_STATE.get(WORKLOADS[name]["kind"], "the workload's initial data at t = 0"),
             "l2": "GPU arm: L2 flushed (256 MB write) between timed steps" if wl.dim == 2 else
@@ -449,7 +472,7 @@ def run_decomposed(args, wl, name):
     clocks = sampler.stop() if sampler else None
     kt, kn = g.kernel_times()
     g.set_profiling(False)
-    units = wl.cells * wl.dofs_per_cell * TAB_S[wl.tableau] * args.steps
+    units = active_cells(wl) * wl.dofs_per_cell * TAB_S[wl.tableau] * args.steps
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
@@ -471,7 +494,7 @@ def run_decomposed(args, wl, name):
     torch.cuda.synchronize()
     t = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = wl.cells * wl.dofs_per_cell * TAB_S[wl.tableau] * e2e_steps / float(t.item())
+    e2e_value = active_cells(wl) * wl.dofs_per_cell * TAB_S[wl.tableau] * e2e_steps / float(t.item())
     nbytes = host_in.numel() * 8 * world  # every rank's local block (owned cells and halo ring)
     if rank == 0:
         inner_f, final_f = algorithmic_flops(wl)
@@ -585,7 +608,7 @@ def run_gb300(args, wl, name):
     clocks = sampler.stop() if sampler else None
     kt, kn = g.kernel_times()
     g.set_profiling(False)
-    value, ms_max = job_rate(ms, wl.cells * wl.dofs_per_cell * TAB_S[wl.tableau] * args.steps, world, dev)
+    value, ms_max = job_rate(ms, active_cells(wl) * wl.dofs_per_cell * TAB_S[wl.tableau] * args.steps, world, dev)
 
     # end to end through the C ABI with host buffers: H2D of the state, one step, D2H
     host_in = torch.from_numpy(g.get_state().reshape(-1).copy()).pin_memory()
@@ -604,7 +627,7 @@ def run_gb300(args, wl, name):
         host_in, host_out = host_out, host_in  # the result is the next step's input
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_value, _ = job_rate(1e3 * e2e_s, wl.cells * wl.dofs_per_cell * TAB_S[wl.tableau] * e2e_steps, world, dev)
+    e2e_value, _ = job_rate(1e3 * e2e_s, active_cells(wl) * wl.dofs_per_cell * TAB_S[wl.tableau] * e2e_steps, world, dev)
 
     if rank == 0:
         inner_f, final_f = algorithmic_flops(wl)
@@ -622,7 +645,7 @@ def run_gb300(args, wl, name):
             dom, avg_ms, fl = "k_inner" + isfx, avg_inner, inner_f
         else:
             dom, avg_ms, fl = "k_final" + sfx, avg_final, final_f
-        achieved = fl * wl.cells / (avg_ms / 1e3) / 1e12
+        achieved = fl * active_cells(wl) / (avg_ms / 1e3) / 1e12
         # the split path runs its operators in FP32: its roofline is the FP32 peak
         peak = FP32_PEAK_TFLOPS if precision == "mixed" else FP64_PEAK_TFLOPS
         peak_src = ("FP32 derived from unit count and clock (152 SMs x 128 lanes x 2 x 2070 MHz)" if precision == "mixed"
