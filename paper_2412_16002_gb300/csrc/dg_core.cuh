@@ -323,10 +323,8 @@ __device__ __forceinline__ void exterior_state(const Params &P, int side, const 
     }
 }
 
-// neighbour across side (0 L, 1 R, 2 B, 3 T), or -1 on a non-periodic boundary or a side
-// that a non-rectangular domain's geometry word gives a boundary kind
+// neighbour across side (0 L, 1 R, 2 B, 3 T), or -1 on a non-periodic boundary
 __device__ __forceinline__ int neighbour(const Params &P, int cell, int side) {
-    if (P.geo != nullptr && ((P.geo[cell] >> (4 * side)) & 15u) != GEO_MESH) return -1;
     int cx = cell % P.nx, cy = cell / P.nx;
     switch (side) {
     case 0: return cx > 0 ? cell - 1 : (P.bc[0] == BC_PERIODIC ? cell + P.nx - 1 : -1);
@@ -334,6 +332,13 @@ __device__ __forceinline__ int neighbour(const Params &P, int cell, int side) {
     case 2: return cy > 0 ? cell - P.nx : (P.bc[2] == BC_PERIODIC ? cell + (P.ny - 1) * P.nx : -1);
     default: return cy < P.ny - 1 ? cell + P.nx : (P.bc[3] == BC_PERIODIC ? cell - (P.ny - 1) * P.nx : -1);
     }
+}
+
+// The same, and -1 on a side that a non-rectangular domain's geometry word gives a boundary
+// kind (the FP64 final stage; the kernels that reject a geometry keep the plain rule)
+__device__ __forceinline__ int neighbour_geo(const Params &P, int cell, int side) {
+    if (P.geo != nullptr && ((P.geo[cell] >> (4 * side)) & 15u) != GEO_MESH) return -1;
+    return neighbour(P, cell, side);
 }
 
 // Exterior trace of a boundary face point of a non-rectangular domain (Examples 4.8, 4.9) in
@@ -1079,7 +1084,7 @@ __device__ __forceinline__ void final_body(const Params &P, const Bufs &B, int b
                 int face = fp / NF, pos = fp - face * NF;
 #pragma unroll
                 for (int c = 0; c < M; ++c) ui[j][c] = tr[((size_t)c * P.ncell + cell) * NTR + fp];
-                int nb = neighbour(P, cell, face);
+                int nb = neighbour_geo(P, cell, face);
                 nbr[j] = nb;
                 int ofp = (face ^ 1) * NF + pos;
                 if (nb >= 0) {
