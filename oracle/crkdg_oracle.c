@@ -49,6 +49,12 @@
  *     + minmod(c_y, D+y, D-y) P_1(eta) (its first Legendre moments limited, every
  *     higher mode dropped), which keeps the average;
  *   - neighbour averages across the boundary follow the boundary condition.
+ *
+ * Non-rectangular domains (Sec. 4.4, Examples 4.8 and 4.9): the domain is a union of
+ * cells of the bounding rectangle; the other cells are solid and take no part.  A
+ * per-cell word gives each side a boundary kind (reflective wall, outflow, a fixed
+ * state, or the exact trace of a planar shock moving at constant speed, evaluated at
+ * the stage time); see orc_set_geometry.
  */
 #include "crkdg_oracle.h"
 
