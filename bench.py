@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -104,9 +105,10 @@ def make_workload(name, seed=0, nx=None):
     if w["kind"] == "sedov_shell":
         return inputs.sedov_shell(w["nx"], w["k"])
     if w["kind"] in ("double_mach", "shock_diffraction"):
-        # a sample of width nx takes cells of side 16 / nx (a 4-unit-wide rectangle 4 nx / 16
-        # cells wide for the double Mach reflection)
-        per_unit = max(2, nx // 16) if nx is not None else w["per_unit"]
+        # a sample of width nx holds about nx^2 cells: the bounding rectangle's area (4 x 2 or
+        # 13 x 12) in cells of side 1 / per_unit
+        area = 8.0 if w["kind"] == "double_mach" else 156.0
+        per_unit = max(2, int(round(nx / math.sqrt(area)))) if nx is not None else w["per_unit"]
         make = inputs.double_mach if w["kind"] == "double_mach" else inputs.shock_diffraction
         return make(cells_per_unit=per_unit, k=w["k"])
     return inputs.riemann_quadrants(seed, w["nx"], w["k"])

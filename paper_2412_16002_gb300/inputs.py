@@ -353,7 +353,9 @@ def double_mach(cells_per_unit=360, k=3, cfl=None, t_end=0.2, gamma=GAMMA):
     rho = 8, w = (4.125 sqrt 3, -4.125), p = 116.5.  Inflow (post-shock) on the left, outflow
     on the right and the bottom, the post-shock state on y = 0 for x < 1/6, reflective walls
     y = 0 (1/6 <= x <= 1) and x = 1 (y <= 0), and on the top side the exact shock motion:
-    post-shock where x < 1/6 + (1 + 20 t)/sqrt 3.  Solid cells hold the ambient state."""
+    post-shock where x < 1/6 + (1 + 20 t)/sqrt 3.  Solid cells hold the ambient state.  The
+    fixed-state part of the wall is the cells whose centre lies at x < 1/6: exactly [0, 1/6)
+    when cells_per_unit is a multiple of 6, as at the paper's 360, 480 and 600."""
     nx, ny = 4 * cells_per_unit, 2 * cells_per_unit
     dom = (0.0, 4.0, -1.0, 1.0)
     h = 1.0 / cells_per_unit
