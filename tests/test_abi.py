@@ -73,3 +73,5 @@ def test_options_default_and_create_argument_checks(lib):
     assert lib2.crkdg_create(ctypes.byref(mesh), 2, 3, ctypes.byref(fl), ctypes.byref(bd), None, ctypes.byref(h)) == L.E_ARG
     assert lib2.crkdg_destroy(None) == L.OK
     assert lib2.crkdg_state_size(None) == 0
+    geo = (ctypes.c_uint * 4)()
+    assert lib2.crkdg_set_geometry(None, geo, None, None, 0.0, 0.0) == L.E_ARG
